@@ -1,0 +1,413 @@
+"""FP64 CPU oracle for MGARD+ multilevel decomposition, recomposition and
+level-wise quantization (Liang et al., "MGARD+: Optimizing Multilevel Methods
+for Error-bounded Scientific Data Reduction", arXiv 2010.05872).
+
+TEST INFRASTRUCTURE ONLY.  This module is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py``.  The product path (the CUDA library and its Python
+binding) never imports it, and it imports nothing from the product package.
+
+What it computes is the plain definition of the transform, written with
+explicit finite-element operators assembled from the grid coordinates:
+
+* ``Q_{l-1}`` is the L2 projection from the level-l piecewise-multilinear
+  space onto the level-(l-1) one (Section 2, "Background"): per axis
+  ``A_d = M_c^{-1} P^T M_f`` with ``M`` the P1 mass matrix (integrals of
+  products of hat functions), ``P`` the 1D linear prolongation and
+  ``M_c`` assembled from the coarse coordinates; the tensor-product operator is
+  applied one axis at a time (axis d-1 first).
+* ``Pi_{l-1}`` is multilinear interpolation from the coarse nodes
+  (Section 2; the 1/2, 1/4, 1/8 stencils of Eq. (multilinear_interp) in
+  Section 4.2 are its uniform-grid case).
+* Decomposition (Section 2, decomposition steps 1-6) stores
+  ``(I - Pi_{l-1}) Q_l u`` at the coefficient nodes ``N*_l`` and ``Q_{l~} u``
+  on ``N_{l~}``.  Unlike the paper's route (interpolant, then the correction
+  computed from the coefficients only), the oracle forms ``Q_{l-1} u``
+  directly as the projection of the level-l function; the paper's identity
+  ``Q_{l-1}u = u|_{N_{l-1}} + Q_{l-1}(I - Pi_{l-1})Q_l u`` is checked in the
+  tests instead of being used here.
+* Recomposition (Section 2, recomposition steps 1-5): the correction
+  ``z = Q_{l-1}(w)`` of the coefficient function ``w``, subtraction, then
+  interpolation plus coefficients.
+* Level tolerances: Eq. (LinfTau) of Section 4.1 with the stopping level of
+  Algorithm 1 (lines 17-20): ``tau_l~ = (1-k) tau / ((1-k^(L+1-l~)) C)``,
+  ``tau_l = k tau_{l-1}``, ``k = sqrt(2^d)``.
+* Quantizer (Section 4.1): zero-centred bins of width ``q_l = 2 tau_l``,
+  label ``round(x / q_l)`` with ties away from zero, value ``label * q_l``.
+
+Readings of points the paper leaves open (non-dyadic hierarchy, depth for
+non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
+that implement them.
+
+Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
+(exact rationals from the finite-element definition, quadrature-based
+orthogonality, Lemma 1 and the printed mass matrix of Section 5.4, the
+interpolation stencils of Eq. (multilinear_interp), dense Kronecker brute
+force, invariants and bounds).  ``linf_constant`` is a reading (the paper
+gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
+worst-case error amplification, and its exact value is "parity unpinned" with
+respect to the paper.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.linalg import solve_banded
+
+__all__ = [
+    "coarse_indices", "Hierarchy", "mass_matrix", "prolongation",
+    "project_axis", "project", "interpolate", "decompose", "recompose",
+    "linf_constant", "level_tolerances", "node_levels", "llround",
+    "quantize", "dequantize", "value_range",
+]
+
+
+# --------------------------------------------------------------------------
+# Grid hierarchy (Section 2, "Background"; Fig. 1)
+# --------------------------------------------------------------------------
+
+def coarse_indices(n: int) -> np.ndarray:
+    """Indices, within one axis of ``n`` level-l nodes, of the nodes that the
+    level-(l-1) grid keeps.
+
+    Section 2 only asks for nested grids ``N_{l-1} subset N_l``; for sizes
+    that are not ``2^k + 1`` the paper says MGARD+ adds dummy nodes during
+    reordering (Section 6.2.2) without defining them.  Reading used here: keep
+    every even index, and when ``n`` is even keep the last node too, so the
+    last coarse cell has no midpoint.  The coarse size is ``n // 2 + 1``.
+    """
+    if n < 2:
+        raise ValueError("an axis needs at least 2 nodes to coarsen")
+    keep = list(range(0, n, 2))
+    if n % 2 == 0:
+        keep.append(n - 1)
+    return np.asarray(keep, dtype=np.int64)
+
+
+@dataclass
+class AxisOps:
+    """1D operators between level l and level l-1 along one axis."""
+    keep: np.ndarray          # coarse node positions inside the fine axis
+    Mf: sp.csr_matrix         # fine P1 mass matrix (n x n)
+    P: sp.csr_matrix          # linear prolongation (n x n')
+    Mc: sp.csr_matrix         # coarse P1 mass matrix (n' x n')
+
+
+class Hierarchy:
+    """Nested tensor-product grids ``N_L > ... > N_0`` (Section 2).
+
+    ``levels[l]`` is the shape of ``N_l``; ``index[l][d]`` maps level-l node
+    positions on axis ``d`` to finest-grid indices; ``coords[l][d]`` are their
+    coordinates.  Every axis is coarsened at every level and the hierarchy
+    stops when the smallest axis has 3 nodes (the 65^3 example coarsens to
+    3x3x3).  Coordinates default to the node index (results do not depend on
+    the scale or origin of the coordinates).
+    """
+
+    def __init__(self, dims, coords=None):
+        dims = tuple(int(n) for n in dims)
+        if not 1 <= len(dims) or any(n < 3 for n in dims):
+            raise ValueError(f"every axis needs at least 3 nodes, got {dims}")
+        self.ndim = len(dims)
+        shapes = [dims]
+        while min(shapes[-1]) > 3:
+            shapes.append(tuple(len(coarse_indices(n)) for n in shapes[-1]))
+        self.L = len(shapes) - 1
+        self.levels = {self.L - i: s for i, s in enumerate(shapes)}
+        if coords is None:
+            coords = [None] * self.ndim
+        xs = []
+        for d, n in enumerate(dims):
+            x = (np.arange(n, dtype=np.float64) if coords[d] is None
+                 else np.asarray(coords[d], dtype=np.float64))
+            if x.shape != (n,):
+                raise ValueError(f"axis {d}: expected {n} coordinates")
+            if not np.all(np.diff(x) > 0):
+                raise ValueError(f"axis {d}: coordinates must increase strictly")
+            xs.append(x)
+        self.index = {self.L: [np.arange(n, dtype=np.int64) for n in dims]}
+        for l in range(self.L, 0, -1):
+            self.index[l - 1] = [ix[coarse_indices(len(ix))] for ix in self.index[l]]
+        self.coords = {l: [xs[d][self.index[l][d]] for d in range(self.ndim)]
+                       for l in range(self.L + 1)}
+        self._ops = {}
+
+    def ops(self, l: int) -> list[AxisOps]:
+        """Per-axis operators of the level l -> l-1 transition."""
+        if l not in self._ops:
+            out = []
+            for d in range(self.ndim):
+                x = self.coords[l][d]
+                keep = coarse_indices(len(x))
+                out.append(AxisOps(keep, mass_matrix(x), prolongation(x, keep),
+                                   mass_matrix(x[keep])))
+            self._ops[l] = out
+        return self._ops[l]
+
+    def nodal_mask(self, l: int) -> np.ndarray:
+        """Boolean array over ``N_l``: True on the nodes of ``N_{l-1}``."""
+        m = np.zeros(self.levels[l], dtype=bool)
+        m[np.ix_(*[o.keep for o in self.ops(l)])] = True
+        return m
+
+
+# --------------------------------------------------------------------------
+# 1D finite-element operators
+# --------------------------------------------------------------------------
+
+def mass_matrix(x: np.ndarray) -> sp.csr_matrix:
+    """P1 mass matrix ``M[i, j] = integral of phi_i phi_j`` on the nodes ``x``.
+
+    On a cell of length ``D`` the two hat functions give ``D/3`` on the
+    diagonal and ``D/6`` off it, so row ``j`` has diagonal
+    ``(D_{j-1} + D_j) / 3`` and neighbours ``D_{j-1}/6``, ``D_j/6``.  For a
+    uniform coarse grid of spacing ``2h`` this is the matrix printed in
+    Section 5.4 (``2h/3`` at the ends, ``4h/3`` inside, ``h/3`` off the
+    diagonal).
+    """
+    D = np.diff(np.asarray(x, dtype=np.float64))
+    diag = np.zeros(len(x))
+    diag[:-1] += D / 3.0
+    diag[1:] += D / 3.0
+    off = D / 6.0
+    return sp.diags([off, diag, off], [-1, 0, 1], format="csr")
+
+
+def prolongation(x: np.ndarray, keep: np.ndarray) -> sp.csr_matrix:
+    """Piecewise-linear interpolation from the nodes ``x[keep]`` to all of
+    ``x`` (``n x n'``).  Kept nodes copy their value; a node between kept
+    nodes ``a < j < b`` takes ``(x_b - x_j)/(x_b - x_a)`` of the left value and
+    ``(x_j - x_a)/(x_b - x_a)`` of the right one (Section 2, ``Pi_l``)."""
+    x = np.asarray(x, dtype=np.float64)
+    n, nc = len(x), len(keep)
+    rows, cols, vals = [], [], []
+    for k, j in enumerate(keep):
+        rows.append(j); cols.append(k); vals.append(1.0)
+    for k in range(nc - 1):
+        a, b = int(keep[k]), int(keep[k + 1])
+        for j in range(a + 1, b):
+            rows += [j, j]
+            cols += [k, k + 1]
+            vals += [(x[b] - x[j]) / (x[b] - x[a]), (x[j] - x[a]) / (x[b] - x[a])]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, nc))
+
+
+def _banded(M: sp.spmatrix) -> np.ndarray:
+    """Tridiagonal matrix in LAPACK banded storage (upper, main, lower)."""
+    n = M.shape[0]
+    ab = np.zeros((3, n))
+    ab[1] = M.diagonal(0)
+    if n > 1:
+        ab[0, 1:] = M.diagonal(1)
+        ab[2, :-1] = M.diagonal(-1)
+    return ab
+
+
+def project_axis(v: np.ndarray, axis: int, op: AxisOps) -> np.ndarray:
+    """Apply ``A = M_c^{-1} P^T M_f`` along one axis: the 1D L2 projection
+    (mass multiply, restriction to the load vector, tridiagonal solve;
+    Section 2 step 4 and Section 5.2-5.4)."""
+    vm = np.moveaxis(v, axis, 0)
+    shape = vm.shape
+    X = np.ascontiguousarray(vm).reshape(shape[0], -1)
+    F = op.P.T @ (op.Mf @ X)
+    Z = solve_banded((1, 1), _banded(op.Mc), F)
+    return np.moveaxis(Z.reshape((op.Mc.shape[0],) + shape[1:]), 0, axis)
+
+
+def project(v: np.ndarray, H: Hierarchy, l: int) -> np.ndarray:
+    """``Q_{l-1}`` of a level-l nodal array: the tensor product of the 1D
+    projections, applied axis by axis, axis d-1 first ("row sweep then
+    column sweep", Section 5.1; the order does not matter in exact
+    arithmetic)."""
+    ops = H.ops(l)
+    out = np.asarray(v, dtype=np.float64)
+    for d in reversed(range(H.ndim)):
+        out = project_axis(out, d, ops[d])
+    return out
+
+
+def interpolate(c: np.ndarray, H: Hierarchy, l: int) -> np.ndarray:
+    """``Pi_{l-1}``: multilinear interpolation of level-(l-1) nodal values to
+    all of ``N_l`` (tensor product of the 1D prolongations)."""
+    out = np.asarray(c, dtype=np.float64)
+    for d, op in enumerate(H.ops(l)):
+        vm = np.moveaxis(out, d, 0)
+        shape = vm.shape
+        X = np.ascontiguousarray(vm).reshape(shape[0], -1)
+        out = np.moveaxis((op.P @ X).reshape((op.P.shape[0],) + shape[1:]), 0, d)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Decomposition / recomposition (Section 2)
+# --------------------------------------------------------------------------
+
+def _check_stop(H: Hierarchy, stop_level: int):
+    if not 0 <= stop_level <= H.L:
+        raise ValueError(f"stop level {stop_level} outside [0, {H.L}]")
+
+
+def decompose(u: np.ndarray, H: Hierarchy, stop_level: int = 0) -> np.ndarray:
+    """Multilevel coefficients ``u_mc`` of ``u`` (Section 2).
+
+    For ``l = L .. l~+1``: ``Q_{l-1}u`` is the projection of ``Q_l u``; the
+    coefficients ``(I - Pi_{l-1}) Q_l u`` are stored at the nodes of
+    ``N*_l``; the nodes of ``N_{l~}`` finally hold ``Q_{l~} u``.  ``u_mc`` is
+    indexed by the finest grid, as Section 2 defines it."""
+    _check_stop(H, stop_level)
+    v = np.asarray(u, dtype=np.float64)
+    if v.shape != H.levels[H.L]:
+        raise ValueError("array shape does not match the hierarchy")
+    out = v.copy()
+    for l in range(H.L, stop_level, -1):
+        keep = [o.keep for o in H.ops(l)]
+        c = project(v, H, l)
+        mc = v - interpolate(v[np.ix_(*keep)], H, l)
+        out[np.ix_(*H.index[l])] = mc          # nodal entries are overwritten below
+        v = c
+    out[np.ix_(*H.index[stop_level])] = v
+    return out
+
+
+def recompose(umc: np.ndarray, H: Hierarchy, stop_level: int = 0) -> np.ndarray:
+    """Inverse of :func:`decompose` (Section 2, recomposition steps 1-5).
+
+    For ``l = l~+1 .. L``: ``z = Q_{l-1} w`` with ``w`` the level-l
+    coefficients (zero on ``N_{l-1}``), ``Pi_{l-1}Q_l u = Q_{l-1}u - z`` on the
+    coarse nodes, then ``Q_l u = Pi_{l-1}(Q_{l-1}u - z) + w``."""
+    _check_stop(H, stop_level)
+    umc = np.asarray(umc, dtype=np.float64)
+    v = umc[np.ix_(*H.index[stop_level])].copy()
+    for l in range(stop_level + 1, H.L + 1):
+        w = umc[np.ix_(*H.index[l])].copy()
+        w[H.nodal_mask(l)] = 0.0
+        z = project(w, H, l)
+        v = interpolate(v - z, H, l) + w
+    return v
+
+
+# --------------------------------------------------------------------------
+# Level-wise quantization (Section 4.1, Algorithm 1)
+# --------------------------------------------------------------------------
+
+def projection_matrix(op: AxisOps) -> np.ndarray:
+    """Dense ``A = M_c^{-1} P^T M_f`` (n' x n) of one axis."""
+    R = (op.P.T @ op.Mf).toarray()
+    return np.linalg.solve(op.Mc.toarray(), R)
+
+
+def linf_constant(H: Hierarchy, stop_level: int = 0) -> float:
+    """``C_Linf`` of Eq. (LInfNormEstimator) for this hierarchy.
+
+    The paper takes the constant from its reference [ainsworth2019] without
+    giving a value.  Reading used here, derived from the recomposition steps:
+    with ``E_l`` the max-norm error of ``Q_l u`` and ``e_l`` that of the
+    level-l coefficients, recomposition gives
+    ``|E_l| <= |E_{l-1}| + (1 + |K_l|) |e_l|`` where ``K_l`` maps the level-l
+    coefficients to the correction (interpolation has convex weights, so it
+    does not enlarge the max norm).  Hence
+    ``C = 1 + max_l |K_l|_inf`` makes ``sum_l tau_l <= tau / C`` sufficient.
+    ``|K_l|_inf`` is the largest row sum over coarse rows of
+    ``prod_d r_d - prod_d s_d`` where ``r_d`` / ``s_d`` are the absolute row
+    sums of ``A_d`` over all / over coarse columns.  It is bounded from above
+    by the telescoping sum
+    ``sum_d (prod_{e<d} max s_e) max(r_d - s_d) (prod_{e>d} max r_e)``,
+    which is what is used (exact in 1D; a valid upper bound in 2D/3D).
+    ``C = 1`` when no level is decomposed.
+    """
+    _check_stop(H, stop_level)
+    C = 1.0
+    for l in range(stop_level + 1, H.L + 1):
+        R, S, Dm = [], [], []
+        for op in H.ops(l):
+            A = np.abs(projection_matrix(op))
+            r = A.sum(axis=1)
+            s = A[:, op.keep].sum(axis=1)
+            R.append(r.max()); S.append(s.max()); Dm.append((r - s).max())
+        norm = 0.0
+        for d in range(H.ndim):
+            term = Dm[d]
+            for e in range(d):
+                term *= S[e]
+            for e in range(d + 1, H.ndim):
+                term *= R[e]
+            norm += term
+        C = max(C, 1.0 + norm)
+    return C
+
+
+def level_tolerances(H: Hierarchy, stop_level: int, tau: float,
+                     C: float | None = None) -> np.ndarray:
+    """Per-level tolerances ``tau_l`` for ``l = 0..L`` (entries below the
+    stopping level are unused and set to ``tau_{l~}``).
+
+    Algorithm 1 line 17 gives ``tau_{l~}``; lines 19-20 scale by
+    ``kappa = sqrt(2^d)`` per level (Eq. (LinfTau) with the sum starting at
+    the stopping level), so that ``sum_{l>=l~} tau_l = tau / C``."""
+    _check_stop(H, stop_level)
+    if C is None:
+        C = linf_constant(H, stop_level)
+    kappa = math.sqrt(2.0 ** H.ndim)
+    m = H.L + 1 - stop_level
+    kpow = 1.0
+    for _ in range(m):
+        kpow *= kappa
+    taus = np.empty(H.L + 1)
+    taus[stop_level] = (1.0 - kappa) * tau / ((1.0 - kpow) * C)
+    for l in range(stop_level + 1, H.L + 1):
+        taus[l] = kappa * taus[l - 1]
+    taus[:stop_level] = taus[stop_level]
+    return taus
+
+
+def node_levels(H: Hierarchy, stop_level: int = 0) -> np.ndarray:
+    """Level of every finest node: the least ``l`` with the node in ``N_l``
+    (Section 2's indexing of ``u_mc``), raised to the stopping level because
+    the whole of ``N_{l~}`` is quantized with ``tau_{l~}`` (Algorithm 1 lines
+    17-18)."""
+    per_axis = []
+    for d in range(H.ndim):
+        lev = np.full(H.levels[H.L][d], H.L, dtype=np.int64)
+        for l in range(H.L - 1, -1, -1):
+            lev[H.index[l][d]] = l
+        per_axis.append(lev)
+    out = per_axis[0]
+    for lev in per_axis[1:]:
+        out = np.maximum.outer(out, lev)
+    return np.maximum(out.reshape(H.levels[H.L]), stop_level)
+
+
+def llround(y: np.ndarray) -> np.ndarray:
+    """Round to the nearest integer, ties away from zero, exactly: the
+    fractional part ``y - trunc(y)`` is exact in binary floating point."""
+    y = np.asarray(y, dtype=np.float64)
+    t = np.trunc(y)
+    return (t + np.sign(y) * (np.abs(y - t) >= 0.5)).astype(np.int64)
+
+
+def quantize(umc: np.ndarray, H: Hierarchy, stop_level: int,
+             taus: np.ndarray) -> np.ndarray:
+    """Labels ``round(u_mc / q_l)`` with bin width ``q_l = 2 tau_l`` and the
+    bin centre as the value (Section 4.1), computed in FP64 (an FP32
+    coefficient is widened first)."""
+    lev = node_levels(H, stop_level)
+    q = 2.0 * np.asarray(taus, dtype=np.float64)[lev]
+    return llround(np.asarray(umc, dtype=np.float64) / q)
+
+
+def dequantize(labels: np.ndarray, H: Hierarchy, stop_level: int,
+               taus: np.ndarray, dtype=np.float64) -> np.ndarray:
+    """Bin centres ``label * q_l`` in FP64, rounded to ``dtype``."""
+    lev = node_levels(H, stop_level)
+    q = 2.0 * np.asarray(taus, dtype=np.float64)[lev]
+    return (np.asarray(labels, dtype=np.int64).astype(np.float64) * q).astype(dtype)
+
+
+def value_range(u: np.ndarray) -> float:
+    """``max u - min u`` in FP64: the scale of a relative error bound."""
+    u = np.asarray(u, dtype=np.float64)
+    return float(u.max() - u.min())

@@ -1,0 +1,456 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here re-types an oracle formula: the expected values come from hand
+derivations (tests/golden), numbers printed in the paper (Lemma 1, the mass
+matrix of Section 5.4, the interpolation stencils of Section 4.2), numerical
+quadrature with an independent piecewise-linear evaluator, exact rational
+arithmetic, dense Kronecker brute force, and invariants of the transform.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy.interpolate import RegularGridInterpolator
+
+from oracle import mgard_oracle as O
+from paper_2010_05872_gb300 import fields as F
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- golden ---
+
+def _golden_cases():
+    cases = []
+    with open(os.path.join(GOLDEN, "corrections.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            dims_s, coords_s, w_s, exp_s = [p.strip() for p in line.split("|")]
+            dims = tuple(int(v) for v in dims_s.split("x"))
+            coords = []
+            for c in coords_s.split(";"):
+                coords.append(None if c == "u" else np.array([float(v) for v in c.split(",")]))
+            w = np.zeros(dims)
+            for ent in w_s.split():
+                idx, val = ent.split(":")
+                w[tuple(int(v) for v in idx.split(","))] = float(val)
+            exp = np.array([float(Fraction(v)) for v in exp_s.split()])
+            cases.append((dims, coords, w, exp))
+    return cases
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: str(c[0]))
+def test_golden_corrections(case):
+    """Hand-derived exact corrections (Section 2 step 4)."""
+    dims, coords, w, exp = case
+    H = O.Hierarchy(dims, coords)
+    z = O.project(w, H, H.L)
+    np.testing.assert_allclose(z.ravel(), exp, rtol=0, atol=1e-15)
+
+
+def test_golden_node_levels():
+    with open(os.path.join(GOLDEN, "node_levels.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            n_s, L_s, lev_s = [p.strip() for p in line.split("|")]
+            H = O.Hierarchy((int(n_s),))
+            assert H.L == int(L_s)
+            assert O.node_levels(H).tolist() == [int(v) for v in lev_s.split()]
+
+
+# ------------------------------------------------ printed paper numbers ---
+
+def test_lemma1_interior_weights():
+    """Lemma 1 (Section 5.2): interior load-vector row of P^T M_f on a
+    uniform grid of spacing h is h (1/12, 1/2, 5/6, 1/2, 1/12)."""
+    h = 0.37
+    x = h * np.arange(17)
+    keep = O.coarse_indices(17)
+    R = (O.prolongation(x, keep).T @ O.mass_matrix(x)).toarray()
+    for k in range(1, len(keep) - 1):
+        row = R[k, 2 * k - 2: 2 * k + 3]
+        np.testing.assert_allclose(row, h * np.array([1 / 12, 1 / 2, 5 / 6, 1 / 2, 1 / 12]),
+                                   rtol=1e-14)
+        assert np.count_nonzero(np.abs(R[k]) > 1e-300) == 5
+
+
+def test_printed_coarse_mass_matrix():
+    """Section 5.4: coarse mass matrix on a level with fine spacing h has
+    2h/3 at the ends, 4h/3 inside and h/3 off the diagonal."""
+    h = 0.25
+    xc = 2 * h * np.arange(7)
+    M = O.mass_matrix(xc).toarray()
+    n = len(xc)
+    for i in range(n):
+        assert M[i, i] == pytest.approx((2 / 3 if i in (0, n - 1) else 4 / 3) * h, rel=1e-15)
+        if i + 1 < n:
+            assert M[i, i + 1] == pytest.approx(h / 3, rel=1e-15)
+            assert M[i + 1, i] == pytest.approx(h / 3, rel=1e-15)
+
+
+def test_interpolation_stencils():
+    """Eq. (multilinear_interp), Section 4.2: edge, plane and cube nodes take
+    1/2, 1/4 and 1/8 of the surrounding nodal values."""
+    H = O.Hierarchy((5, 5, 5))
+    c = _rng(1).standard_normal((3, 3, 3))
+    v = O.interpolate(c, H, 1)
+    u = {(2 * a, 2 * b, 2 * e): c[a, b, e] for a in range(2) for b in range(2) for e in range(2)}
+    assert v[0, 0, 1] == pytest.approx(0.5 * (u[0, 0, 0] + u[0, 0, 2]), abs=1e-15)
+    assert v[0, 1, 1] == pytest.approx(0.25 * (u[0, 0, 0] + u[0, 0, 2] + u[0, 2, 0] + u[0, 2, 2]),
+                                       abs=1e-15)
+    assert v[1, 1, 1] == pytest.approx(0.125 * sum(u.values()), abs=1e-15)
+    for key in np.ndindex(3, 3, 3):
+        assert v[tuple(2 * i for i in key)] == c[key]
+
+
+# ------------------------------------------- quadrature orthogonality ---
+
+def _gauss3():
+    return np.polynomial.legendre.leggauss(3)
+
+
+def _pl_eval_1d(xn, vals, xq):
+    return np.interp(xq, xn, vals)
+
+
+def test_projection_orthogonality_1d_quadrature():
+    """The L2 projection is the coarse function whose error is orthogonal to
+    every coarse hat function: integral (w_h - z_H) phi_k = 0.  Integrals by
+    3-point Gauss-Legendre per fine cell (exact for products of linears),
+    with functions evaluated by np.interp -- independent of the oracle's
+    matrices."""
+    rng = _rng(2)
+    for n in (5, 8, 13, 24):
+        x = np.sort(rng.uniform(0, 3, n))
+        x[0], x[-1] = 0.0, 3.0
+        w = rng.standard_normal(n)
+        H = O.Hierarchy((n,), [x])
+        z = O.project(w, H, H.L)
+        xc = H.coords[H.L - 1][0]
+        gx, gw = _gauss3()
+        resid = np.zeros(len(xc))
+        for a, b in zip(x[:-1], x[1:]):
+            xq = 0.5 * (b - a) * gx + 0.5 * (a + b)
+            wq = 0.5 * (b - a) * gw
+            err = _pl_eval_1d(x, w, xq) - _pl_eval_1d(xc, z, xq)
+            for k in range(len(xc)):
+                e = np.zeros(len(xc)); e[k] = 1.0
+                resid[k] += np.sum(wq * err * _pl_eval_1d(xc, e, xq))
+        assert np.abs(resid).max() < 1e-13 * max(1.0, np.abs(w).max())
+
+
+def test_projection_orthogonality_2d_quadrature():
+    """2D version with a tensor Gauss rule per fine cell and bilinear
+    evaluation by scipy's RegularGridInterpolator."""
+    rng = _rng(3)
+    dims = (6, 7)
+    xs = []
+    for n in dims:
+        x = np.sort(rng.uniform(0, 1, n)); x[0], x[-1] = 0.0, 1.0
+        xs.append(x)
+    w = rng.standard_normal(dims)
+    H = O.Hierarchy(dims, xs)
+    z = O.project(w, H, H.L)
+    xc = H.coords[H.L - 1]
+    fw = RegularGridInterpolator(xs, w)
+    fz = RegularGridInterpolator(xc, z)
+    gx, gw = _gauss3()
+    pts, wts = [], []
+    for a0, b0 in zip(xs[0][:-1], xs[0][1:]):
+        for a1, b1 in zip(xs[1][:-1], xs[1][1:]):
+            q0 = 0.5 * (b0 - a0) * gx + 0.5 * (a0 + b0)
+            q1 = 0.5 * (b1 - a1) * gx + 0.5 * (a1 + b1)
+            P0, P1 = np.meshgrid(q0, q1, indexing="ij")
+            W = np.outer(0.5 * (b0 - a0) * gw, 0.5 * (b1 - a1) * gw)
+            pts.append(np.stack([P0.ravel(), P1.ravel()], 1)); wts.append(W.ravel())
+    pts = np.concatenate(pts); wts = np.concatenate(wts)
+    pts = np.clip(pts, [xs[0][0], xs[1][0]], [xs[0][-1], xs[1][-1]])
+    err = fw(pts) - fz(pts)
+    for k0 in range(len(xc[0])):
+        for k1 in range(len(xc[1])):
+            e = np.zeros((len(xc[0]), len(xc[1]))); e[k0, k1] = 1
+            phi = RegularGridInterpolator(xc, e)(pts)
+            assert abs(np.sum(wts * err * phi)) < 1e-13
+
+
+def test_textbook_l2_projection_1d_continuous():
+    """d = 1 reduces to the textbook P1 L2 projection: projecting the
+    interpolant of a fine function and minimising the L2 error over coarse
+    coefficients by least squares on dense quadrature samples gives the same
+    coarse values (scipy lstsq on sampled hat functions)."""
+    rng = _rng(4)
+    n = 11
+    x = np.sort(rng.uniform(0, 1, n)); x[0], x[-1] = 0, 1
+    w = rng.standard_normal(n)
+    H = O.Hierarchy((n,), [x])
+    z = O.project(w, H, H.L)
+    xc = H.coords[H.L - 1][0]
+    gx, gw = _gauss3()
+    rows, rhs = [], []
+    for a, b in zip(x[:-1], x[1:]):
+        xq = 0.5 * (b - a) * gx + 0.5 * (a + b)
+        sw = np.sqrt(0.5 * (b - a) * gw)
+        basis = np.stack([_pl_eval_1d(xc, np.eye(len(xc))[k], xq) for k in range(len(xc))], 1)
+        rows.append(sw[:, None] * basis); rhs.append(sw * _pl_eval_1d(x, w, xq))
+    zz = np.linalg.lstsq(np.concatenate(rows), np.concatenate(rhs), rcond=None)[0]
+    np.testing.assert_allclose(z, zz, atol=1e-12)
+
+
+# ------------------------------------------------------ brute force -------
+
+def _kron_all(mats):
+    out = mats[0]
+    for m in mats[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+@pytest.mark.parametrize("dims,nonuni", [((9, 9), False), ((8, 6), True), ((5, 6, 7), True),
+                                         ((9, 5, 9), False), ((4, 4, 4), True)])
+def test_dense_kronecker_projection(dims, nonuni):
+    """Q_{l-1} w equals the dense Galerkin projection with the full
+    tensor-product matrices: (P^T M P)^{-1} P^T M w (numpy.linalg.solve)."""
+    rng = _rng(5)
+    coords = None
+    if nonuni:
+        coords = []
+        for n in dims:
+            x = np.cumsum(rng.uniform(0.2, 2.0, n)); coords.append(x)
+    H = O.Hierarchy(dims, coords)
+    w = rng.standard_normal(dims)
+    ops = H.ops(H.L)
+    M = _kron_all([o.Mf.toarray() for o in ops])
+    P = _kron_all([o.P.toarray() for o in ops])
+    z_dense = np.linalg.solve(P.T @ M @ P, P.T @ M @ w.ravel())
+    z = O.project(w, H, H.L)
+    np.testing.assert_allclose(z.ravel(), z_dense, atol=1e-12)
+
+
+def test_galerkin_coarse_mass():
+    """M_c assembled on the coarse coordinates equals P^T M_f P (nested P1
+    spaces)."""
+    rng = _rng(6)
+    for n in (5, 6, 9, 12):
+        x = np.cumsum(rng.uniform(0.1, 1.0, n))
+        keep = O.coarse_indices(n)
+        P = O.prolongation(x, keep)
+        G = (P.T @ O.mass_matrix(x) @ P).toarray()
+        np.testing.assert_allclose(O.mass_matrix(x[keep]).toarray(), G, atol=1e-14)
+
+
+# -------------------------------------------------------- invariants -----
+
+SHAPES = [(9,), (10,), (33,), (17, 17), (12, 9), (9, 9, 9), (10, 7, 12), (17, 9, 6)]
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("nonuni", [False, True])
+def test_identity(dims, nonuni):
+    """Recomposition inverts decomposition (Section 2) to 1e-12."""
+    rng = _rng(7)
+    coords = [F.geometric_coords(n, 1.03 + 0.02 * d) for d, n in enumerate(dims)] if nonuni else None
+    H = O.Hierarchy(dims, coords)
+    u = rng.standard_normal(dims)
+    for stop in sorted({0, H.L // 2, H.L}):
+        umc = O.decompose(u, H, stop)
+        r = O.recompose(umc, H, stop)
+        assert np.abs(r - u).max() <= 1e-12 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_multilinear_input_zero_coefficients(dims):
+    """Interpolation reproduces coarse-representable functions (Section 2),
+    so multilinear input has zero coefficients at every level and the coarse
+    block equals the input restricted to N_{l~}."""
+    coords = [F.geometric_coords(n, 1.05) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    u = F.multilinear_field(dims, coords)
+    for stop in (0, max(0, H.L - 1)):
+        umc = O.decompose(u, H, stop)
+        lev = O.node_levels(H, stop)
+        assert np.abs(umc[lev > stop]).max(initial=0) < 1e-13
+        np.testing.assert_allclose(umc[np.ix_(*H.index[stop])], u[np.ix_(*H.index[stop])],
+                                   atol=1e-13)
+
+
+def test_piecewise_multilinear_on_coarse_level():
+    """A function that is piecewise multilinear on N_k (built with scipy's
+    linear grid interpolator) has zero coefficients at every level above k."""
+    dims = (17, 12, 9)
+    coords = [F.geometric_coords(n, 1.04) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    k = H.L - 2
+    ck = _rng(8).standard_normal(H.levels[k])
+    fine = np.stack(np.meshgrid(*coords, indexing="ij"), -1)
+    u = RegularGridInterpolator(H.coords[k], ck)(fine.reshape(-1, 3)).reshape(dims)
+    umc = O.decompose(u, H, 0)
+    lev = O.node_levels(H)
+    assert np.abs(umc[lev > k]).max() < 1e-12
+    assert np.abs(umc[lev == k]).max() > 1e-3
+
+
+def test_paper_correction_identity():
+    """Section 2 step 4: the projection of the multilevel component equals
+    Q_{l-1}u - Pi_{l-1}Q_l u, i.e. Q_{l-1}u = u|_{N_{l-1}} + Q_{l-1}(mc)."""
+    dims = (13, 10, 9)
+    coords = [F.geometric_coords(n, 1.03) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    u = _rng(9).standard_normal(dims)
+    l = H.L
+    keep = [o.keep for o in H.ops(l)]
+    mc = u - O.interpolate(u[np.ix_(*keep)], H, l)
+    lhs = O.project(u, H, l)
+    rhs = u[np.ix_(*keep)] + O.project(mc, H, l)
+    assert np.abs(lhs - rhs).max() < 1e-13 * np.abs(u).max()
+
+
+def test_scale_shift_invariance():
+    dims = (9, 10, 7)
+    coords = [F.geometric_coords(n, 1.03) for n in dims]
+    u = _rng(10).standard_normal(dims)
+    a = O.decompose(u, O.Hierarchy(dims, coords))
+    b = O.decompose(u, O.Hierarchy(dims, [17.0 * x - 3.0 for x in coords]))
+    np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+# ---------------------------------------------------------- tolerances ----
+
+def _exact_A(n):
+    """A = M_c^{-1} P^T M_f for a uniform 1D grid, in exact rationals:
+    mass matrices from the hat-function integrals h/3, h/6, Gauss-Jordan
+    elimination in Fractions."""
+    h = Fraction(1)
+    Mf = [[Fraction(0)] * n for _ in range(n)]
+    for j in range(n - 1):
+        Mf[j][j] += h / 3; Mf[j + 1][j + 1] += h / 3
+        Mf[j][j + 1] += h / 6; Mf[j + 1][j] += h / 6
+    keep = list(range(0, n, 2)) + ([n - 1] if n % 2 == 0 else [])
+    nc = len(keep)
+    P = [[Fraction(0)] * nc for _ in range(n)]
+    for k, j in enumerate(keep):
+        P[j][k] = Fraction(1)
+    for k in range(nc - 1):
+        a, b = keep[k], keep[k + 1]
+        for j in range(a + 1, b):
+            P[j][k] = Fraction(b - j, b - a); P[j][k + 1] = Fraction(j - a, b - a)
+    R = [[sum(P[i][k] * Mf[i][j] for i in range(n)) for j in range(n)] for k in range(nc)]
+    Mc = [[sum(P[i][k] * sum(Mf[i][j] * P[j][m] for j in range(n)) for i in range(n))
+           for m in range(nc)] for k in range(nc)]
+    aug = [Mc[k][:] + R[k][:] for k in range(nc)]
+    for c in range(nc):
+        piv = aug[c][c]
+        aug[c] = [v / piv for v in aug[c]]
+        for r in range(nc):
+            if r != c and aug[r][c] != 0:
+                f = aug[r][c]
+                aug[r] = [vr - f * vc for vr, vc in zip(aug[r], aug[c])]
+    return [row[nc:] for row in aug], keep
+
+
+@pytest.mark.parametrize("n,expected", [(5, Fraction(7, 4)), (9, Fraction(13, 7))])
+def test_linf_constant_1d_exact(n, expected):
+    """In 1D the constant is 1 + max_k (sum_j |A_kj| - sum_{j coarse} |A_kj|)
+    (derivation in linf_constant); exact rational arithmetic for n = 5, 9."""
+    A, keep = _exact_A(n)
+    val = 1 + max(sum(abs(v) for v in row) - sum(abs(row[j]) for j in keep) for row in A)
+    assert val == expected
+    assert O.linf_constant(O.Hierarchy((n,))) == pytest.approx(float(expected), rel=1e-14)
+
+
+def test_linf_constant_uniform_limit():
+    """Large uniform grids: |A|_inf -> 1 + sqrt(3)/2 per axis (the rows of
+    M_c^{-1} decay with ratio 2 - sqrt(3)), so C -> (1 + sqrt(3)/2)^d."""
+    lim = 1 + np.sqrt(3) / 2
+    for d in (1, 2, 3):
+        C = O.linf_constant(O.Hierarchy((129,) * d))
+        assert C == pytest.approx(lim ** d, rel=1e-9)
+
+
+def test_linf_constant_is_an_upper_bound_1d():
+    """Worst case of one level: coefficient errors of +-1 with the signs of
+    the row of K (coefficients -> correction) that attains its max row sum
+    give a recomposition error of exactly that row sum at the coarse node;
+    C must not be smaller than 1 + that, nor than the largest error."""
+    n = 17
+    H = O.Hierarchy((n,))
+    l = H.L
+    A = O.projection_matrix(H.ops(l)[0])
+    keep = H.ops(l)[0].keep
+    coef = np.setdiff1d(np.arange(n), keep)
+    K = A[:, coef]
+    k = np.argmax(np.abs(K).sum(1))
+    e = np.zeros(n); e[coef] = np.sign(K[k])
+    umc = np.zeros(n)
+    umc[np.ix_(*H.index[l])] = e
+    err = O.recompose(umc, H, l - 1)
+    pos = H.index[l - 1][0][k]
+    assert abs(err[pos]) == pytest.approx(np.abs(K[k]).sum(), rel=1e-12)
+    C = O.linf_constant(H, l - 1)
+    assert C >= 1 + np.abs(K[k]).sum() - 1e-12
+    assert C >= np.abs(err).max()
+
+
+@pytest.mark.parametrize("dims,stop", [((65,), 0), ((33, 17), 1), ((17, 17, 17), 0), ((20, 17, 9), 2)])
+def test_tolerances_sum_and_ratio(dims, stop):
+    """Eq. (LinfTau) / Algorithm 1: tau_{l+1} = kappa tau_l with
+    kappa = sqrt(2^d), and sum_{l >= l~} tau_l = tau / C."""
+    H = O.Hierarchy(dims)
+    tau = 0.37
+    C = O.linf_constant(H, stop)
+    t = O.level_tolerances(H, stop, tau, C)
+    kappa = np.sqrt(2.0 ** len(dims))
+    np.testing.assert_allclose(t[stop + 1:] / t[stop:-1], kappa, rtol=1e-14)
+    assert t[stop:].sum() == pytest.approx(tau / C, rel=1e-13)
+
+
+def test_llround_ties_and_edges():
+    y = np.array([0.5, -0.5, 1.5, -1.5, 2.5, -2.5, 0.49999999999999994,
+                  -0.49999999999999994, 4503599627370495.5, 1e17, -3.0, 0.0])
+    exp = np.array([1, -1, 2, -2, 3, -3, 0, 0, 4503599627370496, 10 ** 17, -3, 0])
+    assert O.llround(y).tolist() == exp.tolist()
+
+
+@pytest.mark.parametrize("dims,stop,nonuni", [((65,), 0, False), ((33, 33), 0, True),
+                                               ((17, 19, 21), 0, False), ((17, 19, 21), 2, True)])
+@pytest.mark.parametrize("rel", [1e-2, 1e-4])
+def test_linf_guarantee(dims, stop, nonuni, rel):
+    """Eq. (LInfNormEstimator) with the level tolerances: quantize,
+    dequantize and recompose; the max error stays within tau, and each
+    coefficient is within its level tolerance."""
+    coords = [F.geometric_coords(n, 1.03) for n in dims] if nonuni else None
+    H = O.Hierarchy(dims, coords)
+    u = F.grf_field(dims, seed=11, dtype=np.float64)
+    tau = rel * O.value_range(u)
+    taus = O.level_tolerances(H, stop, tau)
+    umc = O.decompose(u, H, stop)
+    k = O.quantize(umc, H, stop, taus)
+    deq = O.dequantize(k, H, stop, taus)
+    lev = O.node_levels(H, stop)
+    assert np.all(np.abs(deq - umc) <= taus[lev] * (1 + 1e-12))
+    rec = O.recompose(deq, H, stop)
+    assert np.abs(rec - u).max() <= tau
+
+
+def test_worst_case_quantization_errors_within_bound():
+    """Adversarial coefficient errors: every coefficient off by +-tau_l with
+    random signs (the extreme of each bin), many trials; still within tau."""
+    dims = (17, 17)
+    H = O.Hierarchy(dims)
+    tau = 1.0
+    taus = O.level_tolerances(H, 0, tau)
+    lev = O.node_levels(H)
+    rng = _rng(12)
+    worst = 0.0
+    for _ in range(50):
+        e = taus[lev] * rng.choice([-1.0, 1.0], size=dims)
+        worst = max(worst, np.abs(O.recompose(e, H, 0)).max())
+    assert worst <= tau
