@@ -1,0 +1,153 @@
+/*
+ * mgard_gb.h -- C ABI of the GB300 (sm_103a) MGARD+ hot path: multilevel
+ * decomposition / recomposition of 1-3D tensor-product grids and level-wise
+ * quantization of the multilevel coefficients (Liang et al., arXiv
+ * 2010.05872).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Arrays are C order (the last axis is contiguous), dims[0] the slowest.
+ *    Every axis needs at least 3 nodes; 1 <= ndim <= 3; the last axis may
+ *    have up to 2^30 nodes, every other axis up to 2^18.
+ *  - `dims`, `coords`, `coords[i]` and every `*_out` pointer are HOST
+ *    pointers.  `data`, `coeffs`, `labels` and `workspace` are DEVICE
+ *    pointers owned by the caller; the library never frees them.
+ *  - `coords` may be NULL, and so may any `coords[i]`: that axis is then
+ *    uniform.  Results do not depend on the scale or origin of the
+ *    coordinates.  Given coordinates must be finite and strictly increasing.
+ *  - `dtype` is MGARD_F32 or MGARD_F64: the element type of `data`/`coeffs`
+ *    and the arithmetic type of the transform (level tolerances, bin widths
+ *    and quantization are always FP64).
+ *  - `stop_level` is the stopping level l~ of Algorithm 1 (0 <= l~ <= L):
+ *    levels L..l~+1 are decomposed and the nodes of N_{l~} keep Q_{l~}u.
+ *    0 is the full depth; L leaves the data unchanged.
+ *  - The grid hierarchy (Section 2): every axis is coarsened at every level by
+ *    keeping its even nodes, plus its last node when its length is even
+ *    (n -> n/2 + 1); L is the number of steps until the shortest axis has 3
+ *    nodes.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it and the calls return without waiting, except
+ *    mgard_quantize and mgard_value_range, which wait for their own flags.
+ *  - The first call for a given (device, dims, coords, dtype) builds a plan
+ *    (host FP64 tables, uploaded once with cudaMalloc/cudaMemcpy) and caches
+ *    it until mgard_release_plans().  Make that first call outside any CUDA
+ *    stream capture.
+ *  - Return value: MGARD_OK (0) or one of the negative MGARD_ERR_* codes;
+ *    mgard_error_string() names it.  Argument errors are detected before
+ *    any work is enqueued.
+ */
+#ifndef MGARD_GB_H
+#define MGARD_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { MGARD_F32 = 0, MGARD_F64 = 1 };
+
+enum {
+  MGARD_OK = 0,
+  MGARD_ERR_ARG = -1,       /* NULL or misaligned pointer, bad dtype/ndim, tau <= 0 */
+  MGARD_ERR_SHAPE = -2,     /* ndim outside 1..3, or an axis with fewer than 3 nodes */
+  MGARD_ERR_COORDS = -3,    /* coordinates not finite or not strictly increasing */
+  MGARD_ERR_LEVEL = -4,     /* stop_level outside [0, L] */
+  MGARD_ERR_WORKSPACE = -5, /* workspace NULL, misaligned or smaller than required */
+  MGARD_ERR_OVERFLOW = -6,  /* a label would reach 2^62 in magnitude */
+  MGARD_ERR_NONFINITE = -7, /* NaN or Inf in the input of quantize / value_range */
+  MGARD_ERR_CUDA = -8,      /* a CUDA runtime call or kernel launch failed */
+  MGARD_ERR_TIMEOUT = -9    /* a bounded device-side wait gave up */
+};
+
+/* Number of decomposition levels L of the hierarchy of `dims`. */
+int mgard_num_levels(int ndim, const int64_t* dims, int* L_out);
+
+/* Device workspace (bytes) that mgard_decompose / mgard_recompose need for
+ * `dims` and `dtype`: the compact level-l grids and load vectors of every
+ * coarser level (about 2/7 of the field for 3D).  The workspace must be
+ * 256-byte aligned; its contents on entry do not matter. */
+int mgard_workspace_size(int ndim, const int64_t* dims, int dtype, size_t* bytes);
+
+/* Level tolerances tau_l, l = 0..L (host array of L+1 doubles; entries below
+ * stop_level repeat tau_{l~}).  Eq. (LinfTau) of Section 4.1 with the
+ * stopping level of Algorithm 1 (lines 17-20):
+ *   tau_{l~} = (1 - k) tau_linf / ((1 - k^(L+1-l~)) C_Linf),
+ *   tau_l = k tau_{l-1},  k = sqrt(2^ndim),
+ * and C_Linf = 1 + max over decomposed levels of an upper bound of the
+ * coefficient-to-correction max norm, computed from the coordinates (the
+ * paper does not print the constant; the bound keeps the guarantee
+ * |u - u~|_inf <= tau_linf of Eq. (LInfNormEstimator)).  tau_linf is
+ * absolute and must be > 0. */
+int mgard_level_tolerances(int ndim, const int64_t* dims, const double* const* coords,
+                           int stop_level, double tau_linf, double* tau_out);
+
+/* Multilevel decomposition, in place (Section 2, decomposition steps 1-6).
+ * On return `data` holds u_mc indexed by the finest grid: at a node of
+ * N*_l (l > l~) the coefficient (I - Pi_{l-1}) Q_l u, at a node of N_{l~}
+ * the value of Q_{l~} u.  Per level: coefficient computation, load vector
+ * (mass multiply + restriction, Lemma 1 generalised to any coordinates),
+ * batched tridiagonal mass-matrix solves along every axis (Section 5.3-5.4),
+ * correction application.  `workspace` needs mgard_workspace_size() bytes;
+ * `ws_bytes` is its size. */
+int mgard_decompose(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                    int stop_level, void* data, void* workspace, size_t ws_bytes,
+                    void* stream);
+
+/* Multilevel recomposition, in place: the exact inverse of mgard_decompose
+ * with the same dims, coords, dtype and stop_level (Section 2, recomposition
+ * steps 1-5).  Same workspace rule. */
+int mgard_recompose(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                    int stop_level, void* data, void* workspace, size_t ws_bytes,
+                    void* stream);
+
+/* Level-wise quantization (Section 4.1; Algorithm 1 lines 17-22).  For
+ * every node x of the finest grid, with l the least level such that x is in
+ * N_l, raised to stop_level: labels[x] = round(coeffs[x] / (2 tau_l)) with
+ * ties away from zero, in FP64 (IEEE division).  `coeffs` (dtype) and
+ * `labels` (int64, same element count) are device arrays.  If
+ * `tau_levels_out` is not NULL it receives tau_0..tau_L (host, L+1
+ * doubles).  Waits for the stream and returns MGARD_ERR_NONFINITE /
+ * MGARD_ERR_OVERFLOW if any coefficient was not finite or any label would
+ * reach 2^62 in magnitude (the labels are then incomplete). */
+int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                   int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
+                   double* tau_levels_out, void* stream);
+
+/* Bin centres: coeffs[x] = labels[x] * (2 tau_l), computed in FP64 and
+ * rounded to dtype (Section 4.1).  Arguments as for mgard_quantize. */
+int mgard_dequantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                     int stop_level, double tau_linf, const int64_t* labels, void* coeffs,
+                     void* stream);
+
+/* min and max of a device array of `count` elements of dtype, as doubles in
+ * minmax_out[0], minmax_out[1] (host).  The value range max - min scales a
+ * relative error bound into the absolute tau of the other calls.  Waits for
+ * the stream; MGARD_ERR_NONFINITE if an element is NaN or Inf. */
+int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax_out,
+                      void* stream);
+
+/* Host-buffer forms of decompose / recompose: copy `host_in` (pinned or
+ * pageable host memory, the field's element count of dtype) to the device
+ * buffer `dev_data`, transform it there in place, and copy the result to
+ * `host_out` (may equal host_in).  The stream is synchronised before
+ * returning.  Other arguments as for mgard_decompose. */
+int mgard_decompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, const void* host_in, void* host_out, void* dev_data,
+                         void* workspace, size_t ws_bytes, void* stream);
+int mgard_recompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, const void* host_in, void* host_out, void* dev_data,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/* Free every cached plan (device tables included) of the current device. */
+int mgard_release_plans(void);
+
+/* Static description of an error code. */
+const char* mgard_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGARD_GB_H */

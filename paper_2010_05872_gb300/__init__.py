@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) MGARD+ hot path: multilevel decomposition and
+recomposition of 1-3D tensor-product grids and level-wise quantization
+(Liang et al., arXiv 2010.05872).
+
+The compute lives in ``libmgardgb.so`` (CUDA, C ABI in include/mgard_gb.h);
+``binding`` marshals arguments to it.  Importing the package does not load
+the library; the first call does, and fails loudly when it is missing.
+"""
+from .binding import (  # noqa: F401
+    F32, F64, MgardError, decompose, recompose, quantize, dequantize, value_range,
+    workspace, mgard_num_levels, mgard_workspace_size, mgard_level_tolerances,
+)

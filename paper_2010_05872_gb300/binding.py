@@ -1,0 +1,277 @@
+"""ctypes binding of ``libmgardgb.so`` (the C ABI in ``include/mgard_gb.h``).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library.  The ``mgard_*`` functions mirror the C entry points one to one
+(plain integers for device pointers and streams); the short helpers below
+them take CUDA torch tensors and the current torch stream.  There is no CPU
+path: a missing library, a CPU tensor or a non-zero return code raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmgardgb.so")
+
+F32, F64 = 0, 1
+OK = 0
+ERRORS = {
+    -1: "MGARD_ERR_ARG", -2: "MGARD_ERR_SHAPE", -3: "MGARD_ERR_COORDS", -4: "MGARD_ERR_LEVEL",
+    -5: "MGARD_ERR_WORKSPACE", -6: "MGARD_ERR_OVERFLOW", -7: "MGARD_ERR_NONFINITE",
+    -8: "MGARD_ERR_CUDA", -9: "MGARD_ERR_TIMEOUT",
+}
+
+# Every symbol the header declares, with its ctypes signature.
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_DPP = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "mgard_num_levels": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(ctypes.c_int)]),
+    "mgard_workspace_size": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_size_t)]),
+    "mgard_level_tolerances": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
+                                              ctypes.c_double, _DP]),
+    "mgard_decompose": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                       _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_recompose": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                       _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_quantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, _VP, _VP, _DP, _VP]),
+    "mgard_dequantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, _VP, _VP, _VP]),
+    "mgard_value_range": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _VP, _DP, _VP]),
+    "mgard_decompose_host": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                            _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_recompose_host": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                            _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_release_plans": (ctypes.c_int, []),
+    "mgard_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+class MgardError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        name = ERRORS.get(code, str(code))
+        msg = _lib.mgard_error_string(code).decode() if _lib is not None else name
+        super().__init__(f"{what}: {name} ({msg})" if what else f"{name} ({msg})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+# ------------------------------------------------------------ marshalling ---
+
+class _Shape:
+    """dims / coords as C arrays, kept alive for the duration of a call."""
+
+    def __init__(self, dims, coords=None):
+        dims = [int(n) for n in dims]
+        self.ndim = len(dims)
+        self.dims = (ctypes.c_int64 * self.ndim)(*dims)
+        if coords is None:
+            self.coords = None
+            self._keep = []
+        else:
+            if len(coords) != self.ndim:
+                raise ValueError("one coordinate array (or None) per axis")
+            self._keep = [None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+                          for c in coords]
+            arr = (ctypes.POINTER(ctypes.c_double) * self.ndim)()
+            for d, c in enumerate(self._keep):
+                arr[d] = (ctypes.cast(c.ctypes.data, ctypes.POINTER(ctypes.c_double))
+                          if c is not None else ctypes.POINTER(ctypes.c_double)())
+            self.coords = ctypes.cast(arr, _DPP)
+            self._arr = arr
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise MgardError(rc, what)
+
+
+def mgard_num_levels(dims) -> int:
+    s = _Shape(dims)
+    L = ctypes.c_int()
+    _check(lib().mgard_num_levels(s.ndim, s.dims, ctypes.byref(L)), "mgard_num_levels")
+    return L.value
+
+
+def mgard_workspace_size(dims, dtype: int) -> int:
+    s = _Shape(dims)
+    b = ctypes.c_size_t()
+    _check(lib().mgard_workspace_size(s.ndim, s.dims, dtype, ctypes.byref(b)), "mgard_workspace_size")
+    return b.value
+
+
+def mgard_level_tolerances(dims, coords, stop_level: int, tau: float) -> np.ndarray:
+    s = _Shape(dims, coords)
+    out = np.zeros(mgard_num_levels(dims) + 1)
+    _check(lib().mgard_level_tolerances(s.ndim, s.dims, s.coords, stop_level, float(tau),
+                                        out.ctypes.data_as(_DP)), "mgard_level_tolerances")
+    return out
+
+
+def mgard_decompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_decompose(s.ndim, s.dims, s.coords, dtype, stop_level, data_ptr, ws_ptr,
+                                 ws_bytes, stream)
+
+
+def mgard_recompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_recompose(s.ndim, s.dims, s.coords, dtype, stop_level, data_ptr, ws_ptr,
+                                 ws_bytes, stream)
+
+
+def mgard_decompose_host(dims, coords, dtype, stop_level, host_in, host_out, dev_ptr, ws_ptr,
+                         ws_bytes, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_decompose_host(s.ndim, s.dims, s.coords, dtype, stop_level, host_in,
+                                      host_out, dev_ptr, ws_ptr, ws_bytes, stream)
+
+
+def mgard_recompose_host(dims, coords, dtype, stop_level, host_in, host_out, dev_ptr, ws_ptr,
+                         ws_bytes, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_recompose_host(s.ndim, s.dims, s.coords, dtype, stop_level, host_in,
+                                      host_out, dev_ptr, ws_ptr, ws_bytes, stream)
+
+
+def mgard_quantize(dims, coords, dtype, stop_level, tau, coeffs_ptr, labels_ptr, stream):
+    s = _Shape(dims, coords)
+    taus = np.zeros(mgard_num_levels(dims) + 1)
+    rc = lib().mgard_quantize(s.ndim, s.dims, s.coords, dtype, stop_level, float(tau), coeffs_ptr,
+                              labels_ptr, taus.ctypes.data_as(_DP), stream)
+    return rc, taus
+
+
+def mgard_dequantize(dims, coords, dtype, stop_level, tau, labels_ptr, coeffs_ptr, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_dequantize(s.ndim, s.dims, s.coords, dtype, stop_level, float(tau),
+                                  labels_ptr, coeffs_ptr, stream)
+
+
+def mgard_value_range(count, dtype, data_ptr, stream):
+    out = np.zeros(2)
+    rc = lib().mgard_value_range(int(count), dtype, data_ptr, out.ctypes.data_as(_DP), stream)
+    return rc, out
+
+
+def mgard_release_plans() -> int:
+    return lib().mgard_release_plans()
+
+
+# ------------------------------------------------------- torch helpers ---
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype}: float32 or float64")
+
+
+def _cuda_tensor(t, what="tensor"):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (there is no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous (C order)")
+    return t
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def workspace(shape, dtype, device=None):
+    """A device workspace tensor of the size mgard_decompose needs."""
+    torch = _torch()
+    code = dtype if isinstance(dtype, int) else dtype_code(torch.empty(0, dtype=dtype))
+    nbytes = mgard_workspace_size(shape, code)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def decompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
+    """In-place multilevel decomposition of a CUDA tensor (returns it)."""
+    _cuda_tensor(x, "x")
+    if ws is None:
+        ws = workspace(x.shape, x.dtype, x.device)
+    rc = mgard_decompose(x.shape, coords, dtype_code(x), stop_level, x.data_ptr(), ws.data_ptr(),
+                         ws.numel(), _stream(stream))
+    _check(rc, "mgard_decompose")
+    return x
+
+
+def recompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
+    """In-place multilevel recomposition of a CUDA tensor (returns it)."""
+    _cuda_tensor(x, "x")
+    if ws is None:
+        ws = workspace(x.shape, x.dtype, x.device)
+    rc = mgard_recompose(x.shape, coords, dtype_code(x), stop_level, x.data_ptr(), ws.data_ptr(),
+                         ws.numel(), _stream(stream))
+    _check(rc, "mgard_recompose")
+    return x
+
+
+def quantize(coeffs, tau: float, coords=None, stop_level: int = 0, labels=None, stream=None):
+    """Level-wise labels (int64 CUDA tensor) and the tolerances tau_0..tau_L."""
+    torch = _torch()
+    _cuda_tensor(coeffs, "coeffs")
+    if labels is None:
+        labels = torch.empty(coeffs.shape, dtype=torch.int64, device=coeffs.device)
+    rc, taus = mgard_quantize(coeffs.shape, coords, dtype_code(coeffs), stop_level, tau,
+                              coeffs.data_ptr(), labels.data_ptr(), _stream(stream))
+    _check(rc, "mgard_quantize")
+    return labels, taus
+
+
+def dequantize(labels, tau: float, dtype, coords=None, stop_level: int = 0, out=None, stream=None):
+    torch = _torch()
+    _cuda_tensor(labels, "labels")
+    if out is None:
+        out = torch.empty(labels.shape, dtype=dtype, device=labels.device)
+    rc = mgard_dequantize(labels.shape, coords, dtype_code(out), stop_level, tau,
+                          labels.data_ptr(), out.data_ptr(), _stream(stream))
+    _check(rc, "mgard_dequantize")
+    return out
+
+
+def value_range(x, stream=None):
+    """(min, max) of a CUDA tensor, computed on the device."""
+    _cuda_tensor(x, "x")
+    rc, out = mgard_value_range(x.numel(), dtype_code(x), x.data_ptr(), _stream(stream))
+    _check(rc, "mgard_value_range")
+    return float(out[0]), float(out[1])

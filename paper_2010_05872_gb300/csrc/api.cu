@@ -1,0 +1,481 @@
+// extern "C" entry points declared in include/mgard_gb.h: argument checks,
+// the per-device plan cache (host tables uploaded once), the workspace
+// layout and the level loops of decomposition / recomposition (Section 2).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "mgard_gb.h"
+#include "plan.hpp"
+
+namespace mgb {
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Plan tables resident on one device in the element type of the transform.
+struct DevPlan {
+  HostPlan h;
+  int dtype = MGARD_F32;
+  int device = 0;
+  void* dmem = nullptr;
+  std::vector<LevelK<float>> lvf;   // [L+1], entry l = transition l -> l-1
+  std::vector<LevelK<double>> lvd;
+  const uint8_t* lev[3] = {nullptr, nullptr, nullptr};
+  std::vector<size_t> offB, offF;   // workspace offsets of the level-l grids / load vectors
+  size_t ws_bytes = 0;
+  ~DevPlan() {
+    if (dmem) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(device);
+      cudaFree(dmem);
+      cudaSetDevice(cur);
+    }
+  }
+};
+
+// Small per-device scratch for flags and reductions (allocated once).
+struct DevCtx {
+  unsigned int* flags = nullptr;  // [4]
+  double* partial = nullptr;      // [2 * kMinmaxBlocks]
+  double* result = nullptr;       // [2]
+  unsigned int* h_flags = nullptr;  // pinned host mirrors
+  double* h_result = nullptr;
+  std::mutex mu;                  // serialises the calls that wait on these flags
+};
+
+std::mutex g_mu;
+std::map<std::string, std::unique_ptr<DevPlan>> g_plans;
+std::map<int, std::unique_ptr<DevCtx>> g_ctx;
+
+template <typename T>
+void fill_levels(DevPlan& p, const std::vector<std::vector<size_t>>& offs, char* base,
+                 std::vector<LevelK<T>>& out) {
+  out.assign(p.h.L + 1, LevelK<T>{});
+  for (int l = 1; l <= p.h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const AxisTables& t = p.h.ax[l][a];
+      const size_t* o = offs[l * 3 + a].data();
+      AxisK<T>& k = out[l].ax[a];
+      k.iwl = reinterpret_cast<const T*>(base + o[0]);
+      k.iwr = reinterpret_cast<const T*>(base + o[1]);
+      k.rw = reinterpret_cast<const T*>(base + o[2]);
+      k.ta = reinterpret_cast<const T*>(base + o[3]);
+      k.tm = reinterpret_cast<const T*>(base + o[4]);
+      k.tc = reinterpret_cast<const T*>(base + o[5]);
+      k.n = t.n;
+      k.nc = t.nc;
+    }
+}
+
+template <typename T>
+int upload(DevPlan& p) {
+  const HostPlan& h = p.h;
+  std::vector<std::vector<size_t>> offs((h.L + 1) * 3);
+  size_t total = 0;
+  auto reserve = [&](size_t bytes) { const size_t o = total; total = align_up(total + bytes, 16); return o; };
+  for (int l = 1; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const AxisTables& t = h.ax[l][a];
+      auto& o = offs[l * 3 + a];
+      o.push_back(reserve(sizeof(T) * t.iwl.size()));
+      o.push_back(reserve(sizeof(T) * t.iwr.size()));
+      o.push_back(reserve(sizeof(T) * t.rw.size()));
+      o.push_back(reserve(sizeof(T) * t.ta.size()));
+      o.push_back(reserve(sizeof(T) * t.tm.size()));
+      o.push_back(reserve(sizeof(T) * t.tc.size()));
+    }
+  size_t lev_off[3];
+  for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
+  std::vector<char> stage(total, 0);
+  auto put = [&](size_t off, const std::vector<double>& v) {
+    T* dst = reinterpret_cast<T*>(stage.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) dst[i] = static_cast<T>(v[i]);
+  };
+  for (int l = 1; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const AxisTables& t = h.ax[l][a];
+      const auto& o = offs[l * 3 + a];
+      put(o[0], t.iwl); put(o[1], t.iwr); put(o[2], t.rw);
+      put(o[3], t.ta); put(o[4], t.tm); put(o[5], t.tc);
+    }
+  for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
+  if (cudaMalloc(&p.dmem, total) != cudaSuccess) return MGARD_ERR_CUDA;
+  if (cudaMemcpy(p.dmem, stage.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) return MGARD_ERR_CUDA;
+  char* base = static_cast<char*>(p.dmem);
+  if constexpr (sizeof(T) == 4) fill_levels<float>(p, offs, base, p.lvf);
+  else fill_levels<double>(p, offs, base, p.lvd);
+  for (int a = 0; a < 3; ++a) p.lev[a] = reinterpret_cast<const uint8_t*>(base + lev_off[a]);
+  return MGARD_OK;
+}
+
+size_t elem_size(int dtype) { return dtype == MGARD_F64 ? 8 : 4; }
+
+void layout_workspace(DevPlan& p) {
+  const size_t es = elem_size(p.dtype);
+  p.offB.assign(p.h.L + 1, 0);
+  p.offF.assign(p.h.L + 1, 0);
+  size_t off = 0;
+  for (int l = p.h.L - 1; l >= 0; --l) {
+    const size_t cnt = static_cast<size_t>(p.h.shape[l][0] * p.h.shape[l][1] * p.h.shape[l][2]);
+    p.offB[l] = off; off = align_up(off + cnt * es, kAlign);
+    p.offF[l] = off; off = align_up(off + cnt * es, kAlign);
+  }
+  p.ws_bytes = off;
+}
+
+std::string plan_key(int device, int dtype, const HostPlan& h) {
+  std::string k;
+  auto app = [&](const void* d, size_t n) { k.append(static_cast<const char*>(d), n); };
+  app(&device, sizeof device);
+  app(&dtype, sizeof dtype);
+  app(&h.ndim, sizeof h.ndim);
+  app(h.dims3.data(), sizeof(int64_t) * 3);
+  app(h.coords_key.data(), sizeof(double) * h.coords_key.size());
+  return k;
+}
+
+// Look up (or build and upload) the plan of this shape/coords/dtype on the
+// current device.
+int get_plan(int ndim, const int64_t* dims, const double* const* coords, int dtype, DevPlan** out) {
+  if (dtype != MGARD_F32 && dtype != MGARD_F64) return MGARD_ERR_ARG;
+  int rc = check_shape(ndim, dims);
+  if (rc != MGARD_OK) return rc;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return MGARD_ERR_CUDA;
+  // Cheap key first: coordinates are validated by the full build.
+  HostPlan probe;
+  probe.ndim = ndim;
+  const int pad = 3 - ndim;
+  for (int d = 0; d < ndim; ++d) probe.dims3[pad + d] = dims[d];
+  for (int d = 0; d < ndim; ++d) {
+    const double* c = coords ? coords[d] : nullptr;
+    if (c) probe.coords_key.insert(probe.coords_key.end(), c, c + dims[d]);
+    probe.coords_key.push_back(c ? 1.0 : 0.0);
+  }
+  const std::string key = plan_key(device, dtype, probe);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) { *out = it->second.get(); return MGARD_OK; }
+  auto p = std::make_unique<DevPlan>();
+  rc = build_host_plan(ndim, dims, coords, p->h);
+  if (rc != MGARD_OK) return rc;
+  p->dtype = dtype;
+  p->device = device;
+  rc = (dtype == MGARD_F64) ? upload<double>(*p) : upload<float>(*p);
+  if (rc != MGARD_OK) return rc;
+  layout_workspace(*p);
+  *out = p.get();
+  g_plans.emplace(key, std::move(p));
+  return MGARD_OK;
+}
+
+DevCtx* get_ctx() {
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ctx.find(device);
+  if (it != g_ctx.end()) return it->second.get();
+  auto c = std::make_unique<DevCtx>();
+  if (cudaMalloc(&c->flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&c->partial, 2 * kMinmaxBlocks * sizeof(double)) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&c->result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
+  if (cudaMallocHost(&c->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
+  if (cudaMallocHost(&c->h_result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
+  DevCtx* raw = c.get();
+  g_ctx.emplace(device, std::move(c));
+  return raw;
+}
+
+inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MGARD_OK : MGARD_ERR_CUDA; }
+#define MGB_TRY(expr) do { const cudaError_t e_ = (expr); if (e_ != cudaSuccess) return MGARD_ERR_CUDA; } while (0)
+
+int check_transform_args(const DevPlan& p, int stop_level, const void* data, const void* ws,
+                         size_t ws_bytes) {
+  if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
+  if (data == nullptr || reinterpret_cast<uintptr_t>(data) % elem_size(p.dtype) != 0) return MGARD_ERR_ARG;
+  if (p.h.L > stop_level) {
+    if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % kAlign != 0) return MGARD_ERR_WORKSPACE;
+    if (ws_bytes < p.ws_bytes) return MGARD_ERR_WORKSPACE;
+  }
+  return MGARD_OK;
+}
+
+template <typename T>
+const std::vector<LevelK<T>>& levels(const DevPlan& p);
+template <>
+const std::vector<LevelK<float>>& levels<float>(const DevPlan& p) { return p.lvf; }
+template <>
+const std::vector<LevelK<double>>& levels<double>(const DevPlan& p) { return p.lvd; }
+
+// Decomposition, levels L .. l~+1: load vector (reads the level-l grid only),
+// solves with the correction applied to the gathered coarse values; then,
+// coarsest first, the finishing pass writes each level's coefficients and the
+// final coarser values into the level-l grid.
+template <typename T>
+int run_decompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s) {
+  const int L = p.h.L;
+  const auto& lv = levels<T>(p);
+  std::vector<T*> B(L + 1), F(L + 1);
+  B[L] = data;
+  for (int l = 0; l < L; ++l) {
+    B[l] = reinterpret_cast<T*>(ws + p.offB[l]);
+    F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
+  }
+  for (int l = L; l > stop; --l) {
+    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, s));
+  }
+  for (int l = stop + 1; l <= L; ++l)
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], s));
+  return MGARD_OK;
+}
+
+// Recomposition: gather every level's coarse part and load vector top-down,
+// then bottom-up solve, subtract the correction and interpolate.
+template <typename T>
+int run_recompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s) {
+  const int L = p.h.L;
+  const auto& lv = levels<T>(p);
+  std::vector<T*> B(L + 1), F(L + 1);
+  B[L] = data;
+  for (int l = 0; l < L; ++l) {
+    B[l] = reinterpret_cast<T*>(ws + p.offB[l]);
+    F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
+  }
+  for (int l = L; l > stop; --l)
+    MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], s));
+  for (int l = stop + 1; l <= L; ++l) {
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, s));
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], s));
+  }
+  return MGARD_OK;
+}
+
+int transform(bool dec, int ndim, const int64_t* dims, const double* const* coords, int dtype,
+              int stop_level, void* data, void* workspace, size_t ws_bytes, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*p, stop_level, data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  if (stop_level == p->h.L) return MGARD_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  if (dtype == MGARD_F64)
+    return dec ? run_decompose<double>(*p, stop_level, static_cast<double*>(data), ws, s)
+               : run_recompose<double>(*p, stop_level, static_cast<double*>(data), ws, s);
+  return dec ? run_decompose<float>(*p, stop_level, static_cast<float*>(data), ws, s)
+             : run_recompose<float>(*p, stop_level, static_cast<float*>(data), ws, s);
+}
+
+int transform_host(bool dec, int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                   int stop_level, const void* host_in, void* host_out, void* dev_data,
+                   void* workspace, size_t ws_bytes, void* stream) {
+  if (host_in == nullptr || host_out == nullptr) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*p, stop_level, dev_data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = static_cast<size_t>(p->h.count()) * elem_size(dtype);
+  MGB_TRY(cudaMemcpyAsync(dev_data, host_in, bytes, cudaMemcpyHostToDevice, s));
+  rc = transform(dec, ndim, dims, coords, dtype, stop_level, dev_data, workspace, ws_bytes, stream);
+  if (rc != MGARD_OK) return rc;
+  MGB_TRY(cudaMemcpyAsync(host_out, dev_data, bytes, cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  return MGARD_OK;
+}
+
+int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, double* tau_out) {
+  if (!(tau > 0.0) || !std::isfinite(tau)) return MGARD_ERR_ARG;
+  if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
+  double t[kMaxLevels];
+  level_tolerances(p.h, stop_level, tau, t);
+  for (int l = 0; l < 48; ++l) tab.q[l] = 0.0;
+  for (int l = 0; l <= p.h.L; ++l) tab.q[l] = 2.0 * t[l];
+  if (tau_out)
+    for (int l = 0; l <= p.h.L; ++l) tau_out[l] = t[l];
+  return MGARD_OK;
+}
+
+}  // namespace
+}  // namespace mgb
+
+using namespace mgb;
+
+extern "C" {
+
+int mgard_num_levels(int ndim, const int64_t* dims, int* L_out) {
+  if (L_out == nullptr) return MGARD_ERR_ARG;
+  return count_levels(ndim, dims, L_out);
+}
+
+int mgard_workspace_size(int ndim, const int64_t* dims, int dtype, size_t* bytes) {
+  if (bytes == nullptr) return MGARD_ERR_ARG;
+  if (dtype != MGARD_F32 && dtype != MGARD_F64) return MGARD_ERR_ARG;
+  int L = 0;
+  int rc = count_levels(ndim, dims, &L);
+  if (rc != MGARD_OK) return rc;
+  int64_t cur[3] = {1, 1, 1};
+  const int pad = 3 - ndim;
+  for (int d = 0; d < ndim; ++d) cur[pad + d] = dims[d];
+  size_t off = 0;
+  const size_t es = elem_size(dtype);
+  for (int l = L - 1; l >= 0; --l) {
+    for (int a = pad; a < 3; ++a) cur[a] = cur[a] / 2 + 1;
+    const size_t cnt = static_cast<size_t>(cur[0] * cur[1] * cur[2]);
+    off = align_up(off + cnt * es, kAlign);
+    off = align_up(off + cnt * es, kAlign);
+  }
+  *bytes = off;
+  return MGARD_OK;
+}
+
+int mgard_level_tolerances(int ndim, const int64_t* dims, const double* const* coords,
+                           int stop_level, double tau_linf, double* tau_out) {
+  if (tau_out == nullptr) return MGARD_ERR_ARG;
+  if (!(tau_linf > 0.0) || !std::isfinite(tau_linf)) return MGARD_ERR_ARG;
+  HostPlan h;
+  int rc = build_host_plan(ndim, dims, coords, h);
+  if (rc != MGARD_OK) return rc;
+  if (stop_level < 0 || stop_level > h.L) return MGARD_ERR_LEVEL;
+  level_tolerances(h, stop_level, tau_linf, tau_out);
+  return MGARD_OK;
+}
+
+int mgard_decompose(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                    int stop_level, void* data, void* workspace, size_t ws_bytes, void* stream) {
+  return transform(true, ndim, dims, coords, dtype, stop_level, data, workspace, ws_bytes, stream);
+}
+
+int mgard_recompose(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                    int stop_level, void* data, void* workspace, size_t ws_bytes, void* stream) {
+  return transform(false, ndim, dims, coords, dtype, stop_level, data, workspace, ws_bytes, stream);
+}
+
+int mgard_decompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, const void* host_in, void* host_out, void* dev_data,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  return transform_host(true, ndim, dims, coords, dtype, stop_level, host_in, host_out, dev_data,
+                        workspace, ws_bytes, stream);
+}
+
+int mgard_recompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, const void* host_in, void* host_out, void* dev_data,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  return transform_host(false, ndim, dims, coords, dtype, stop_level, host_in, host_out, dev_data,
+                        workspace, ws_bytes, stream);
+}
+
+int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                   int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
+                   double* tau_levels_out, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  if (coeffs == nullptr || labels == nullptr) return MGARD_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(coeffs) % elem_size(dtype) || reinterpret_cast<uintptr_t>(labels) % 8)
+    return MGARD_ERR_ARG;
+  LevelTable tab;
+  rc = make_table(*p, stop_level, tau_linf, tab, tau_levels_out);
+  if (rc != MGARD_OK) return rc;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MGB_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s));
+  const auto& d = p->h.dims3;
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p->lev[0], p->lev[1],
+                                    p->lev[2], d[0], d[1], d[2], stop_level, tab, c->flags, s));
+  else
+    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p->lev[0], p->lev[1],
+                                   p->lev[2], d[0], d[1], d[2], stop_level, tab, c->flags, s));
+  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  const unsigned f = c->h_flags[0];
+  if (f & 1u) return MGARD_ERR_NONFINITE;
+  if (f & 2u) return MGARD_ERR_OVERFLOW;
+  return MGARD_OK;
+}
+
+int mgard_dequantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                     int stop_level, double tau_linf, const int64_t* labels, void* coeffs,
+                     void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  if (coeffs == nullptr || labels == nullptr) return MGARD_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(coeffs) % elem_size(dtype) || reinterpret_cast<uintptr_t>(labels) % 8)
+    return MGARD_ERR_ARG;
+  LevelTable tab;
+  rc = make_table(*p, stop_level, tau_linf, tab, nullptr);
+  if (rc != MGARD_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto& d = p->h.dims3;
+  if (dtype == MGARD_F64)
+    return cuda_rc(launch_dequantize<double>(labels, static_cast<double*>(coeffs), p->lev[0],
+                                             p->lev[1], p->lev[2], d[0], d[1], d[2], stop_level, tab, s));
+  return cuda_rc(launch_dequantize<float>(labels, static_cast<float*>(coeffs), p->lev[0], p->lev[1],
+                                          p->lev[2], d[0], d[1], d[2], stop_level, tab, s));
+}
+
+int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax_out, void* stream) {
+  if (count < 1 || data == nullptr || minmax_out == nullptr) return MGARD_ERR_ARG;
+  if (dtype != MGARD_F32 && dtype != MGARD_F64) return MGARD_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(data) % elem_size(dtype)) return MGARD_ERR_ARG;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MGB_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s));
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_minmax<double>(static_cast<const double*>(data), count, c->partial, c->flags, c->result, s));
+  else
+    MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, c->partial, c->flags, c->result, s));
+  MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  if (c->h_flags[0] & 1u) return MGARD_ERR_NONFINITE;
+  minmax_out[0] = c->h_result[0];
+  minmax_out[1] = c->h_result[1];
+  return MGARD_OK;
+}
+
+int mgard_release_plans(void) {
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end();) {
+    if (it->second->device == device) it = g_plans.erase(it);
+    else ++it;
+  }
+  return MGARD_OK;
+}
+
+const char* mgard_error_string(int code) {
+  switch (code) {
+    case MGARD_OK: return "ok";
+    case MGARD_ERR_ARG: return "invalid argument (null or misaligned pointer, bad dtype, tau <= 0)";
+    case MGARD_ERR_SHAPE: return "invalid shape (ndim must be 1..3 and every axis >= 3 nodes)";
+    case MGARD_ERR_COORDS: return "coordinates must be finite and strictly increasing";
+    case MGARD_ERR_LEVEL: return "stop level outside [0, L]";
+    case MGARD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case MGARD_ERR_OVERFLOW: return "a quantization label would exceed 2^62 in magnitude";
+    case MGARD_ERR_NONFINITE: return "input contains NaN or Inf";
+    case MGARD_ERR_CUDA: return "CUDA runtime error";
+    case MGARD_ERR_TIMEOUT: return "bounded device-side wait timed out";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Device-side views of the plan tables and the launchers of the transform
+// kernels.  Every grid is handled as 3D (n0, n1, n2) with n2 contiguous;
+// padded leading axes have n = nc = 1 and identity tables.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgb {
+
+template <typename T>
+struct AxisK {
+  const T* iwl;  // [n]  left interpolation weight of coefficient nodes
+  const T* iwr;  // [n]  right interpolation weight of coefficient nodes
+  const T* rw;   // [nc*5] load-vector weights on fine offsets -2..+2
+  const T* ta;   // [nc] Thomas: sub-diagonal
+  const T* tm;   // [nc] Thomas: reciprocal pivot
+  const T* tc;   // [nc] Thomas: eliminated super-diagonal
+  int n;
+  int nc;
+};
+
+template <typename T>
+struct LevelK {
+  AxisK<T> ax[3];
+};
+
+// How the last tridiagonal solve of a level writes its result x.
+enum ApplyMode : int {
+  kApplyNone = 0,       // F <- x
+  kApplyDecompose = 1,  // B <- B + x and F <- old B  (B held u on N_{l-1})
+  kApplyRecompose = 2,  // B <- B - x                 (B held Q_{l-1}u)
+};
+
+// Load vector of one level, read-only on `fine` (level-l grid, n0 x n1 x n2):
+//   dec = true : w = fine - Pi(fine at nodal nodes) on coefficient nodes
+//   dec = false: w = fine on coefficient nodes (fine holds u_mc)
+//   w = 0 on nodal nodes; F = (R0 x R1 x R2) w on the coarse grid; and the
+//   nodal values of `fine` are gathered into `coarse` (nc0 x nc1 x nc2).
+template <typename T>
+cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
+                               cudaStream_t s);
+
+// Batched Thomas solves of M_c along every axis (2, then 1, then 0), the
+// last one applying its result to B as `mode` says.
+template <typename T>
+cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, cudaStream_t s);
+
+// In-place finishing pass over the level-l grid `fine`:
+//   nodal nodes       : fine <- nodal_src[k]
+//   coefficient nodes : fine <- fine + sign * Pi(interp_src)
+// Decomposition: nodal_src = B_{l-1} (final coarse values), interp_src =
+// F_{l-1} (saved u on N_{l-1}), sign = -1.  Recomposition: nodal_src =
+// interp_src = B_{l-1} (the interpolant's coarse values), sign = +1.
+template <typename T>
+cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* interp_src, T sign,
+                          T* fine, cudaStream_t s);
+
+// Quantization / dequantization / value range (quantize.cu).
+struct LevelTable {
+  double q[48];  // bin width 2 tau_l per level
+};
+template <typename T>
+cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev0,
+                            const uint8_t* lev1, const uint8_t* lev2, int64_t n0, int64_t n1,
+                            int64_t n2, int stop_level, const LevelTable& tab,
+                            unsigned int* flags, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* lev0,
+                              const uint8_t* lev1, const uint8_t* lev2, int64_t n0, int64_t n1,
+                              int64_t n2, int stop_level, const LevelTable& tab, cudaStream_t s);
+template <typename T>
+cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigned int* flags,
+                          double* result, cudaStream_t s);
+constexpr int kMinmaxBlocks = 608;  // 4 x 152 SMs
+
+}  // namespace mgb

@@ -1,0 +1,56 @@
+// Host-side plan of the multilevel transform: grid hierarchy, per-level
+// per-axis 1D operator tables and level tolerances, all in FP64.
+//
+// The tables are the data the GPU kernels need for one level transition
+// l -> l-1 along one axis (Section 2; Section 5.2 Lemma 1; Section 5.4):
+//   iwl/iwr : linear-interpolation weights of each coefficient node from its
+//             two coarse neighbours (0 on nodal nodes),
+//   rw      : the load-vector (mass multiply + restriction, P^T M_f) row of
+//             each coarse node, as 5 weights on fine offsets -2..+2 around the
+//             coarse node's fine position,
+//   ta/tm/tc: Thomas factors of the coarse mass matrix M_c: sub-diagonal a_k,
+//             reciprocal pivot m_k and eliminated super-diagonal c'_k
+//             (precomputed once, Section 5.4 "intermediate variable reuse").
+// rw and M_c are both divided by the mean coarse spacing, which cancels in
+// M_c^{-1} P^T M_f and keeps FP32 tables O(1).
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <vector>
+
+namespace mgb {
+
+constexpr int kMaxLevels = 40;
+
+struct AxisTables {
+  int n = 1;   // fine nodes on this axis at level l (1 = padded axis)
+  int nc = 1;  // coarse nodes, n / 2 + 1
+  std::vector<double> iwl, iwr;    // [n]
+  std::vector<double> rw;          // [nc * 5]
+  std::vector<double> ta, tm, tc;  // [nc]
+  double rmax = 1, smax = 1, dmax = 0;  // row-sum maxima of |M_c^{-1} P^T M_f|
+};
+
+struct HostPlan {
+  int ndim = 0;                           // dimensionality given by the caller
+  std::array<int64_t, 3> dims3{1, 1, 1};  // padded to 3 axes (leading 1s)
+  int L = 0;
+  std::vector<std::array<int64_t, 3>> shape;  // [L+1] level shapes (padded)
+  std::vector<std::array<AxisTables, 3>> ax;  // [L+1]; entry l = transition l -> l-1
+  std::array<std::vector<uint8_t>, 3> lev;    // per finest index: least level containing it
+  std::vector<double> knorm;                  // [L+1] bound on |K_l|_inf (entry 0 unused)
+  std::vector<double> coords_key;             // coordinates as given (for the plan cache)
+  int64_t count() const { return dims3[0] * dims3[1] * dims3[2]; }
+};
+
+// Returns MGARD_OK or an MGARD_ERR_* code.
+int check_shape(int ndim, const int64_t* dims);
+int count_levels(int ndim, const int64_t* dims, int* L);
+int build_host_plan(int ndim, const int64_t* dims, const double* const* coords, HostPlan& out);
+
+double linf_constant(const HostPlan& p, int stop_level);
+// tau_out receives L+1 values (entries below stop_level repeat tau_{stop}).
+void level_tolerances(const HostPlan& p, int stop_level, double tau, double* tau_out);
+
+}  // namespace mgb

@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+exports every symbol its header declares, and the host-only entry points
+(hierarchy depth, workspace size, level tolerances, argument errors) agree
+with the oracle and the header."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mgard_oracle as O
+from paper_2010_05872_gb300 import binding as B
+from paper_2010_05872_gb300 import build as build_mod
+from paper_2010_05872_gb300 import fields as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return B.lib()
+
+
+def _declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(mgard_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_symbols_exported(lib):
+    declared = _declared_symbols()
+    assert "mgard_decompose" in declared and "mgard_quantize" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+        ctypes.cast(getattr(lib, name), ctypes.c_void_p)
+    assert sorted(B.exported_symbols()) == declared
+
+
+@pytest.mark.parametrize("dims", [(3,), (4,), (9,), (10,), (65, 65, 65), (500, 500, 100),
+                                  (513, 513, 513), (33, 257, 100), (1025, 4096)])
+def test_num_levels_matches_oracle(lib, dims):
+    assert B.mgard_num_levels(dims) == O.Hierarchy(dims).L
+
+
+def test_workspace_size(lib):
+    for dims in [(65, 65, 65), (500, 500, 100), (10,), (17, 12)]:
+        H = O.Hierarchy(dims)
+        for dtype, es in ((B.F32, 4), (B.F64, 8)):
+            need = 2 * es * sum(int(np.prod(H.levels[l])) for l in range(H.L))
+            got = B.mgard_workspace_size(dims, dtype)
+            assert need <= got <= need + 2 * 256 * (H.L + 1)
+            assert got % 256 == 0
+
+
+@pytest.mark.parametrize("dims,kind,stop", [((65, 65, 65), "u", 0), ((500, 500, 100), "z", 3),
+                                            ((500, 500, 100), "z", 0), ((33,), "g", 0),
+                                            ((20, 17), "g", 1), ((9, 9, 9), "u", 2)])
+def test_level_tolerances_match_oracle(lib, dims, kind, stop):
+    if kind == "u":
+        coords = None
+    elif kind == "z":
+        coords = [None] * (len(dims) - 1) + [F.geometric_coords(dims[-1], 1.03)]
+    else:
+        coords = [F.geometric_coords(n, 1.05) for n in dims]
+    tau = 1e-3
+    got = B.mgard_level_tolerances(dims, coords, stop, tau)
+    exp = O.level_tolerances(O.Hierarchy(dims, coords), stop, tau)
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=0)
+
+
+def _rc(fn, *args):
+    try:
+        fn(*args)
+    except B.MgardError as e:
+        return e.code
+    return 0
+
+
+def test_argument_errors(lib):
+    assert _rc(B.mgard_num_levels, (2, 5)) == -2
+    assert _rc(B.mgard_num_levels, (5, 5, 5, 5)) == -2
+    assert _rc(B.mgard_level_tolerances, (9, 9), None, 3, 1.0) == -4
+    assert _rc(B.mgard_level_tolerances, (9, 9), None, 0, 0.0) == -1
+    assert _rc(B.mgard_level_tolerances, (9, 9), None, 0, float("nan")) == -1
+    bad = [np.array([0, 1, 2, 2, 3, 4, 5, 6, 7.0]), None]
+    assert _rc(B.mgard_level_tolerances, (9, 9), bad, 0, 1.0) == -3
+    assert _rc(B.mgard_workspace_size, (9, 9), 7) == -1
+    # Shape and dtype errors of the device entry points are reported before
+    # any CUDA call.
+    assert B.mgard_decompose((2, 9), None, B.F32, 0, 0, 0, 0, 0) == -2
+    assert B.mgard_recompose((9, 9), None, 5, 0, 0, 0, 0, 0) == -1
+    assert lib.mgard_error_string(-5).decode().startswith("workspace")
