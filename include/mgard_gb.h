@@ -140,8 +140,43 @@ int mgard_recompose_host(int ndim, const int64_t* dims, const double* const* coo
                          int stop_level, const void* host_in, void* host_out, void* dev_data,
                          void* workspace, size_t ws_bytes, void* stream);
 
+/* Host-buffer compression round trip (Algorithm 1 with a fixed stopping
+ * level and the uniform quantizer of Section 4.1 also on Q_{l~}u in place of
+ * the external compressor; the lossless back end stays outside):
+ * mgard_compress_host copies `host_field` to `dev_data`, takes the value
+ * range on the device, sets tau_linf = rel_bound * (max - min) (a constant
+ * field uses rel_bound * |value|, or rel_bound if it is 0), decomposes,
+ * quantizes into `dev_labels` (int64, element count of the field) and copies
+ * the labels to `host_labels`; *tau_out receives tau_linf.
+ * mgard_decompress_host copies `host_labels` to `dev_labels`, dequantizes
+ * into `dev_data`, recomposes and copies the field to `host_field`.  Both
+ * synchronise the stream before returning; the error codes are those of the
+ * calls they chain. */
+int mgard_compress_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                        int stop_level, double rel_bound, const void* host_field,
+                        int64_t* host_labels, double* tau_out, void* dev_data, int64_t* dev_labels,
+                        void* workspace, size_t ws_bytes, void* stream);
+int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                          int stop_level, double tau_linf, const int64_t* host_labels,
+                          void* host_field, void* dev_data, int64_t* dev_labels, void* workspace,
+                          size_t ws_bytes, void* stream);
+
 /* Free every cached plan (device tables included) of the current device. */
 int mgard_release_plans(void);
+
+/* Kernel timing trace (host-side bookkeeping, no effect on results).
+ * mgard_trace_enable(1) clears earlier records and starts bracketing every
+ * kernel launch of this library with CUDA events on the launch stream;
+ * mgard_trace_enable(0) stops.  mgard_trace_read waits for the recorded
+ * events and returns one row per (kernel kind, fine level; -1 for the
+ * level-free kernels) with the launch count, the summed device time in ms and
+ * the summed algorithmic bytes (each input read once, each output written
+ * once); up to max_rows rows are written, *rows_out receives the number of
+ * rows available.  mgard_trace_kernel_name names a kind. */
+int mgard_trace_enable(int on);
+int mgard_trace_read(int max_rows, int* kind, int* level, int64_t* launches, double* total_ms,
+                     double* bytes, int* rows_out);
+const char* mgard_trace_kernel_name(int kind);
 
 /* Static description of an error code. */
 const char* mgard_error_string(int code);

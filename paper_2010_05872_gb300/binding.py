@@ -48,8 +48,19 @@ _SIGNATURES = {
                                             _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "mgard_recompose_host": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                             _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_compress_host": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, _VP, _VP, _DP, _VP, _VP, _VP,
+                                           ctypes.c_size_t, _VP]),
+    "mgard_decompress_host": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, _VP, _VP, _VP, _VP, _VP,
+                                             ctypes.c_size_t, _VP]),
     "mgard_release_plans": (ctypes.c_int, []),
     "mgard_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mgard_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mgard_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "mgard_trace_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
 _lib = None
@@ -181,8 +192,49 @@ def mgard_value_range(count, dtype, data_ptr, stream):
     return rc, out
 
 
+def mgard_compress_host(dims, coords, dtype, stop_level, rel_bound, host_field_ptr,
+                        host_labels_ptr, dev_data_ptr, dev_labels_ptr, ws_ptr, ws_bytes, stream):
+    s = _Shape(dims, coords)
+    tau = ctypes.c_double()
+    rc = lib().mgard_compress_host(s.ndim, s.dims, s.coords, dtype, stop_level, float(rel_bound),
+                                   host_field_ptr, host_labels_ptr, ctypes.byref(tau),
+                                   dev_data_ptr, dev_labels_ptr, ws_ptr, ws_bytes, stream)
+    return rc, tau.value
+
+
+def mgard_decompress_host(dims, coords, dtype, stop_level, tau, host_labels_ptr, host_field_ptr,
+                          dev_data_ptr, dev_labels_ptr, ws_ptr, ws_bytes, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_decompress_host(s.ndim, s.dims, s.coords, dtype, stop_level, float(tau),
+                                       host_labels_ptr, host_field_ptr, dev_data_ptr,
+                                       dev_labels_ptr, ws_ptr, ws_bytes, stream)
+
+
 def mgard_release_plans() -> int:
     return lib().mgard_release_plans()
+
+
+def mgard_trace_enable(on: bool) -> int:
+    return lib().mgard_trace_enable(1 if on else 0)
+
+
+def mgard_trace_read():
+    """Rows of the kernel timing trace: dicts with kernel name, kind, level,
+    launches, total_ms and bytes (algorithmic)."""
+    n = ctypes.c_int()
+    _check(lib().mgard_trace_read(0, None, None, None, None, None, ctypes.byref(n)),
+           "mgard_trace_read")
+    m = n.value
+    kind = (ctypes.c_int * max(m, 1))()
+    level = (ctypes.c_int * max(m, 1))()
+    launches = (ctypes.c_int64 * max(m, 1))()
+    ms = (ctypes.c_double * max(m, 1))()
+    nbytes = (ctypes.c_double * max(m, 1))()
+    _check(lib().mgard_trace_read(m, kind, level, launches, ms, nbytes, ctypes.byref(n)),
+           "mgard_trace_read")
+    return [dict(kernel=lib().mgard_trace_kernel_name(kind[i]).decode(), kind=kind[i],
+                 level=level[i], launches=launches[i], total_ms=ms[i], bytes=nbytes[i])
+            for i in range(min(m, n.value))]
 
 
 # ------------------------------------------------------- torch helpers ---

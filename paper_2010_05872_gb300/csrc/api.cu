@@ -230,11 +230,11 @@ int run_decompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s)
     F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
   }
   for (int l = L; l > stop; --l) {
-    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], s));
-    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, s));
+    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, s));
   }
   for (int l = stop + 1; l <= L; ++l)
-    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], s));
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, s));
   return MGARD_OK;
 }
 
@@ -251,10 +251,10 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s)
     F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
   }
   for (int l = L; l > stop; --l)
-    MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], s));
+    MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], l, s));
   for (int l = stop + 1; l <= L; ++l) {
-    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, s));
-    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, l, s));
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], l, s));
   }
   return MGARD_OK;
 }
@@ -448,6 +448,64 @@ int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax
   if (c->h_flags[0] & 1u) return MGARD_ERR_NONFINITE;
   minmax_out[0] = c->h_result[0];
   minmax_out[1] = c->h_result[1];
+  return MGARD_OK;
+}
+
+int mgard_compress_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                        int stop_level, double rel_bound, const void* host_field,
+                        int64_t* host_labels, double* tau_out, void* dev_data, int64_t* dev_labels,
+                        void* workspace, size_t ws_bytes, void* stream) {
+  if (host_field == nullptr || host_labels == nullptr || tau_out == nullptr) return MGARD_ERR_ARG;
+  if (!(rel_bound > 0.0) || !std::isfinite(rel_bound)) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*p, stop_level, dev_data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  if (dev_labels == nullptr || reinterpret_cast<uintptr_t>(dev_labels) % 8) return MGARD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t count = p->h.count();
+  const size_t bytes = static_cast<size_t>(count) * elem_size(dtype);
+  MGB_TRY(cudaMemcpyAsync(dev_data, host_field, bytes, cudaMemcpyHostToDevice, s));
+  double mm[2];
+  rc = mgard_value_range(count, dtype, dev_data, mm, stream);
+  if (rc != MGARD_OK) return rc;
+  double tau = rel_bound * (mm[1] - mm[0]);
+  if (!(tau > 0.0)) tau = rel_bound * (std::fabs(mm[0]) > 0.0 ? std::fabs(mm[0]) : 1.0);
+  rc = transform(true, ndim, dims, coords, dtype, stop_level, dev_data, workspace, ws_bytes, stream);
+  if (rc != MGARD_OK) return rc;
+  rc = mgard_quantize(ndim, dims, coords, dtype, stop_level, tau, dev_data, dev_labels, nullptr,
+                      stream);
+  if (rc != MGARD_OK) return rc;
+  MGB_TRY(cudaMemcpyAsync(host_labels, dev_labels, static_cast<size_t>(count) * 8,
+                          cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  *tau_out = tau;
+  return MGARD_OK;
+}
+
+int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                          int stop_level, double tau_linf, const int64_t* host_labels,
+                          void* host_field, void* dev_data, int64_t* dev_labels, void* workspace,
+                          size_t ws_bytes, void* stream) {
+  if (host_field == nullptr || host_labels == nullptr) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*p, stop_level, dev_data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  if (dev_labels == nullptr || reinterpret_cast<uintptr_t>(dev_labels) % 8) return MGARD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t count = p->h.count();
+  MGB_TRY(cudaMemcpyAsync(dev_labels, host_labels, static_cast<size_t>(count) * 8,
+                          cudaMemcpyHostToDevice, s));
+  rc = mgard_dequantize(ndim, dims, coords, dtype, stop_level, tau_linf, dev_labels, dev_data, stream);
+  if (rc != MGARD_OK) return rc;
+  rc = transform(false, ndim, dims, coords, dtype, stop_level, dev_data, workspace, ws_bytes, stream);
+  if (rc != MGARD_OK) return rc;
+  MGB_TRY(cudaMemcpyAsync(host_field, dev_data, static_cast<size_t>(count) * elem_size(dtype),
+                          cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
   return MGARD_OK;
 }
 

@@ -1,5 +1,6 @@
 // Device-side views of the plan tables and the launchers of the transform
-// kernels.  Every grid is handled as 3D (n0, n1, n2) with n2 contiguous;
+// kernels (`level` is the fine level of the transition, used to tag the
+// kernel timing trace).  Every grid is handled as 3D (n0, n1, n2) with n2 contiguous;
 // padded leading axes have n = nc = 1 and identity tables.
 #pragma once
 
@@ -39,12 +40,13 @@ enum ApplyMode : int {
 //   nodal values of `fine` are gathered into `coarse` (nc0 x nc1 x nc2).
 template <typename T>
 cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
-                               cudaStream_t s);
+                               int level, cudaStream_t s);
 
 // Batched Thomas solves of M_c along every axis (2, then 1, then 0), the
 // last one applying its result to B as `mode` says.
 template <typename T>
-cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, cudaStream_t s);
+cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int level,
+                          cudaStream_t s);
 
 // In-place finishing pass over the level-l grid `fine`:
 //   nodal nodes       : fine <- nodal_src[k]
@@ -54,7 +56,7 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, cudaS
 // interp_src = B_{l-1} (the interpolant's coarse values), sign = +1.
 template <typename T>
 cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* interp_src, T sign,
-                          T* fine, cudaStream_t s);
+                          T* fine, int level, cudaStream_t s);
 
 // Quantization / dequantization / value range (quantize.cu).
 struct LevelTable {

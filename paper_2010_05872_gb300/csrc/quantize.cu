@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "kernels.cuh"
+#include "trace.hpp"
 
 namespace mgb {
 
@@ -147,6 +148,7 @@ cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev
                             const uint8_t* lev1, const uint8_t* lev2, int64_t n0, int64_t n1,
                             int64_t n2, int stop_level, const LevelTable& tab,
                             unsigned int* flags, cudaStream_t s) {
+  TraceScope ts(kKQuantize, -1, double(n0) * n1 * n2 * (sizeof(T) + 8), s);
   quantize_kernel<T><<<row_grid(n0, n1, n2), kThreads, 0, s>>>(coeffs, labels, lev0, lev1, lev2,
                                                                 n0, n1, n2, stop_level, tab, flags);
   return cudaGetLastError();
@@ -156,6 +158,7 @@ template <typename T>
 cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* lev0,
                               const uint8_t* lev1, const uint8_t* lev2, int64_t n0, int64_t n1,
                               int64_t n2, int stop_level, const LevelTable& tab, cudaStream_t s) {
+  TraceScope ts(kKDequantize, -1, double(n0) * n1 * n2 * (sizeof(T) + 8), s);
   dequantize_kernel<T><<<row_grid(n0, n1, n2), kThreads, 0, s>>>(labels, coeffs, lev0, lev1, lev2,
                                                                   n0, n1, n2, stop_level, tab);
   return cudaGetLastError();
@@ -167,6 +170,7 @@ cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigne
   int64_t blocks = (count + kThreads - 1) / kThreads;
   if (blocks > kMinmaxBlocks) blocks = kMinmaxBlocks;
   if (blocks < 1) blocks = 1;
+  TraceScope ts(kKMinmax, -1, double(count) * sizeof(T), s);
   minmax_partial_kernel<T><<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(data, count, partial,
                                                                              flags);
   minmax_final_kernel<<<1, kThreads, 0, s>>>(partial, static_cast<int>(blocks), result);

@@ -1,0 +1,38 @@
+// Kernel timing trace: while enabled, every kernel launch of the library is
+// bracketed by CUDA events recorded on its own stream, tagged with the kernel
+// kind, the level it worked on and its algorithmic bytes (each input read
+// once, each output written once).  mgard_trace_read() aggregates them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mgb {
+
+enum KernelKind : int {
+  kKLoadVectorDec = 0,
+  kKLoadVectorRec,
+  kKSolveContig,
+  kKSolveStrided,
+  kKFinishDec,
+  kKFinishRec,
+  kKQuantize,
+  kKDequantize,
+  kKMinmax,
+  kKNumKinds
+};
+
+const char* kernel_kind_name(int kind);
+
+class TraceScope {
+ public:
+  TraceScope(int kind, int level, double bytes, cudaStream_t s);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  int slot_ = -1;
+  cudaStream_t s_ = nullptr;
+};
+
+}  // namespace mgb

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "trace.hpp"
 
 namespace mgb {
 
@@ -296,7 +297,7 @@ inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a
 
 template <typename T>
 cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
-                               cudaStream_t s) {
+                               int level, cudaStream_t s) {
   const Tile t = pick_tile(lv);
   const int tk0 = lv.ax[0].n == 1 ? 1 : t.t0, tk1 = lv.ax[1].n == 1 ? 1 : t.t1, tk2 = t.t2;
   const int S0 = region(tk0, lv.ax[0].n), S1 = region(tk1, lv.ax[1].n), S2 = region(tk2, lv.ax[2].n);
@@ -304,6 +305,9 @@ cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* 
                                    static_cast<size_t>(S0) * S1 * tk2 +
                                    static_cast<size_t>(S0) * tk1 * tk2);
   dim3 grid(ceil_div(lv.ax[2].nc, tk2), ceil_div(lv.ax[1].nc, tk1), ceil_div(lv.ax[0].nc, tk0));
+  const double nf = double(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
+  const double ncs = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
+  TraceScope ts(dec ? kKLoadVectorDec : kKLoadVectorRec, level, sizeof(T) * (nf + 2 * ncs), s);
   if (dec) {
     cudaFuncSetAttribute(load_vector_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
@@ -317,12 +321,16 @@ cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* 
 }
 
 template <typename T>
-cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, cudaStream_t s) {
+cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int level,
+                          cudaStream_t s) {
   const int64_t c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   int last = 0;
   while (lv.ax[last].n == 1) ++last;  // lowest active axis is solved last
   for (int a = 2; a >= last; --a) {
     const int m = (a == last) ? mode : kApplyNone;
+    const double passes = m == kApplyDecompose ? 4.0 : m == kApplyRecompose ? 3.0 : 2.0;
+    TraceScope ts(a == 2 ? kKSolveContig : kKSolveStrided, level,
+                  sizeof(T) * passes * double(c0) * c1 * c2, s);
     if (a == 2) {
       const int64_t nlines = c0 * c1;
       const size_t per_row = sizeof(T) * static_cast<size_t>(c2 | 1);
@@ -347,26 +355,30 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, cudaS
 
 template <typename T>
 cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* interp_src, T sign,
-                          T* fine, cudaStream_t s) {
+                          T* fine, int level, cudaStream_t s) {
   const int n2 = lv.ax[2].n;
   const int bx = static_cast<int>(std::min<int64_t>(ceil_div(n2, kThreads), 64));
   const int64_t nrows = static_cast<int64_t>(lv.ax[0].n) * lv.ax[1].n;
   dim3 grid(bx, static_cast<unsigned>(std::min<int64_t>(nrows, 65535)));
+  const double nf = double(nrows) * n2;
+  const double ncs = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
+  TraceScope ts(sign < T(0) ? kKFinishDec : kKFinishRec, level,
+                sizeof(T) * (2 * nf + (nodal_src == interp_src ? 1 : 2) * ncs), s);
   finish_kernel<T><<<grid, kThreads, 0, s>>>(lv, nodal_src, interp_src, sign, fine);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_load_vector<float>(const LevelK<float>&, bool, const float*, float*,
-                                               float*, cudaStream_t);
+                                               float*, int, cudaStream_t);
 template cudaError_t launch_load_vector<double>(const LevelK<double>&, bool, const double*,
-                                                double*, double*, cudaStream_t);
-template cudaError_t launch_solves<float>(const LevelK<float>&, float*, float*, ApplyMode,
+                                                double*, double*, int, cudaStream_t);
+template cudaError_t launch_solves<float>(const LevelK<float>&, float*, float*, ApplyMode, int,
                                           cudaStream_t);
-template cudaError_t launch_solves<double>(const LevelK<double>&, double*, double*, ApplyMode,
+template cudaError_t launch_solves<double>(const LevelK<double>&, double*, double*, ApplyMode, int,
                                            cudaStream_t);
 template cudaError_t launch_finish<float>(const LevelK<float>&, const float*, const float*, float,
-                                          float*, cudaStream_t);
+                                          float*, int, cudaStream_t);
 template cudaError_t launch_finish<double>(const LevelK<double>&, const double*, const double*,
-                                           double, double*, cudaStream_t);
+                                           double, double*, int, cudaStream_t);
 
 }  // namespace mgb
