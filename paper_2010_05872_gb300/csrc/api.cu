@@ -28,6 +28,7 @@ struct DevPlan {
   std::vector<LevelK<float>> lvf;   // [L+1], entry l = transition l -> l-1
   std::vector<LevelK<double>> lvd;
   const uint8_t* lev[3] = {nullptr, nullptr, nullptr};
+  const uint8_t* lev01 = nullptr;   // per-row level (quantizer)
   std::vector<size_t> offB, offF;   // workspace offsets of the level-l grids / load vectors
   size_t ws_bytes = 0;
   ~DevPlan() {
@@ -94,6 +95,7 @@ int upload(DevPlan& p) {
     }
   size_t lev_off[3];
   for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
+  const size_t lev01_off = reserve(h.lev01.size());
   std::vector<char> stage(total, 0);
   auto put = [&](size_t off, const std::vector<double>& v) {
     T* dst = reinterpret_cast<T*>(stage.data() + off);
@@ -107,12 +109,14 @@ int upload(DevPlan& p) {
       put(o[3], t.ta); put(o[4], t.tm); put(o[5], t.tc);
     }
   for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
+  std::memcpy(stage.data() + lev01_off, h.lev01.data(), h.lev01.size());
   if (cudaMalloc(&p.dmem, total) != cudaSuccess) return MGARD_ERR_CUDA;
   if (cudaMemcpy(p.dmem, stage.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) return MGARD_ERR_CUDA;
   char* base = static_cast<char*>(p.dmem);
   if constexpr (sizeof(T) == 4) fill_levels<float>(p, offs, base, p.lvf);
   else fill_levels<double>(p, offs, base, p.lvd);
   for (int a = 0; a < 3; ++a) p.lev[a] = reinterpret_cast<const uint8_t*>(base + lev_off[a]);
+  p.lev01 = reinterpret_cast<const uint8_t*>(base + lev01_off);
   return MGARD_OK;
 }
 
@@ -185,6 +189,7 @@ DevCtx* get_ctx() {
   if (it != g_ctx.end()) return it->second.get();
   auto c = std::make_unique<DevCtx>();
   if (cudaMalloc(&c->flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
+  if (cudaMemset(c->flags, 0, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
   if (cudaMalloc(&c->partial, 2 * kMinmaxBlocks * sizeof(double)) != cudaSuccess) return nullptr;
   if (cudaMalloc(&c->result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
   if (cudaMallocHost(&c->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
@@ -220,7 +225,8 @@ const std::vector<LevelK<double>>& levels<double>(const DevPlan& p) { return p.l
 // coarsest first, the finishing pass writes each level's coefficients and the
 // final coarser values into the level-l grid.
 template <typename T>
-int run_decompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s) {
+int run_decompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* status,
+                  cudaStream_t s) {
   const int L = p.h.L;
   const auto& lv = levels<T>(p);
   std::vector<T*> B(L + 1), F(L + 1);
@@ -230,18 +236,19 @@ int run_decompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s)
     F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
   }
   for (int l = L; l > stop; --l) {
-    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, s));
+    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, status, s));
     MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, s));
   }
   for (int l = stop + 1; l <= L; ++l)
-    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, s));
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, status, s));
   return MGARD_OK;
 }
 
 // Recomposition: gather every level's coarse part and load vector top-down,
 // then bottom-up solve, subtract the correction and interpolate.
 template <typename T>
-int run_recompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s) {
+int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* status,
+                  cudaStream_t s) {
   const int L = p.h.L;
   const auto& lv = levels<T>(p);
   std::vector<T*> B(L + 1), F(L + 1);
@@ -251,10 +258,10 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, cudaStream_t s)
     F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
   }
   for (int l = L; l > stop; --l)
-    MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], l, s));
+    MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], l, status, s));
   for (int l = stop + 1; l <= L; ++l) {
     MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, l, s));
-    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], l, s));
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], l, status, s));
   }
   return MGARD_OK;
 }
@@ -269,11 +276,14 @@ int transform(bool dec, int ndim, const int64_t* dims, const double* const* coor
   if (stop_level == p->h.L) return MGARD_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  unsigned int* status = c->flags + 1;
   if (dtype == MGARD_F64)
-    return dec ? run_decompose<double>(*p, stop_level, static_cast<double*>(data), ws, s)
-               : run_recompose<double>(*p, stop_level, static_cast<double*>(data), ws, s);
-  return dec ? run_decompose<float>(*p, stop_level, static_cast<float*>(data), ws, s)
-             : run_recompose<float>(*p, stop_level, static_cast<float*>(data), ws, s);
+    return dec ? run_decompose<double>(*p, stop_level, static_cast<double*>(data), ws, status, s)
+               : run_recompose<double>(*p, stop_level, static_cast<double*>(data), ws, status, s);
+  return dec ? run_decompose<float>(*p, stop_level, static_cast<float*>(data), ws, status, s)
+             : run_recompose<float>(*p, stop_level, static_cast<float*>(data), ws, status, s);
 }
 
 int transform_host(bool dec, int ndim, const int64_t* dims, const double* const* coords, int dtype,
@@ -300,8 +310,26 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
   if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
   double t[kMaxLevels];
   level_tolerances(p.h, stop_level, tau, t);
-  for (int l = 0; l < 48; ++l) tab.q[l] = 0.0;
-  for (int l = 0; l <= p.h.L; ++l) tab.q[l] = 2.0 * t[l];
+  for (int l = 0; l < 48; ++l) {
+    tab.q[l] = 1.0;
+    tab.rq[l] = std::nanf("");
+    tab.qf[l] = 1.0f;
+    tab.dqf[l] = 0.0f;
+  }
+  for (int l = 0; l <= p.h.L; ++l) {
+    tab.q[l] = 2.0 * t[l];
+    // The FP32 reciprocal drives the exact fast path of the quantizer; it is
+    // only usable when it is a normal float.
+    const double r = 1.0 / tab.q[l];
+    const float rf = static_cast<float>(r);
+    tab.rq[l] = (std::isfinite(rf) && rf >= 1.17549435e-38f) ? rf : std::nanf("");
+    // FP32 split of q for the dequantizer's FP32 route (q - fl32(q) is exact
+    // in FP64); a q outside the normal FP32 range disables that route.
+    const float qf = static_cast<float>(tab.q[l]);
+    const bool qok = std::isfinite(qf) && qf >= 1.17549435e-38f;
+    tab.qf[l] = qok ? qf : std::nanf("");
+    tab.dqf[l] = qok ? static_cast<float>(tab.q[l] - static_cast<double>(qf)) : 0.0f;
+  }
   if (tau_out)
     for (int l = 0; l <= p.h.L; ++l) tau_out[l] = t[l];
   return MGARD_OK;
@@ -395,13 +423,17 @@ int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, i
   MGB_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s));
   const auto& d = p->h.dims3;
   if (dtype == MGARD_F64)
-    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p->lev[0], p->lev[1],
-                                    p->lev[2], d[0], d[1], d[2], stop_level, tab, c->flags, s));
+    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p->lev01, p->lev[2],
+                                    d[0] * d[1], d[2], stop_level, tab, c->flags, s));
   else
-    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p->lev[0], p->lev[1],
-                                   p->lev[2], d[0], d[1], d[2], stop_level, tab, c->flags, s));
-  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p->lev01, p->lev[2],
+                                   d[0] * d[1], d[2], stop_level, tab, c->flags, s));
+  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
+  if (c->h_flags[1]) {
+    MGB_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(unsigned), s));
+    return MGARD_ERR_TIMEOUT;
+  }
   const unsigned f = c->h_flags[0];
   if (f & 1u) return MGARD_ERR_NONFINITE;
   if (f & 2u) return MGARD_ERR_OVERFLOW;
@@ -423,10 +455,10 @@ int mgard_dequantize(int ndim, const int64_t* dims, const double* const* coords,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const auto& d = p->h.dims3;
   if (dtype == MGARD_F64)
-    return cuda_rc(launch_dequantize<double>(labels, static_cast<double*>(coeffs), p->lev[0],
-                                             p->lev[1], p->lev[2], d[0], d[1], d[2], stop_level, tab, s));
-  return cuda_rc(launch_dequantize<float>(labels, static_cast<float*>(coeffs), p->lev[0], p->lev[1],
-                                          p->lev[2], d[0], d[1], d[2], stop_level, tab, s));
+    return cuda_rc(launch_dequantize<double>(labels, static_cast<double*>(coeffs), p->lev01,
+                                             p->lev[2], d[0] * d[1], d[2], stop_level, tab, s));
+  return cuda_rc(launch_dequantize<float>(labels, static_cast<float*>(coeffs), p->lev01, p->lev[2],
+                                          d[0] * d[1], d[2], stop_level, tab, s));
 }
 
 int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax_out, void* stream) {
@@ -443,8 +475,12 @@ int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax
   else
     MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, c->partial, c->flags, c->result, s));
   MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
+  if (c->h_flags[1]) {
+    MGB_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(unsigned), s));
+    return MGARD_ERR_TIMEOUT;
+  }
   if (c->h_flags[0] & 1u) return MGARD_ERR_NONFINITE;
   minmax_out[0] = c->h_result[0];
   minmax_out[1] = c->h_result[1];

@@ -1,0 +1,471 @@
+// In-place finishing pass over a level-l grid (Section 2):
+//   decomposition : coefficient nodes get v - Pi(v on N_{l-1}) (the saved
+//                   nodal values), nodal nodes get the final coarser values;
+//   recomposition : coefficient nodes get u_mc + Pi(coarse values), nodal
+//                   nodes get the coarse values.
+// Layout of the work: a CTA takes kRows consecutive fine rows (j0, j1) and a
+// chunk of up to kCols columns.  Every row first gets its "combined" coarse
+// row in shared memory: the up to 4 coarse rows its corners come from,
+// weighted by the axis-0 and axis-1 interpolation weights.  Then one thread
+// per fine column walks the rows; its column data (nodal or coefficient,
+// coarse index, axis-2 weights) stays in registers and its kRows loads are
+// issued together.
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tma.cuh"
+#include "trace.hpp"
+
+namespace mgb {
+namespace {
+
+__device__ __forceinline__ bool is_coef(int j, int n) { return (j & 1) && (j != n - 1); }
+__device__ __forceinline__ int nodal_k(int j, int n, int nc) { return j == n - 1 ? nc - 1 : (j >> 1); }
+
+constexpr int kRows = 16;
+constexpr int kCols = 640;           // even
+constexpr int kMaxThreads = kCols;
+constexpr int kCW = kCols / 2 + 1;   // combined coarse values per row and chunk
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads)
+finish_kernel(LevelK<T> lv, const T* __restrict__ nodal_src, const T* __restrict__ interp_src,
+              T sign, T* __restrict__ fine) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* crow = reinterpret_cast<T*>(smem_raw);  // kRows x kCW
+  __shared__ int64_t s_nodal[kRows];         // coarse row offset (fully nodal rows) or -1
+  __shared__ int64_t s_o00[kRows];           // coarse row of the (low, low) corner
+  __shared__ int s_q[kRows];                 // bit 1: axis-0 coefficient, bit 0: axis-1
+  __shared__ T s_w[kRows][4];                // corner weights
+
+  const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
+  const int c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
+  const int64_t nrows = static_cast<int64_t>(n0) * n1;
+  const int64_t ngroups = (nrows + kRows - 1) / kRows;
+  const int nchunks = (n2 + kCols - 1) / kCols;
+  const int tid = threadIdx.x;
+
+  for (int64_t b = blockIdx.x; b < ngroups * nchunks; b += gridDim.x) {
+    const int64_t rg = b / nchunks;
+    const int cx = static_cast<int>(b - rg * nchunks);
+    const int64_t r0 = rg * kRows;
+    const int R = static_cast<int>(min(static_cast<int64_t>(kRows), nrows - r0));
+    const int jlo = cx * kCols, jhi = min(jlo + kCols, n2);  // fine columns [jlo, jhi)
+    const int klo = jlo / 2, khi = min(jhi / 2, c2 - 1);      // coarse columns [klo, khi]
+    const int kw = khi - klo + 1;
+
+    // Row data, one thread per row: corner coarse row, weights, and the
+    // coarse row of fully nodal rows.
+    if (tid < R) {
+      const int64_t rr = r0 + tid;
+      const int j0 = static_cast<int>(rr / n1), j1 = static_cast<int>(rr - static_cast<int64_t>(j0) * n1);
+      const bool q0 = is_coef(j0, n0), q1 = is_coef(j1, n1);
+      const int a0 = q0 ? (j0 - 1) >> 1 : nodal_k(j0, n0, c0);
+      const int a1 = q1 ? (j1 - 1) >> 1 : nodal_k(j1, n1, c1);
+      const T wl0 = q0 ? lv.ax[0].iwl[j0] : T(1), wr0 = q0 ? lv.ax[0].iwr[j0] : T(0);
+      const T wl1 = q1 ? lv.ax[1].iwl[j1] : T(1), wr1 = q1 ? lv.ax[1].iwr[j1] : T(0);
+      const int64_t o00 = (static_cast<int64_t>(a0) * c1 + a1) * c2;
+      s_o00[tid] = o00;
+      s_nodal[tid] = (q0 || q1) ? -1 : o00;
+      s_q[tid] = (q0 ? 2 : 0) | (q1 ? 1 : 0);
+      s_w[tid][0] = wl0 * wl1;
+      s_w[tid][1] = wl0 * wr1;
+      s_w[tid][2] = wr0 * wl1;
+      s_w[tid][3] = wr0 * wr1;
+    }
+    __syncthreads();
+    // Combined coarse rows: items (row, coarse column) flat, 8 per thread in
+    // flight.  i / kw (i < kRows kw, kw <= kCW) is exact through
+    // (i + 0.5) / kw in FP32: that quotient is at least 1 / (2 kw) from an
+    // integer and the FP32 estimate is within kRows 2^-22 of it.
+    {
+      const int items = R * kw;
+      const float inv_kw = 1.0f / static_cast<float>(kw);
+      for (int base = tid; base < items; base += 8 * blockDim.x) {
+        T v[8];
+        int slot[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = base + u * blockDim.x;
+          slot[u] = -1;
+          v[u] = T(0);
+          if (i < items) {
+            const int rl = static_cast<int>((static_cast<float>(i) + 0.5f) * inv_kw);
+            const int k = i - rl * kw;
+            const int q = s_q[rl];
+            const T* s00 = interp_src + s_o00[rl] + klo + k;
+            T x = s_w[rl][0] * s00[0];
+            if (q & 1) x += s_w[rl][1] * s00[c2];
+            if (q & 2) {
+              const T* s10 = s00 + static_cast<int64_t>(c1) * c2;
+              x += s_w[rl][2] * s10[0];
+              if (q & 1) x += s_w[rl][3] * s10[c2];
+            }
+            v[u] = x;
+            slot[u] = rl * kCW + k;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (slot[u] >= 0) crow[slot[u]] = v[u];
+      }
+    }
+    __syncthreads();
+
+    const int j2 = jlo + tid;
+    if (j2 < jhi) {
+      const bool q2 = is_coef(j2, n2);
+      const int kn = nodal_k(j2, n2, c2);  // coarse index (nodal column)
+      const int km = (j2 >> 1) - klo;      // left coarse neighbour (coefficient column)
+      const T wl2 = q2 ? lv.ax[2].iwl[j2] : T(1), wr2 = q2 ? lv.ax[2].iwr[j2] : T(0);
+      const int kl = q2 ? km : kn - klo, kr = q2 ? km + 1 : kn - klo;
+      T f[kRows];
+#pragma unroll
+      for (int rl = 0; rl < kRows; ++rl)
+        if (rl < R) f[rl] = fine[(r0 + rl) * n2 + j2];
+#pragma unroll
+      for (int rl = 0; rl < kRows; ++rl) {
+        if (rl < R) {
+          const int64_t no = s_nodal[rl];
+          T out;
+          if (no >= 0 && !q2) {
+            out = nodal_src[no + kn];
+          } else {
+            const T* cr = crow + rl * kCW;
+            out = f[rl] + sign * (wl2 * cr[kl] + wr2 * cr[kr]);
+          }
+          fine[(r0 + rl) * n2 + j2] = out;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Marching form for 2D and 3D levels whose rows fit one CTA.  A CTA owns the
+// fine rows of T1 coarse rows along axis 1 (all columns, or a column chunk of
+// a 2D level) and walks pairs of fine planes (2m, 2m+1) along axis 0.  Per
+// pair it needs the fine rows of both planes and coarse planes m and m+1;
+// each arrives by one 1D TMA bulk copy (its enclosing 16-byte-aligned range,
+// offset kept, no byte past an array's end requested, ragged ends by plain
+// loads), the next pair's data while the current pair is computed.  One
+// thread per fine column: its axis-2 data stays in registers, rows are walked
+// with uniform row data, each output is one coalesced store.
+// ---------------------------------------------------------------------------
+constexpr int kFMaxThreads = 640;
+
+// Pipeline depth and coarse rows per CTA along axis 1, per element type:
+// NS stages of (two fine planes, one coarse plane) with NS - 1 in flight.
+template <typename T>
+struct FinishCfg;
+template <>
+struct FinishCfg<float> {
+  static constexpr int NS = 3, T1 = 4;
+};
+template <>
+struct FinishCfg<double> {
+  static constexpr int NS = 2, T1 = 4;
+};
+
+struct FinishGeom {
+  int t1, tc2, t0;       // coarse rows per CTA, fine columns per chunk, plane pairs per CTA
+  int nb0, nb1, nb2;     // CTAs along axes 0, 1, 2
+  int FBUF, CBUF;        // elements of a fine-plane buffer and of a coarse-plane buffer
+  int threads;
+};
+
+// Marching form: a CTA owns fine plane pairs [M0, M1) (planes 2m, 2m + 1) of
+// up to 2 T1C fine rows and a chunk of fine columns, one thread per column.
+// Stage m brings fine planes 2m, 2m + 1 and coarse plane m + 1 (the first
+// stage also coarse plane M0) with 1D bulk copies of the contiguous row
+// range; coarse planes sit in a ring of NS + 1 buffers.
+//
+// The interpolant is separable (Section 2, multilinear Pi): a thread first
+// interpolates each staged coarse row along axis 2 at its column, then along
+// axis 1 to every fine row, and keeps the result of coarse plane m (A) in
+// registers, so fine plane 2m reads A and plane 2m + 1 combines A with the
+// next coarse plane (B) along axis 0.  A nodal node takes its coarse value
+// exactly: weights (1, 0) or (0, 1), never a rounded mix.
+template <typename T, int NS, int T1C>
+__global__ void __launch_bounds__(kFMaxThreads)
+finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
+                    const T* __restrict__ interp_src, T sign, T* __restrict__ fine,
+                    FinishGeom g, unsigned int* __restrict__ status) {
+  constexpr int NC = NS + 1;  // coarse ring
+  constexpr int R1M = 2 * T1C, RCM = T1C + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[NS];
+  __shared__ int s_fshift[2 * NS];  // fine buffers: stage x plane
+  __shared__ int s_cshift[NC];      // coarse ring
+
+  const int tid = threadIdx.x;
+  const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
+  const int c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
+  const int b2 = blockIdx.x % g.nb2;
+  const int b1 = (blockIdx.x / g.nb2) % g.nb1;
+  const int b0 = blockIdx.x / (g.nb2 * g.nb1);
+  const int npairs = (n0 + 1) / 2;
+  const int K1 = b1 * g.t1, T1 = min(g.t1, c1 - K1);
+  const int M0 = b0 * g.t0, M1 = min(M0 + g.t0, npairs);     // plane pairs [M0, M1)
+  const int J2lo = b2 * g.tc2, J2hi = min(J2lo + g.tc2, n2);  // fine columns
+  const int W2 = J2hi - J2lo;
+  const int klo2 = J2lo / 2, khi2 = min(J2hi / 2, c2 - 1);
+  const int kw = khi2 - klo2 + 1;
+  const int r1lo = 2 * K1, r1hi = min(2 * (K1 + T1), n1);     // owned fine rows [r1lo, r1hi)
+  const int R1 = r1hi - r1lo;
+  const int k1lo = K1, k1hi = min(K1 + T1, c1 - 1);           // coarse rows needed
+  const int R1c = k1hi - k1lo + 1;
+
+  T* fbuf = reinterpret_cast<T*>(smem_raw);                // 2 NS x FBUF
+  T* cbuf = fbuf + 2 * NS * static_cast<size_t>(g.FBUF);   // NC x CBUF
+
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const uint64_t flim = (static_cast<uint64_t>(n0) * n1 * n2 * sizeof(T)) & ~15ull;
+  const uint64_t clim = (static_cast<uint64_t>(c0) * c1 * c2 * sizeof(T)) & ~15ull;
+  // One region [e0, e0 + len) of `src` into dst (16-byte-aligned superset by
+  // bulk copy, elements past the last whole 16 bytes of the array by plain
+  // loads); returns the bulk bytes.
+  auto region = [&](const T* src, uint64_t lim, uint64_t e0, int len, T* dst, int* shift_slot,
+                    uint64_t* bar, bool count_only) -> unsigned {
+    const uint64_t sb = e0 * sizeof(T), eb = sb + static_cast<uint64_t>(len) * sizeof(T);
+    const uint64_t ab = sb & ~15ull;
+    uint64_t bb = (eb + 15) & ~15ull;
+    if (bb > lim) bb = lim;
+    const unsigned bytes = bb > ab ? static_cast<unsigned>(bb - ab) : 0u;
+    if (count_only) return bytes;
+    const int shift = static_cast<int>((sb - ab) / sizeof(T));
+    if (tid == 0) {
+      *shift_slot = shift;
+      if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(src) + ab, bytes, bar);
+    }
+    const uint64_t tail0 = bb > sb ? bb : sb;
+    for (uint64_t x = tail0 + tid * sizeof(T); x < eb; x += blockDim.x * sizeof(T))
+      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = src[x / sizeof(T)];
+    return bytes;
+  };
+  // Stage for plane pair m: fine planes 2m, 2m + 1, coarse plane m + 1 and,
+  // for the first pair, coarse plane m.
+  auto issue = [&](int m, int stage) {
+    unsigned bytes = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1 && tid == 0) mbar_arrive_expect_tx(&bars[stage], bytes);
+      for (int w = 0; w < 2; ++w) {
+        const int j0 = 2 * m + w;
+        if (j0 >= n0) continue;
+        const uint64_t e0 = (static_cast<uint64_t>(j0) * n1 + r1lo) * n2 + J2lo;
+        const int len = (R1 - 1) * n2 + W2;
+        bytes += region(fine, flim, e0, len, fbuf + static_cast<size_t>(2 * stage + w) * g.FBUF,
+                        &s_fshift[2 * stage + w], &bars[stage], pass == 0);
+      }
+      for (int cm = (m == M0 ? m : m + 1); cm <= m + 1; ++cm) {
+        if (cm >= c0) continue;
+        const uint64_t e0 = (static_cast<uint64_t>(cm) * c1 + k1lo) * c2 + klo2;
+        const int len = (R1c - 1) * c2 + kw;
+        bytes += region(interp_src, clim, e0, len, cbuf + static_cast<size_t>(cm % NC) * g.CBUF,
+                        &s_cshift[cm % NC], &bars[stage], pass == 0);
+      }
+    }
+  };
+
+  // Column data of this thread (axis 2).
+  const int j2 = J2lo + tid;
+  const bool colact = tid < W2;
+  const bool q2 = colact && is_coef(j2, n2);
+  const int kn2 = colact ? nodal_k(j2, n2, c2) : 0;
+  const int kl = (q2 ? (j2 >> 1) : kn2) - klo2, kr = q2 ? kl + 1 : kl;
+  const T wl2 = q2 ? lv.ax[2].iwl[j2] : T(1), wr2 = q2 ? lv.ax[2].iwr[j2] : T(0);
+  // Row data (axis 1, the same for every thread).  Even rows are nodal with
+  // coarse row r / 2; odd row r mixes coarse rows r / 2 and r / 2 + 1, except
+  // a last fine row n1 - 1 that is nodal (even n1): weights (0, 1).
+  T wl1[T1C], wr1[T1C];
+  unsigned q1mask = 0u;  // bit r: fine row r is a coefficient row
+#pragma unroll
+  for (int i = 0; i < T1C; ++i) {
+    const int j1 = r1lo + 2 * i + 1;
+    const bool q = 2 * i + 1 < R1 && is_coef(j1, n1);
+    wl1[i] = q ? lv.ax[1].iwl[j1] : T(0);
+    wr1[i] = q ? lv.ax[1].iwr[j1] : T(1);
+    if (q) q1mask |= 1u << (2 * i + 1);
+  }
+  // Interpolant of coarse plane `cm` at this column and every owned fine row.
+  auto interp_plane = [&](int cm, T (&out)[R1M]) {
+    const T* C = cbuf + static_cast<size_t>(cm % NC) * g.CBUF + s_cshift[cm % NC];
+    T i2[RCM];
+#pragma unroll
+    for (int i = 0; i < RCM; ++i)
+      i2[i] = (i < R1c) ? wl2 * C[i * c2 + kl] + wr2 * C[i * c2 + kr] : T(0);
+#pragma unroll
+    for (int i = 0; i < T1C; ++i) {
+      out[2 * i] = i2[i];
+      out[2 * i + 1] = (i + 1 < RCM) ? wl1[i] * i2[i] + wr1[i] * i2[i + 1] : i2[i];
+    }
+  };
+
+  unsigned phases = 0u;   // bit i: parity to wait for on bars[i]
+  unsigned pending = 0u;  // bit i: bars[i] has copies in flight
+  for (int i = 0; i < NS - 1 && M0 + i < M1; ++i) {
+    issue(M0 + i, i);
+    pending |= 1u << i;
+  }
+  T A[R1M], B[R1M];
+  for (int m = M0; m < M1; ++m) {
+    const int stage = (m - M0) % NS;
+    const bool got = mbar_wait(&bars[stage], (phases >> stage) & 1u, kWaitLimitNs);
+    if (__syncthreads_or(!got)) {
+      // A copy did not land in time: record it, give every stage still in
+      // flight a second bounded wait so nothing lands after the CTA exits.
+      if (tid == 0) *reinterpret_cast<volatile unsigned*>(status) = 1u;
+      for (int i = 0; i < NS; ++i)
+        if ((pending >> i) & 1u) mbar_wait(&bars[i], (phases >> i) & 1u, kWaitLimitNs);
+      return;
+    }
+    phases ^= 1u << stage;
+    pending &= ~(1u << stage);
+    if (m + NS - 1 < M1) {
+      // The stage refilled here was last read in the previous pair.
+      const int st = (m - M0 + NS - 1) % NS;
+      if (tid == 0) fence_proxy_async();
+      issue(m + NS - 1, st);
+      pending |= 1u << st;
+    }
+    if (colact) {
+      if (m == M0) interp_plane(m, A);
+      const bool has_b = m + 1 < c0;
+      if (has_b) interp_plane(m + 1, B);
+      // Fine plane 2m: nodal along axis 0, coarse plane m.
+      {
+        const int j0 = 2 * m;
+        const T* fb = fbuf + static_cast<size_t>(2 * stage) * g.FBUF + s_fshift[2 * stage];
+        T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo) * n2 + j2;
+        const T* nsrc = nodal_src + (static_cast<int64_t>(m) * c1 + k1lo) * c2 + kn2;
+#pragma unroll
+        for (int r = 0; r < R1M; ++r) {
+          if (r < R1) {
+            const bool nodal = !q2 && !((q1mask >> r) & 1u);
+            // Fully nodal rows sit on coarse row r / 2, or (0, 1) row r / 2 + 1.
+            const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
+            dst[static_cast<int64_t>(r) * n2] =
+                nodal ? nsrc[static_cast<int64_t>(kr1) * c2] : fb[r * n2 + tid] + sign * A[r];
+          }
+        }
+      }
+      // Fine plane 2m + 1: coarse planes m and m + 1, or the nodal last
+      // plane of an even axis (coarse plane m + 1 alone).
+      const int j0 = 2 * m + 1;
+      if (j0 < n0) {
+        const bool q0 = is_coef(j0, n0);
+        const T wl0 = q0 ? lv.ax[0].iwl[j0] : T(0), wr0 = q0 ? lv.ax[0].iwr[j0] : T(1);
+        const T* fb = fbuf + static_cast<size_t>(2 * stage + 1) * g.FBUF + s_fshift[2 * stage + 1];
+        T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo) * n2 + j2;
+        const T* nsrc = nodal_src + (static_cast<int64_t>(m + 1) * c1 + k1lo) * c2 + kn2;
+#pragma unroll
+        for (int r = 0; r < R1M; ++r) {
+          if (r < R1) {
+            const bool nodal = !q0 && !q2 && !((q1mask >> r) & 1u);
+            const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
+            dst[static_cast<int64_t>(r) * n2] =
+                nodal ? nsrc[static_cast<int64_t>(kr1) * c2]
+                      : fb[r * n2 + tid] + sign * (wl0 * A[r] + wr0 * B[r]);
+          }
+        }
+      }
+      if (has_b) {
+#pragma unroll
+        for (int r = 0; r < R1M; ++r) A[r] = B[r];
+      }
+    }
+    __syncthreads();  // this stage's buffers may be refilled
+  }
+}
+
+template <typename T>
+bool finish_geometry(const LevelK<T>& lv, FinishGeom& g) {
+  const int n1 = lv.ax[1].n, n2 = lv.ax[2].n, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
+  g.t1 = (n1 == 1) ? 1 : FinishCfg<T>::T1;
+  if (n1 == 1) g.tc2 = std::min(n2, kFMaxThreads - (kFMaxThreads % 2));
+  else if (n2 <= kFMaxThreads) g.tc2 = n2;
+  else return false;  // 3D rows wider than one CTA: not contiguous per plane
+  if (g.tc2 < n2 && (g.tc2 & 1)) --g.tc2;
+  g.threads = 32 * ((g.tc2 + 31) / 32);
+  const int vec = 16 / static_cast<int>(sizeof(T));
+  const int R1 = (n1 == 1) ? 1 : 2 * g.t1;
+  g.FBUF = (((R1 - 1) * n2 + g.tc2 + 2 * vec) / vec + 1) * vec;
+  const int kwmax = std::min(g.tc2 / 2 + 1, c2);
+  const int R1c = std::min(g.t1 + 1, c1);
+  g.CBUF = (((R1c - 1) * c2 + kwmax + 2 * vec) / vec + 1) * vec;
+  g.nb1 = (c1 + g.t1 - 1) / g.t1;
+  g.nb2 = (n2 + g.tc2 - 1) / g.tc2;
+  return g.threads <= kFMaxThreads;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* interp_src, T sign,
+                          T* fine, int level, unsigned int* status, cudaStream_t s) {
+  const LevelK<T>& lv = lv_in;
+  const int64_t nf_all = int64_t(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
+  const double ncs_all = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
+  if (!(lv.ax[0].n == 1 && lv.ax[1].n == 1) && nf_all >= (int64_t(1) << 17)) {
+    LevelK<T> mv = lv_in;
+    if (mv.ax[0].n == 1) std::swap(mv.ax[0], mv.ax[1]);  // 2D: march along the rows
+    FinishGeom g{};
+    if (finish_geometry(mv, g)) {
+      TraceScope ts(sign < T(0) ? kKFinishDec : kKFinishRec, level,
+                    sizeof(T) * (2 * double(nf_all) + (nodal_src == interp_src ? 1 : 2) * ncs_all), s);
+      constexpr int NS = FinishCfg<T>::NS;
+      const size_t smem = sizeof(T) * (2 * NS * static_cast<size_t>(g.FBUF) +
+                                       (NS + 1) * static_cast<size_t>(g.CBUF));
+      auto kernel = finish_march_kernel<T, NS, FinishCfg<T>::T1>;
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+      int per_sm = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
+      per_sm = std::max(per_sm, 1);
+      const int npairs = (mv.ax[0].n + 1) / 2;
+      const int cols = g.nb1 * g.nb2, slots = 152 * per_sm;
+      int best_t0 = npairs, best_score = 1 << 30;
+      for (int waves = 1; waves <= 16; ++waves) {
+        const int chunks = std::max(1, (slots * waves + cols - 1) / cols);
+        const int t0 = std::min(std::max(4, (npairs + chunks - 1) / chunks), npairs);
+        const int ctas = ((npairs + t0 - 1) / t0) * cols;
+        const int used = (ctas + slots - 1) / slots;
+        const int score = used * slots - ctas + 4 * waves * per_sm;
+        if (score < best_score) { best_score = score; best_t0 = t0; }
+      }
+      g.t0 = best_t0;
+      g.nb0 = (npairs + g.t0 - 1) / g.t0;
+      kernel<<<static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2), g.threads, smem, s>>>(
+          mv, nodal_src, interp_src, sign, fine, g, status);
+      return cudaGetLastError();
+    }
+  }
+  const int n2 = lv.ax[2].n;
+  const int64_t nrows = static_cast<int64_t>(lv.ax[0].n) * lv.ax[1].n;
+  const int64_t work = ((nrows + kRows - 1) / kRows) * ((n2 + kCols - 1) / kCols);
+  const int threads = 32 * ((std::min(n2, kCols) + 31) / 32);
+  const size_t smem = sizeof(T) * kRows * kCW;
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(work, 1 << 30));
+  const double nf = double(nrows) * n2;
+  const double ncs = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
+  TraceScope ts(sign < T(0) ? kKFinishDec : kKFinishRec, level,
+                sizeof(T) * (2 * nf + (nodal_src == interp_src ? 1 : 2) * ncs), s);
+  cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  finish_kernel<T><<<grid, threads, smem, s>>>(lv, nodal_src, interp_src, sign, fine);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_finish<float>(const LevelK<float>&, const float*, const float*, float,
+                                          float*, int, unsigned int*, cudaStream_t);
+template cudaError_t launch_finish<double>(const LevelK<double>&, const double*, const double*,
+                                           double, double*, int, unsigned int*, cudaStream_t);
+
+}  // namespace mgb

@@ -38,9 +38,18 @@ enum ApplyMode : int {
 //   dec = false: w = fine on coefficient nodes (fine holds u_mc)
 //   w = 0 on nodal nodes; F = (R0 x R1 x R2) w on the coarse grid; and the
 //   nodal values of `fine` are gathered into `coarse` (nc0 x nc1 x nc2).
+// `status` receives 1 if a bounded device-side wait gave up.
 template <typename T>
 cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
-                               int level, cudaStream_t s);
+                               int level, unsigned int* status, cudaStream_t s);
+
+// The marching TMA-staged form of the load vector (load_vector.cu), used for
+// 2D and 3D levels that fill the GPU.
+template <typename T>
+bool load_vector_march_supported(const LevelK<T>& lv);
+template <typename T>
+cudaError_t launch_load_vector_march(const LevelK<T>& lv, bool dec, const T* fine, T* coarse,
+                                     T* F, unsigned int* status, cudaStream_t s);
 
 // Batched Thomas solves of M_c along every axis (2, then 1, then 0), the
 // last one applying its result to B as `mode` says.
@@ -56,21 +65,25 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
 // interp_src = B_{l-1} (the interpolant's coarse values), sign = +1.
 template <typename T>
 cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* interp_src, T sign,
-                          T* fine, int level, cudaStream_t s);
+                          T* fine, int level, unsigned int* status, cudaStream_t s);
 
-// Quantization / dequantization / value range (quantize.cu).
+// Quantization / dequantization / value range (quantize.cu).  The field is
+// viewed as `rows` rows (j0, j1) of n2 contiguous elements; lev01 holds the
+// level of each row, lev2 that of each column.
 struct LevelTable {
-  double q[48];  // bin width 2 tau_l per level
+  double q[48];   // bin width 2 tau_l per level
+  float rq[48];   // fl32(1 / q_l), or NaN where that is not a normal float
+  float qf[48];   // fl32(q_l)
+  float dqf[48];  // fl32(q_l - fl32(q_l))
 };
 template <typename T>
-cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev0,
-                            const uint8_t* lev1, const uint8_t* lev2, int64_t n0, int64_t n1,
-                            int64_t n2, int stop_level, const LevelTable& tab,
-                            unsigned int* flags, cudaStream_t s);
+cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev01,
+                            const uint8_t* lev2, int64_t rows, int64_t n2, int stop_level,
+                            const LevelTable& tab, unsigned int* flags, cudaStream_t s);
 template <typename T>
-cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* lev0,
-                              const uint8_t* lev1, const uint8_t* lev2, int64_t n0, int64_t n1,
-                              int64_t n2, int stop_level, const LevelTable& tab, cudaStream_t s);
+cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* lev01,
+                              const uint8_t* lev2, int64_t rows, int64_t n2, int stop_level,
+                              const LevelTable& tab, cudaStream_t s);
 template <typename T>
 cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigned int* flags,
                           double* result, cudaStream_t s);

@@ -241,6 +241,10 @@ int build_host_plan(int ndim, const int64_t* dims, const double* const* coords, 
     for (int l = L - 1; l >= 0; --l)
       for (int64_t j : idx[l][a]) lv[j] = static_cast<uint8_t>(l);
   }
+  p.lev01.resize(static_cast<size_t>(p.dims3[0] * p.dims3[1]));
+  for (int64_t j0 = 0; j0 < p.dims3[0]; ++j0)
+    for (int64_t j1 = 0; j1 < p.dims3[1]; ++j1)
+      p.lev01[j0 * p.dims3[1] + j1] = std::max(p.lev[0][j0], p.lev[1][j1]);
   return MGARD_OK;
 }
 

@@ -39,6 +39,7 @@ struct HostPlan {
   std::vector<std::array<int64_t, 3>> shape;  // [L+1] level shapes (padded)
   std::vector<std::array<AxisTables, 3>> ax;  // [L+1]; entry l = transition l -> l-1
   std::array<std::vector<uint8_t>, 3> lev;    // per finest index: least level containing it
+  std::vector<uint8_t> lev01;                 // per finest row (j0, j1): max(lev[0][j0], lev[1][j1])
   std::vector<double> knorm;                  // [L+1] bound on |K_l|_inf (entry 0 unused)
   std::vector<double> coords_key;             // coordinates as given (for the plan cache)
   int64_t count() const { return dims3[0] * dims3[1] * dims3[2]; }

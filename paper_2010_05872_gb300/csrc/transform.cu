@@ -1,9 +1,7 @@
-// sm_103a kernels of one level transition l -> l-1 of the multilevel
-// transform (Section 2): load vector (coefficients, mass multiply and
-// restriction fused, Section 5.2), batched tridiagonal solves (Section 5.3),
-// correction application, and the in-place finishing pass that writes the
-// coefficients of decomposition / the interpolant plus coefficients of
-// recomposition.
+// Generic tiled load-vector kernel of one level transition l -> l-1 (Section
+// 2 step 4, Section 5.2): coefficients, mass multiply and restriction fused
+// on a 3D tile staged in shared memory.  Used for 1D levels and for levels
+// too small or too wide for the marching kernel of load_vector.cu.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -164,140 +162,20 @@ load_vector_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict__ coa
   }
 }
 
-// ---------------------------------------------------------------------------
-// Tridiagonal solves.  Forward: y_k = (f_k - a_k y_{k-1}) m_k; backward:
-// x_k = y_k - c'_k x_{k+1} (Thomas with precomputed factors).
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void apply_x(T* F, T* B, int64_t idx, T x, int mode) {
-  if (mode == kApplyNone) {
-    F[idx] = x;
-  } else if (mode == kApplyDecompose) {
-    const T old = B[idx];
-    B[idx] = old + x;
-    F[idx] = old;
-  } else {
-    B[idx] = B[idx] - x;
-  }
-}
-
-// Lines along a strided axis: element k of line (outer, inner) sits at
-// outer * nc * stride + k * stride + inner.  One thread per line; adjacent
-// threads take adjacent `inner`, so every step is a coalesced row access.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-solve_strided_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t outer,
-                     int64_t stride, int mode) {
-  const int64_t line = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (line >= outer * stride) return;
-  const int64_t o = line / stride, in = line - o * stride;
-  const int nc = ax.nc;
-  const int64_t base = o * nc * stride + in;
-  T y = T(0);
-  for (int k = 0; k < nc; ++k) {
-    const int64_t idx = base + k * stride;
-    y = (F[idx] - ax.ta[k] * y) * ax.tm[k];
-    F[idx] = y;
-  }
-  T x = T(0);
-  for (int k = nc - 1; k >= 0; --k) {
-    const int64_t idx = base + k * stride;
-    x = F[idx] - ax.tc[k] * x;
-    apply_x(F, B, idx, x, mode);
-  }
-}
-
-// Lines along the contiguous axis: a CTA stages `rows` whole lines in shared
-// memory with coalesced loads, one thread per line solves in place (row
-// pitch nc|1 keeps the threads on distinct banks), then stores.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-solve_contig_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines,
-                    int rows, int mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);
-  const int nc = ax.nc, pitch = nc | 1;
-  const int64_t first = static_cast<int64_t>(blockIdx.x) * rows;
-  const int64_t left = nlines - first;
-  const int nr = static_cast<int>(left < rows ? left : rows);
-  const int64_t base = first * nc;
-  for (int i = threadIdx.x; i < nr * nc; i += blockDim.x) {
-    const int r = i / nc, k = i - r * nc;
-    s[r * pitch + k] = F[base + i];
-  }
-  __syncthreads();
-  if (threadIdx.x < nr) {
-    T* l = s + threadIdx.x * pitch;
-    T y = T(0);
-    for (int k = 0; k < nc; ++k) {
-      y = (l[k] - ax.ta[k] * y) * ax.tm[k];
-      l[k] = y;
-    }
-    T x = T(0);
-    for (int k = nc - 1; k >= 0; --k) {
-      x = l[k] - ax.tc[k] * x;
-      l[k] = x;
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nr * nc; i += blockDim.x) {
-    const int r = i / nc, k = i - r * nc;
-    apply_x(F, B, base + i, s[r * pitch + k], mode);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Finishing pass: one thread per fine node, rows along the contiguous axis.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-finish_kernel(LevelK<T> lv, const T* __restrict__ nodal_src, const T* __restrict__ interp_src,
-              T sign, T* __restrict__ fine) {
-  const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
-  const int c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
-  const int64_t nrows = static_cast<int64_t>(n0) * n1;
-  for (int64_t rr = blockIdx.y; rr < nrows; rr += gridDim.y) {
-    const int j0 = static_cast<int>(rr / n1), j1 = static_cast<int>(rr - static_cast<int64_t>(j0) * n1);
-    const bool q0 = is_coef(j0, n0), q1 = is_coef(j1, n1);
-    const int64_t row = rr * n2;
-    // Coarse rows of the (up to 4) corner lines of this fine row.
-    const int a0 = q0 ? (j0 - 1) >> 1 : nodal_k(j0, n0, lv.ax[0].nc);
-    const int b0 = q0 ? (j0 + 1) >> 1 : a0;
-    const int a1 = q1 ? (j1 - 1) >> 1 : nodal_k(j1, n1, c1);
-    const int b1 = q1 ? (j1 + 1) >> 1 : a1;
-    const T wl0 = q0 ? lv.ax[0].iwl[j0] : T(1), wr0 = q0 ? lv.ax[0].iwr[j0] : T(0);
-    const T wl1 = q1 ? lv.ax[1].iwl[j1] : T(1), wr1 = q1 ? lv.ax[1].iwr[j1] : T(0);
-    const int64_t r00 = (static_cast<int64_t>(a0) * c1 + a1) * c2;
-    const int64_t r01 = (static_cast<int64_t>(a0) * c1 + b1) * c2;
-    const int64_t r10 = (static_cast<int64_t>(b0) * c1 + a1) * c2;
-    const int64_t r11 = (static_cast<int64_t>(b0) * c1 + b1) * c2;
-    for (int j2 = blockIdx.x * blockDim.x + threadIdx.x; j2 < n2; j2 += gridDim.x * blockDim.x) {
-      const bool q2 = is_coef(j2, n2);
-      if (!(q0 || q1 || q2)) {
-        fine[row + j2] = nodal_src[r00 + nodal_k(j2, n2, c2)];
-        continue;
-      }
-      const int a2 = q2 ? (j2 - 1) >> 1 : nodal_k(j2, n2, c2);
-      const int b2 = q2 ? (j2 + 1) >> 1 : a2;
-      const T wl2 = q2 ? lv.ax[2].iwl[j2] : T(1), wr2 = q2 ? lv.ax[2].iwr[j2] : T(0);
-      T v = wl0 * wl1 * (interp_src[r00 + a2] * wl2 + (q2 ? wr2 * interp_src[r00 + b2] : T(0)));
-      if (q1) v += wl0 * wr1 * (interp_src[r01 + a2] * wl2 + (q2 ? wr2 * interp_src[r01 + b2] : T(0)));
-      if (q0) {
-        v += wr0 * wl1 * (interp_src[r10 + a2] * wl2 + (q2 ? wr2 * interp_src[r10 + b2] : T(0)));
-        if (q1) v += wr0 * wr1 * (interp_src[r11 + a2] * wl2 + (q2 ? wr2 * interp_src[r11 + b2] : T(0)));
-      }
-      fine[row + j2] = fine[row + j2] + sign * v;
-    }
-  }
-}
-
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
-                               int level, cudaStream_t s) {
+                               int level, unsigned int* status, cudaStream_t s) {
+  const double nfine = double(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
+  const double ncoarse = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
+  if (load_vector_march_supported(lv)) {
+    TraceScope ts(dec ? kKLoadVectorDec : kKLoadVectorRec, level,
+                  sizeof(T) * (nfine + 2 * ncoarse), s);
+    return launch_load_vector_march(lv, dec, fine, coarse, F, status, s);
+  }
   const Tile t = pick_tile(lv);
   const int tk0 = lv.ax[0].n == 1 ? 1 : t.t0, tk1 = lv.ax[1].n == 1 ? 1 : t.t1, tk2 = t.t2;
   const int S0 = region(tk0, lv.ax[0].n), S1 = region(tk1, lv.ax[1].n), S2 = region(tk2, lv.ax[2].n);
@@ -320,65 +198,11 @@ cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* 
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int level,
-                          cudaStream_t s) {
-  const int64_t c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
-  int last = 0;
-  while (lv.ax[last].n == 1) ++last;  // lowest active axis is solved last
-  for (int a = 2; a >= last; --a) {
-    const int m = (a == last) ? mode : kApplyNone;
-    const double passes = m == kApplyDecompose ? 4.0 : m == kApplyRecompose ? 3.0 : 2.0;
-    TraceScope ts(a == 2 ? kKSolveContig : kKSolveStrided, level,
-                  sizeof(T) * passes * double(c0) * c1 * c2, s);
-    if (a == 2) {
-      const int64_t nlines = c0 * c1;
-      const size_t per_row = sizeof(T) * static_cast<size_t>(c2 | 1);
-      int rows = static_cast<int>(std::min<size_t>(64, (96 * 1024) / per_row));
-      rows = std::max(rows, 1);
-      const size_t smem = per_row * rows;
-      cudaFuncSetAttribute(solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
-      solve_contig_kernel<T><<<ceil_div(nlines, rows), kThreads, smem, s>>>(lv.ax[2], F, B, nlines,
-                                                                             rows, m);
-    } else {
-      const int64_t outer = (a == 0) ? 1 : c0;
-      const int64_t stride = (a == 0) ? c1 * c2 : c2;
-      solve_strided_kernel<T><<<ceil_div(outer * stride, kThreads), kThreads, 0, s>>>(
-          lv.ax[a], F, B, outer, stride, m);
-    }
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-template <typename T>
-cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* interp_src, T sign,
-                          T* fine, int level, cudaStream_t s) {
-  const int n2 = lv.ax[2].n;
-  const int bx = static_cast<int>(std::min<int64_t>(ceil_div(n2, kThreads), 64));
-  const int64_t nrows = static_cast<int64_t>(lv.ax[0].n) * lv.ax[1].n;
-  dim3 grid(bx, static_cast<unsigned>(std::min<int64_t>(nrows, 65535)));
-  const double nf = double(nrows) * n2;
-  const double ncs = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
-  TraceScope ts(sign < T(0) ? kKFinishDec : kKFinishRec, level,
-                sizeof(T) * (2 * nf + (nodal_src == interp_src ? 1 : 2) * ncs), s);
-  finish_kernel<T><<<grid, kThreads, 0, s>>>(lv, nodal_src, interp_src, sign, fine);
-  return cudaGetLastError();
-}
-
 template cudaError_t launch_load_vector<float>(const LevelK<float>&, bool, const float*, float*,
-                                               float*, int, cudaStream_t);
+                                               float*, int, unsigned int*, cudaStream_t);
 template cudaError_t launch_load_vector<double>(const LevelK<double>&, bool, const double*,
-                                                double*, double*, int, cudaStream_t);
-template cudaError_t launch_solves<float>(const LevelK<float>&, float*, float*, ApplyMode, int,
-                                          cudaStream_t);
-template cudaError_t launch_solves<double>(const LevelK<double>&, double*, double*, ApplyMode, int,
-                                           cudaStream_t);
-template cudaError_t launch_finish<float>(const LevelK<float>&, const float*, const float*, float,
-                                          float*, int, cudaStream_t);
-template cudaError_t launch_finish<double>(const LevelK<double>&, const double*, const double*,
-                                           double, double*, int, cudaStream_t);
+                                                double*, double*, int, unsigned int*, cudaStream_t);
+
+
 
 }  // namespace mgb

@@ -65,6 +65,9 @@ CASES = [
     ((1025, 33), "u", 0), ((9, 9, 9), "u", 0), ((5, 5, 5), "u", 0), ((10, 7, 12), "g", 0),
     ((17, 9, 6), "u", 1), ((33, 33, 33), "z", 0), ((70, 45, 133), "g", 0), ((65, 65, 65), "u", 0),
     ((40, 65, 100), "z", 2), ((100, 50, 4), "u", 0),
+    # Levels of at least 2^17 nodes take the marching kernels: 2D with rows
+    # in one chunk and in several, 3D with even axes, rows too wide to march.
+    ((400, 1500), "g", 0), ((1030, 258), "u", 0), ((66, 64, 62), "g", 0), ((34, 40, 600), "u", 1),
 ]
 
 
@@ -261,3 +264,58 @@ def test_full_size_nonuniform_500x500x100(cuda, stop):
     rec = gpu_recompose(torch, B.dequantize(labels, tau, torch.float32, coords, stop), coords, stop)
     err = (rec.double() - torch.from_numpy(u).cuda().double()).abs().max().item()
     assert err <= tau
+
+
+# --------------------------------------------- quantizer rounding edges ---
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+def test_quantize_rounding_boundaries(cuda, dtype):
+    """Coefficients placed on, and a few ulps around, the half-integer bin
+    boundaries of every level (where the FP32 fast path must defer to the
+    FP64 division), plus huge and tiny magnitudes: labels equal the oracle's."""
+    torch = cuda
+    dims = (4097,)
+    H = O.Hierarchy(dims)
+    taus = B.mgard_level_tolerances(dims, None, 0, 0.37)
+    lev = O.node_levels(H)
+    q = 2.0 * taus[lev]
+    rng = np.random.default_rng(3)
+    k = rng.integers(-2 ** 21, 2 ** 21, size=dims).astype(np.float64)
+    k[::7] = rng.integers(-40, 40, size=k[::7].shape)
+    base = (k + np.where(k >= 0, 0.5, -0.5)) * q
+    x = base.astype(dtype)
+    steps = rng.integers(-3, 4, size=dims)
+    for s in range(1, 4):
+        sel = steps == s
+        x[sel] = np.nextafter(x[sel], np.array(np.inf, dtype=dtype))
+        sel = steps == -s
+        x[sel] = np.nextafter(x[sel], np.array(-np.inf, dtype=dtype))
+    x[::11] = (rng.standard_normal(x[::11].shape) * 1e-30).astype(dtype)
+    x[::13] = (rng.standard_normal(x[::13].shape) * q[::13] * 3e5).astype(dtype)
+    xt = torch.from_numpy(x).cuda()
+    labels, t2 = B.quantize(xt, 0.37)
+    exp = O.quantize(x.astype(np.float64), H, 0, t2)
+    assert np.array_equal(labels.cpu().numpy(), exp)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+def test_dequantize_exact_products(cuda, dtype):
+    """label * q rounded to FP64 and then to the element type, for labels
+    from 0 to 2^45 in magnitude and tolerances that put results from the
+    subnormal to the overflow range of FP32: bit-exact with the oracle."""
+    torch = cuda
+    dims = (8193,)
+    H = O.Hierarchy(dims)
+    lev = O.node_levels(H)
+    rng = np.random.default_rng(4)
+    mags = rng.integers(0, 46, size=dims)
+    labels = (rng.integers(0, 2 ** 62, size=dims) >> (62 - mags)) * rng.choice([-1, 1], size=dims)
+    labels[::5] = rng.integers(-3, 4, size=labels[::5].shape)
+    for tau in (0.37, 1e-30, 3e-45, 1e25):
+        taus = B.mgard_level_tolerances(dims, None, 0, tau)
+        lt = torch.from_numpy(labels.astype(np.int64)).cuda()
+        got = B.dequantize(lt, tau, torch.float64 if dtype == np.float64 else torch.float32)
+        with np.errstate(over="ignore"):
+            exp = O.dequantize(labels, H, 0, taus, dtype=dtype)
+        g = got.cpu().numpy()
+        assert np.array_equal(g.view(np.uint8), exp.view(np.uint8)), tau
