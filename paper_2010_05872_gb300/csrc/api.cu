@@ -71,6 +71,8 @@ void fill_levels(DevPlan& p, const std::vector<std::vector<size_t>>& offs, char*
       k.ta = reinterpret_cast<const T*>(base + o[3]);
       k.tm = reinterpret_cast<const T*>(base + o[4]);
       k.tc = reinterpret_cast<const T*>(base + o[5]);
+      k.xd = reinterpret_cast<const T*>(base + o[6]);
+      k.xr = reinterpret_cast<const T*>(base + o[7]);
       k.n = t.n;
       k.nc = t.nc;
     }
@@ -92,6 +94,8 @@ int upload(DevPlan& p) {
       o.push_back(reserve(sizeof(T) * t.ta.size()));
       o.push_back(reserve(sizeof(T) * t.tm.size()));
       o.push_back(reserve(sizeof(T) * t.tc.size()));
+      o.push_back(reserve(sizeof(T) * t.xd.size()));
+      o.push_back(reserve(sizeof(T) * t.xr.size()));
     }
   size_t lev_off[3];
   for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
@@ -107,6 +111,7 @@ int upload(DevPlan& p) {
       const auto& o = offs[l * 3 + a];
       put(o[0], t.iwl); put(o[1], t.iwr); put(o[2], t.rw);
       put(o[3], t.ta); put(o[4], t.tm); put(o[5], t.tc);
+      put(o[6], t.xd); put(o[7], t.xr);
     }
   for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
   std::memcpy(stage.data() + lev01_off, h.lev01.data(), h.lev01.size());

@@ -229,9 +229,11 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
 
   const uint64_t flim = (static_cast<uint64_t>(n0) * n1 * n2 * sizeof(T)) & ~15ull;
   const uint64_t clim = (static_cast<uint64_t>(c0) * c1 * c2 * sizeof(T)) & ~15ull;
-  // One region [e0, e0 + len) of `src` into dst (16-byte-aligned superset by
-  // bulk copy, elements past the last whole 16 bytes of the array by plain
-  // loads); returns the bulk bytes.
+  // Copies are issued by thread 0 alone.  One region [e0, e0 + len) of
+  // `src` into dst: the 16-byte-aligned superset by bulk copy, and the at
+  // most 15 bytes past the last whole 16 bytes of the array by plain loads
+  // (visible to the CTA after the barrier that ends the wait).  Returns the
+  // bulk bytes.
   auto region = [&](const T* src, uint64_t lim, uint64_t e0, int len, T* dst, int* shift_slot,
                     uint64_t* bar, bool count_only) -> unsigned {
     const uint64_t sb = e0 * sizeof(T), eb = sb + static_cast<uint64_t>(len) * sizeof(T);
@@ -241,21 +243,18 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
     const unsigned bytes = bb > ab ? static_cast<unsigned>(bb - ab) : 0u;
     if (count_only) return bytes;
     const int shift = static_cast<int>((sb - ab) / sizeof(T));
-    if (tid == 0) {
-      *shift_slot = shift;
-      if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(src) + ab, bytes, bar);
-    }
-    const uint64_t tail0 = bb > sb ? bb : sb;
-    for (uint64_t x = tail0 + tid * sizeof(T); x < eb; x += blockDim.x * sizeof(T))
+    *shift_slot = shift;
+    if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(src) + ab, bytes, bar);
+    for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
       dst[shift + static_cast<int>((x - sb) / sizeof(T))] = src[x / sizeof(T)];
     return bytes;
   };
   // Stage for plane pair m: fine planes 2m, 2m + 1, coarse plane m + 1 and,
-  // for the first pair, coarse plane m.
+  // for the first pair, coarse plane m (thread 0 only).
   auto issue = [&](int m, int stage) {
     unsigned bytes = 0;
     for (int pass = 0; pass < 2; ++pass) {
-      if (pass == 1 && tid == 0) mbar_arrive_expect_tx(&bars[stage], bytes);
+      if (pass == 1) mbar_arrive_expect_tx(&bars[stage], bytes);
       for (int w = 0; w < 2; ++w) {
         const int j0 = 2 * m + w;
         if (j0 >= n0) continue;
@@ -311,7 +310,7 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
   unsigned phases = 0u;   // bit i: parity to wait for on bars[i]
   unsigned pending = 0u;  // bit i: bars[i] has copies in flight
   for (int i = 0; i < NS - 1 && M0 + i < M1; ++i) {
-    issue(M0 + i, i);
+    if (tid == 0) issue(M0 + i, i);
     pending |= 1u << i;
   }
   T A[R1M], B[R1M];
@@ -331,8 +330,10 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
     if (m + NS - 1 < M1) {
       // The stage refilled here was last read in the previous pair.
       const int st = (m - M0 + NS - 1) % NS;
-      if (tid == 0) fence_proxy_async();
-      issue(m + NS - 1, st);
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(m + NS - 1, st);
+      }
       pending |= 1u << st;
     }
     if (colact) {
@@ -351,8 +352,7 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
             const bool nodal = !q2 && !((q1mask >> r) & 1u);
             // Fully nodal rows sit on coarse row r / 2, or (0, 1) row r / 2 + 1.
             const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
-            dst[static_cast<int64_t>(r) * n2] =
-                nodal ? nsrc[static_cast<int64_t>(kr1) * c2] : fb[r * n2 + tid] + sign * A[r];
+            dst[r * n2] = nodal ? nsrc[kr1 * c2] : fb[r * n2 + tid] + sign * A[r];
           }
         }
       }
@@ -370,9 +370,7 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
           if (r < R1) {
             const bool nodal = !q0 && !q2 && !((q1mask >> r) & 1u);
             const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
-            dst[static_cast<int64_t>(r) * n2] =
-                nodal ? nsrc[static_cast<int64_t>(kr1) * c2]
-                      : fb[r * n2 + tid] + sign * (wl0 * A[r] + wr0 * B[r]);
+            dst[r * n2] = nodal ? nsrc[kr1 * c2] : fb[r * n2 + tid] + sign * (wl0 * A[r] + wr0 * B[r]);
           }
         }
       }

@@ -14,6 +14,8 @@ struct AxisK {
   const T* iwl;  // [n]  left interpolation weight of coefficient nodes
   const T* iwr;  // [n]  right interpolation weight of coefficient nodes
   const T* rw;   // [nc*5] load-vector weights on fine offsets -2..+2
+  const T* xd;   // [nc*3] R P on coarse nodes k-1, k, k+1 (decomposition)
+  const T* xr;   // [nc*3] R S on coarse nodes k-1, k, k+1 (recomposition)
   const T* ta;   // [nc] Thomas: sub-diagonal
   const T* tm;   // [nc] Thomas: reciprocal pivot
   const T* tc;   // [nc] Thomas: eliminated super-diagonal
@@ -87,6 +89,6 @@ cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* l
 template <typename T>
 cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigned int* flags,
                           double* result, cudaStream_t s);
-constexpr int kMinmaxBlocks = 608;  // 4 x 152 SMs
+constexpr int kMinmaxBlocks = 1216;  // 8 x 152 SMs
 
 }  // namespace mgb

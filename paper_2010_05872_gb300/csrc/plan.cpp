@@ -67,6 +67,35 @@ void build_axis(const std::vector<double>& x, AxisTables& t) {
       }
   }
 
+  // The load-vector rows taken against coarse nodes, tridiagonal on the
+  // coarse grid: xd = R P (P the prolongation: 1 on the node itself and the
+  // interpolation weights on its coefficient neighbours; the coarse mass
+  // matrix in the scaling of R) and xr = R S (S: the coarse node's own fine
+  // node only).  Entry 3k + d belongs to coarse node k - 1 + d.
+  t.xd.assign(static_cast<size_t>(nc) * 3, 0.0);
+  t.xr.assign(static_cast<size_t>(nc) * 3, 0.0);
+  for (int k = 0; k < nc; ++k) {
+    const int c = cpos(k, n);
+    for (int d = 0; d < 3; ++d) {
+      const int kk = k - 1 + d;
+      if (kk < 0 || kk >= nc) continue;
+      const int ck = cpos(kk, n);
+      double sd = 0.0, sr = 0.0;
+      for (int off = 0; off < 5; ++off) {
+        const int j = c + off - 2;
+        if (j < 0 || j >= n) continue;
+        double pj = 0.0;  // P[j, kk]
+        if (j == ck) pj = 1.0;
+        else if (is_coef(j, n) && j - 1 == ck) pj = t.iwl[j];
+        else if (is_coef(j, n) && j + 1 == ck) pj = t.iwr[j];
+        sd += t.rw[static_cast<size_t>(k) * 5 + off] * pj;
+        if (j == ck) sr += t.rw[static_cast<size_t>(k) * 5 + off];
+      }
+      t.xd[static_cast<size_t>(k) * 3 + d] = sd;
+      t.xr[static_cast<size_t>(k) * 3 + d] = sr;
+    }
+  }
+
   // Coarse mass matrix on the coarse coordinates and its Thomas factors.
   std::vector<double> xc(nc), a(nc, 0.0), b(nc, 0.0), cu(nc, 0.0);
   for (int k = 0; k < nc; ++k) xc[k] = x[cpos(k, n)];
@@ -133,6 +162,8 @@ void padded_axis(AxisTables& t) {
   t.n = 1; t.nc = 1;
   t.iwl.assign(1, 0.0); t.iwr.assign(1, 0.0);
   t.rw = {0.0, 0.0, 1.0, 0.0, 0.0};
+  t.xd = {0.0, 1.0, 0.0};
+  t.xr = {0.0, 1.0, 0.0};
   t.ta.assign(1, 0.0); t.tm.assign(1, 1.0); t.tc.assign(1, 0.0);
   t.rmax = 1.0; t.smax = 1.0; t.dmax = 0.0;
 }

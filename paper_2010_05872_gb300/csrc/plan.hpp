@@ -28,6 +28,7 @@ struct AxisTables {
   int nc = 1;  // coarse nodes, n / 2 + 1
   std::vector<double> iwl, iwr;    // [n]
   std::vector<double> rw;          // [nc * 5]
+  std::vector<double> xd, xr;      // [nc * 3] R P and R S on coarse nodes k-1, k, k+1
   std::vector<double> ta, tm, tc;  // [nc]
   double rmax = 1, smax = 1, dmax = 0;  // row-sum maxima of |M_c^{-1} P^T M_f|
 };

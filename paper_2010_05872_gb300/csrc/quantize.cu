@@ -159,7 +159,7 @@ __device__ __noinline__ float dequantize_f64_route(long long k, double q) {
 // step and through FP64 (whose rounding moves it by at most 2^-53 |r|).
 // Returns false near a midpoint or outside [2^-100, FLT_MAX].
 __device__ __forceinline__ bool deq_f32_fast(long long k, float qf, float dqf, float& out) {
-  const float K = static_cast<float>(k < 0 ? -k : k);
+  const float K = static_cast<float>(static_cast<int>(k < 0 ? -k : k));  // exact: |k| < 2^24
   const float p = __fmul_rn(K, qf);
   const float e = __fmaf_rn(K, qf, -p);
   const float t = __fmaf_rn(K, dqf, e);
@@ -328,8 +328,23 @@ minmax_partial_kernel(const T* __restrict__ data, uint64_t count, double* __rest
   const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   uint64_t done = 0;
   if (VEC) {
+    // Four 16-byte loads of a thread in flight at a time.
     const uint64_t ngroups = count / 4;
-    for (uint64_t g = tid; g < ngroups; g += stride) {
+    uint64_t g = tid;
+    for (; g + 3 * stride < ngroups; g += 4 * stride) {
+      T v[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Vec4<T>::load(data + (g + i * stride) * 4, v[i]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          bad |= !finite_val(v[i][u]);
+          mn = fmin(mn, v[i][u]);
+          mx = fmax(mx, v[i][u]);
+        }
+    }
+    for (; g < ngroups; g += stride) {
       T v[4];
       Vec4<T>::load(data + g * 4, v);
 #pragma unroll
@@ -393,9 +408,16 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 }  // namespace
 
-unsigned row_blocks(int64_t nrows, int64_t n2, int threads) {
+// Row-tile kernels run as a persistent grid: as many CTAs as fit on the
+// 152 SMs at once, each looping over row groups, so no CTA is launched for
+// a few KB of work.
+template <typename K>
+unsigned row_blocks(K kernel, int64_t nrows, int64_t n2, int threads) {
   const int64_t work = ((nrows + kQRows - 1) / kQRows) * ((n2 + threads - 1) / threads);
-  return static_cast<unsigned>(work < (1 << 30) ? work : (1 << 30));
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  const int64_t cap = 152 * static_cast<int64_t>(std::max(per_sm, 1));
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min(work, cap)));
 }
 
 int row_threads(int64_t n2) {
@@ -410,7 +432,7 @@ cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev
   const uint64_t count = static_cast<uint64_t>(rows) * n2;
   TraceScope ts(kKQuantize, -1, double(count) * (sizeof(T) + 8), s);
   const int threads = row_threads(n2);
-  quantize_kernel<T><<<row_blocks(rows, n2, threads), threads, 0, s>>>(
+  quantize_kernel<T><<<row_blocks(quantize_kernel<T>, rows, n2, threads), threads, 0, s>>>(
       coeffs, labels, lev01, lev2, n2, rows, stop_level, tab, flags);
   return cudaGetLastError();
 }
@@ -422,7 +444,7 @@ cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* l
   const uint64_t count = static_cast<uint64_t>(rows) * n2;
   TraceScope ts(kKDequantize, -1, double(count) * (sizeof(T) + 8), s);
   const int threads = row_threads(n2);
-  dequantize_kernel<T><<<row_blocks(rows, n2, threads), threads, 0, s>>>(
+  dequantize_kernel<T><<<row_blocks(dequantize_kernel<T>, rows, n2, threads), threads, 0, s>>>(
       labels, coeffs, lev01, lev2, n2, rows, stop_level, tab);
   return cudaGetLastError();
 }
