@@ -349,8 +349,7 @@ def run_gpu(args, rank, world, local_rank):
     b_alg = 2 * 2 * 4 * sum(sizes)
     path_frac = b_alg / ((phase["decompose"] + phase["recompose"]) / args.steps * 1e-3) / 1e9 / peak
 
-    # The value-range scope launches two kernels (partial and final reduction).
-    launches = sum(r["launches"] * (2 if r["kernel"].startswith("minmax") else 1) for r in trace)
+    launches = B.mgard_trace_kernel_launches()
     kernels = sorted(({"kernel": r["kernel"], "level": r["level"], "launches": r["launches"],
                        "ms_per_step": r["total_ms"] / args.steps,
                        "gbs": r["bytes"] / (r["total_ms"] * 1e-3) / 1e9} for r in trace),

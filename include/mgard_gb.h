@@ -172,8 +172,13 @@ int mgard_release_plans(void);
  * level-free kernels) with the launch count, the summed device time in ms and
  * the summed algorithmic bytes (each input read once, each output written
  * once); up to max_rows rows are written, *rows_out receives the number of
- * rows available.  mgard_trace_kernel_name names a kind. */
+ * rows available; a row's launch count is the number of traced calls of
+ * that kind (a call can launch more than one kernel).
+ * mgard_trace_kernel_name names a kind.  mgard_trace_kernel_launches returns
+ * the number of kernels this library launched while tracing was on since the
+ * last mgard_trace_enable(1). */
 int mgard_trace_enable(int on);
+int64_t mgard_trace_kernel_launches(void);
 int mgard_trace_read(int max_rows, int* kind, int* level, int64_t* launches, double* total_ms,
                      double* bytes, int* rows_out);
 const char* mgard_trace_kernel_name(int kind);

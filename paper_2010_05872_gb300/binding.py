@@ -61,6 +61,7 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
                                         ctypes.POINTER(ctypes.c_int)]),
     "mgard_trace_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "mgard_trace_kernel_launches": (ctypes.c_int64, []),
 }
 
 _lib = None
@@ -216,6 +217,11 @@ def mgard_release_plans() -> int:
 
 def mgard_trace_enable(on: bool) -> int:
     return lib().mgard_trace_enable(1 if on else 0)
+
+
+def mgard_trace_kernel_launches() -> int:
+    """Kernels launched by the library while tracing was on."""
+    return int(lib().mgard_trace_kernel_launches())
 
 
 def mgard_trace_read():

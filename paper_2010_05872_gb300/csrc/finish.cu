@@ -154,7 +154,7 @@ finish_kernel(LevelK<T> lv, const T* __restrict__ nodal_src, const T* __restrict
 // thread per fine column: its axis-2 data stays in registers, rows are walked
 // with uniform row data, each output is one coalesced store.
 // ---------------------------------------------------------------------------
-constexpr int kFMaxThreads = 640;
+constexpr int kFMaxThreads = 576;
 
 // Pipeline depth and coarse rows per CTA along axis 1, per element type:
 // NS stages of (two fine planes, one coarse plane) with NS - 1 in flight.
@@ -162,7 +162,7 @@ template <typename T>
 struct FinishCfg;
 template <>
 struct FinishCfg<float> {
-  static constexpr int NS = 3, T1 = 4;
+  static constexpr int NS = 2, T1 = 4;
 };
 template <>
 struct FinishCfg<double> {
@@ -189,7 +189,7 @@ struct FinishGeom {
 // next coarse plane (B) along axis 0.  A nodal node takes its coarse value
 // exactly: weights (1, 0) or (0, 1), never a rounded mix.
 template <typename T, int NS, int T1C>
-__global__ void __launch_bounds__(kFMaxThreads)
+__global__ void __launch_bounds__(kFMaxThreads, sizeof(T) == 4 ? 2 : 1)
 finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
                     const T* __restrict__ interp_src, T sign, T* __restrict__ fine,
                     FinishGeom g, unsigned int* __restrict__ status) {
@@ -199,6 +199,7 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
   __shared__ __align__(8) uint64_t bars[NS];
   __shared__ int s_fshift[2 * NS];  // fine buffers: stage x plane
   __shared__ int s_cshift[NC];      // coarse ring
+  __shared__ int s_nshift[NC];      // ring of nodal-source planes (decomposition)
 
   const int tid = threadIdx.x;
   const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
@@ -220,6 +221,10 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
 
   T* fbuf = reinterpret_cast<T*>(smem_raw);                // 2 NS x FBUF
   T* cbuf = fbuf + 2 * NS * static_cast<size_t>(g.FBUF);   // NC x CBUF
+  T* nbuf = cbuf + NC * static_cast<size_t>(g.CBUF);       // NC x CBUF when sep
+  // Decomposition takes nodal values from a second coarse array; in
+  // recomposition they are the interpolant's own coarse values.
+  const bool sep = nodal_src != interp_src;
 
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
@@ -269,6 +274,9 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
         const int len = (R1c - 1) * c2 + kw;
         bytes += region(interp_src, clim, e0, len, cbuf + static_cast<size_t>(cm % NC) * g.CBUF,
                         &s_cshift[cm % NC], &bars[stage], pass == 0);
+        if (sep)
+          bytes += region(nodal_src, clim, e0, len, nbuf + static_cast<size_t>(cm % NC) * g.CBUF,
+                          &s_nshift[cm % NC], &bars[stage], pass == 0);
       }
     }
   };
@@ -280,17 +288,21 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
   const int kn2 = colact ? nodal_k(j2, n2, c2) : 0;
   const int kl = (q2 ? (j2 >> 1) : kn2) - klo2, kr = q2 ? kl + 1 : kl;
   const T wl2 = q2 ? lv.ax[2].iwl[j2] : T(1), wr2 = q2 ? lv.ax[2].iwr[j2] : T(0);
+  const int kcol = kn2 - klo2;  // staged coarse column of a nodal column
   // Row data (axis 1, the same for every thread).  Even rows are nodal with
   // coarse row r / 2; odd row r mixes coarse rows r / 2 and r / 2 + 1, except
   // a last fine row n1 - 1 that is nodal (even n1): weights (0, 1).
-  T wl1[T1C], wr1[T1C];
+  // The weights sit in shared memory (read after the first wait's barrier).
+  __shared__ T s_wl1[T1C], s_wr1[T1C];
   unsigned q1mask = 0u;  // bit r: fine row r is a coefficient row
 #pragma unroll
   for (int i = 0; i < T1C; ++i) {
     const int j1 = r1lo + 2 * i + 1;
     const bool q = 2 * i + 1 < R1 && is_coef(j1, n1);
-    wl1[i] = q ? lv.ax[1].iwl[j1] : T(0);
-    wr1[i] = q ? lv.ax[1].iwr[j1] : T(1);
+    if (tid == i) {
+      s_wl1[i] = q ? lv.ax[1].iwl[j1] : T(0);
+      s_wr1[i] = q ? lv.ax[1].iwr[j1] : T(1);
+    }
     if (q) q1mask |= 1u << (2 * i + 1);
   }
   // Interpolant of coarse plane `cm` at this column and every owned fine row.
@@ -303,7 +315,7 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
 #pragma unroll
     for (int i = 0; i < T1C; ++i) {
       out[2 * i] = i2[i];
-      out[2 * i + 1] = (i + 1 < RCM) ? wl1[i] * i2[i] + wr1[i] * i2[i + 1] : i2[i];
+      out[2 * i + 1] = s_wl1[i] * i2[i] + s_wr1[i] * i2[i + 1];
     }
   };
 
@@ -345,14 +357,15 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
         const int j0 = 2 * m;
         const T* fb = fbuf + static_cast<size_t>(2 * stage) * g.FBUF + s_fshift[2 * stage];
         T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo) * n2 + j2;
-        const T* nsrc = nodal_src + (static_cast<int64_t>(m) * c1 + k1lo) * c2 + kn2;
+        const T* nsrc = nbuf + static_cast<size_t>(m % NC) * g.CBUF + s_nshift[m % NC] + kcol;
 #pragma unroll
         for (int r = 0; r < R1M; ++r) {
           if (r < R1) {
             const bool nodal = !q2 && !((q1mask >> r) & 1u);
             // Fully nodal rows sit on coarse row r / 2, or (0, 1) row r / 2 + 1.
             const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
-            dst[r * n2] = nodal ? nsrc[kr1 * c2] : fb[r * n2 + tid] + sign * A[r];
+            const T v = A[r];
+            dst[r * n2] = nodal ? (sep ? nsrc[kr1 * c2] : v) : fb[r * n2 + tid] + sign * v;
           }
         }
       }
@@ -364,13 +377,15 @@ finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
         const T wl0 = q0 ? lv.ax[0].iwl[j0] : T(0), wr0 = q0 ? lv.ax[0].iwr[j0] : T(1);
         const T* fb = fbuf + static_cast<size_t>(2 * stage + 1) * g.FBUF + s_fshift[2 * stage + 1];
         T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo) * n2 + j2;
-        const T* nsrc = nodal_src + (static_cast<int64_t>(m + 1) * c1 + k1lo) * c2 + kn2;
+        const int mn = (m + 1) % NC;
+        const T* nsrc = nbuf + static_cast<size_t>(mn) * g.CBUF + s_nshift[mn] + kcol;
 #pragma unroll
         for (int r = 0; r < R1M; ++r) {
           if (r < R1) {
             const bool nodal = !q0 && !q2 && !((q1mask >> r) & 1u);
             const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
-            dst[r * n2] = nodal ? nsrc[kr1 * c2] : fb[r * n2 + tid] + sign * (wl0 * A[r] + wr0 * B[r]);
+            const T v = wl0 * A[r] + wr0 * B[r];
+            dst[r * n2] = nodal ? (sep ? nsrc[kr1 * c2] : v) : fb[r * n2 + tid] + sign * v;
           }
         }
       }
@@ -419,8 +434,9 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
       TraceScope ts(sign < T(0) ? kKFinishDec : kKFinishRec, level,
                     sizeof(T) * (2 * double(nf_all) + (nodal_src == interp_src ? 1 : 2) * ncs_all), s);
       constexpr int NS = FinishCfg<T>::NS;
-      const size_t smem = sizeof(T) * (2 * NS * static_cast<size_t>(g.FBUF) +
-                                       (NS + 1) * static_cast<size_t>(g.CBUF));
+      const size_t smem =
+          sizeof(T) * (2 * NS * static_cast<size_t>(g.FBUF) +
+                       (nodal_src == interp_src ? 1 : 2) * (NS + 1) * static_cast<size_t>(g.CBUF));
       auto kernel = finish_march_kernel<T, NS, FinishCfg<T>::T1>;
       cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem));

@@ -306,6 +306,104 @@ dequantize_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
   }
 }
 
+// Flat forms for aligned arrays: a thread takes vectors of 4 consecutive
+// elements (16-byte loads and stores), kQU vectors in flight, over a
+// persistent grid.  The row of element e is umulhi(e, M) with
+// M = ceil(2^64 / n2), exact for every e of the array (checked on the host);
+// the 4 elements of a vector span at most two rows (n2 >= 4).
+constexpr int kQU = 4;
+constexpr int kQThreads = 256;
+
+__device__ __forceinline__ void vec_levels(uint64_t e, uint64_t magic, uint32_t n2,
+                                           const uint8_t* __restrict__ lev01,
+                                           const uint8_t* __restrict__ lev2, int stop, int lv[4]) {
+  const uint64_t row = __umul64hi(e, magic);
+  const uint32_t col = static_cast<uint32_t>(e - row * n2);
+  const int la = max(static_cast<int>(__ldg(lev01 + row)), stop);
+  const int lb = (col + 3 >= n2) ? max(static_cast<int>(__ldg(lev01 + row + 1)), stop) : la;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uint32_t c = col + u;
+    const bool wrap = c >= n2;
+    if (wrap) c -= n2;
+    lv[u] = max(static_cast<int>(__ldg(lev2 + c)), wrap ? lb : la);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads)
+quantize_flat_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
+                     const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
+                     uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab,
+                     unsigned int* __restrict__ flags) {
+  __shared__ SmemTable st;
+  load_table(tab, st);
+  unsigned bad = 0;
+  const uint64_t step = static_cast<uint64_t>(gridDim.x) * kQThreads * kQU;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kQThreads * kQU + threadIdx.x;
+       base < nvec; base += step) {
+    T x[kQU][4];
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+      if (v < nvec) Vec4<T>::load(coeffs + 4 * v, x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+      if (v < nvec) {
+        int lv[4];
+        vec_levels(4 * v, magic, n2, lev01, lev2, stop, lv);
+        long long k[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) k[i] = quantize_one(x[u][i], st.q[lv[i]], st.rq[lv[i]], bad);
+        longlong2* out = reinterpret_cast<longlong2*>(labels + 4 * v);
+        out[0] = make_longlong2(k[0], k[1]);
+        out[1] = make_longlong2(k[2], k[3]);
+      }
+    }
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads)
+dequantize_flat_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
+                       const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
+                       uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab) {
+  __shared__ SmemTable st;
+  load_table(tab, st);
+  const uint64_t step = static_cast<uint64_t>(gridDim.x) * kQThreads * kQU;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kQThreads * kQU + threadIdx.x;
+       base < nvec; base += step) {
+    longlong2 k[kQU][2];
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+      if (v < nvec) {
+        const longlong2* in = reinterpret_cast<const longlong2*>(labels + 4 * v);
+        k[u][0] = in[0];
+        k[u][1] = in[1];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+      if (v < nvec) {
+        int lv[4];
+        vec_levels(4 * v, magic, n2, lev01, lev2, stop, lv);
+        const long long kk[4] = {k[u][0].x, k[u][0].y, k[u][1].x, k[u][1].y};
+        T y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          y[i] = dequantize_one(kk[i], st.q[lv[i]], st.qf[lv[i]], st.dqf[lv[i]],
+                                static_cast<T*>(nullptr));
+        Vec4<T>::store(coeffs + 4 * v, y);
+      }
+    }
+  }
+}
+
 // Block-wide min/max in the element type (exact), then FP64 partials;
 // non-finite elements are flagged and left out.
 template <typename T>
@@ -420,6 +518,28 @@ unsigned row_blocks(K kernel, int64_t nrows, int64_t n2, int threads) {
   return static_cast<unsigned>(std::max<int64_t>(1, std::min(work, cap)));
 }
 
+// M = ceil(2^64 / n2) gives row = umulhi(e, M) exactly while e (M n2 - 2^64)
+// < 2^64 for every element index e < count.
+bool flat_magic(uint64_t count, int64_t n2, uint64_t& magic) {
+  if (n2 < 4 || n2 > (int64_t(1) << 31)) return false;
+  const unsigned __int128 two64 = static_cast<unsigned __int128>(1) << 64;
+  const unsigned __int128 m = (two64 + static_cast<uint64_t>(n2) - 1) / static_cast<uint64_t>(n2);
+  if (m >> 64) return false;
+  const unsigned __int128 eps = m * static_cast<uint64_t>(n2) - two64;
+  if (eps != 0 && static_cast<unsigned __int128>(count) * eps >= two64) return false;
+  magic = static_cast<uint64_t>(m);
+  return true;
+}
+
+template <typename K>
+unsigned flat_blocks(K kernel, uint64_t nvec) {
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kQThreads, 0);
+  const uint64_t need = (nvec + uint64_t(kQThreads) * kQU - 1) / (uint64_t(kQThreads) * kQU);
+  const uint64_t cap = 152ull * static_cast<uint64_t>(std::max(per_sm, 1));
+  return static_cast<unsigned>(std::max<uint64_t>(1, std::min(need, cap)));
+}
+
 int row_threads(int64_t n2) {
   const int64_t t = 32 * ((std::min<int64_t>(n2, kQCols) + 31) / 32);
   return static_cast<int>(t < 64 ? 64 : t);
@@ -431,6 +551,23 @@ cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev
                             const LevelTable& tab, unsigned int* flags, cudaStream_t s) {
   const uint64_t count = static_cast<uint64_t>(rows) * n2;
   TraceScope ts(kKQuantize, -1, double(count) * (sizeof(T) + 8), s);
+  uint64_t magic = 0;
+  if (aligned16(coeffs) && aligned16(labels) && flat_magic(count, n2, magic)) {
+    const uint64_t nvec = count / 4;
+    if (nvec > 0)
+      quantize_flat_kernel<T><<<flat_blocks(quantize_flat_kernel<T>, nvec), kQThreads, 0, s>>>(
+          coeffs, labels, lev01, lev2, nvec, static_cast<uint32_t>(n2), magic, stop_level, tab,
+          flags);
+    if (count % 4 == 0) return cudaGetLastError();
+    // The last count % 4 elements: one row-tile pass over the last row
+    // would redo work, so the row-tile kernel takes the whole last row.
+    const int64_t r_last = rows - 1;
+    ts.more_kernels(1);
+    quantize_kernel<T><<<1, row_threads(n2), 0, s>>>(coeffs + r_last * n2, labels + r_last * n2,
+                                                    lev01 + r_last, lev2, n2, 1, stop_level, tab,
+                                                    flags);
+    return cudaGetLastError();
+  }
   const int threads = row_threads(n2);
   quantize_kernel<T><<<row_blocks(quantize_kernel<T>, rows, n2, threads), threads, 0, s>>>(
       coeffs, labels, lev01, lev2, n2, rows, stop_level, tab, flags);
@@ -443,6 +580,19 @@ cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* l
                               const LevelTable& tab, cudaStream_t s) {
   const uint64_t count = static_cast<uint64_t>(rows) * n2;
   TraceScope ts(kKDequantize, -1, double(count) * (sizeof(T) + 8), s);
+  uint64_t magic = 0;
+  if (aligned16(coeffs) && aligned16(labels) && flat_magic(count, n2, magic)) {
+    const uint64_t nvec = count / 4;
+    if (nvec > 0)
+      dequantize_flat_kernel<T><<<flat_blocks(dequantize_flat_kernel<T>, nvec), kQThreads, 0, s>>>(
+          labels, coeffs, lev01, lev2, nvec, static_cast<uint32_t>(n2), magic, stop_level, tab);
+    if (count % 4 == 0) return cudaGetLastError();
+    const int64_t r_last = rows - 1;
+    ts.more_kernels(1);
+    dequantize_kernel<T><<<1, row_threads(n2), 0, s>>>(labels + r_last * n2, coeffs + r_last * n2,
+                                                      lev01 + r_last, lev2, n2, 1, stop_level, tab);
+    return cudaGetLastError();
+  }
   const int threads = row_threads(n2);
   dequantize_kernel<T><<<row_blocks(dequantize_kernel<T>, rows, n2, threads), threads, 0, s>>>(
       labels, coeffs, lev01, lev2, n2, rows, stop_level, tab);
@@ -462,6 +612,7 @@ cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigne
   else
     minmax_partial_kernel<T, false><<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(
         data, static_cast<uint64_t>(count), partial, flags);
+  ts.more_kernels(1);
   minmax_final_kernel<<<1, kThreads, 0, s>>>(partial, static_cast<int>(blocks), result);
   return cudaGetLastError();
 }

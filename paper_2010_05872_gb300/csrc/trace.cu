@@ -20,6 +20,7 @@ struct Rec {
 };
 
 std::atomic<bool> g_on{false};
+std::atomic<int64_t> g_kernels{0};
 std::mutex g_tmu;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
@@ -55,12 +56,18 @@ const char* kernel_kind_name(int kind) {
 
 TraceScope::TraceScope(int kind, int level, double bytes, cudaStream_t s) : s_(s) {
   if (!g_on.load(std::memory_order_relaxed)) return;
+  on_ = true;
+  g_kernels.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_tmu);
   Rec r{kind, level, bytes, take_event(), take_event()};
   if (r.a == nullptr || r.b == nullptr) return;
   cudaEventRecord(r.a, s);
   slot_ = static_cast<int>(g_recs.size());
   g_recs.push_back(r);
+}
+
+void TraceScope::more_kernels(int n) {
+  if (on_) g_kernels.fetch_add(n, std::memory_order_relaxed);
 }
 
 TraceScope::~TraceScope() {
@@ -82,6 +89,7 @@ int mgard_trace_enable(int on) {
       cudaEventSynchronize(r.b);
     }
     recycle_all();
+    g_kernels.store(0);
   }
   g_on.store(on != 0);
   return MGARD_OK;
@@ -117,5 +125,7 @@ int mgard_trace_read(int max_rows, int* kind, int* level, int64_t* launches, dou
 }
 
 const char* mgard_trace_kernel_name(int kind) { return kernel_kind_name(kind); }
+
+int64_t mgard_trace_kernel_launches(void) { return g_kernels.load(); }
 
 }  // extern "C"

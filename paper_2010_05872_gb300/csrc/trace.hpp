@@ -29,9 +29,12 @@ class TraceScope {
   ~TraceScope();
   TraceScope(const TraceScope&) = delete;
   TraceScope& operator=(const TraceScope&) = delete;
+  // Count `n` more kernel launches in this scope (one is counted already).
+  void more_kernels(int n);
 
  private:
   int slot_ = -1;
+  bool on_ = false;
   cudaStream_t s_ = nullptr;
 };
 
