@@ -350,6 +350,9 @@ def run_gpu(args, rank, world, local_rank):
     path_frac = b_alg / ((phase["decompose"] + phase["recompose"]) / args.steps * 1e-3) / 1e9 / peak
 
     launches = B.mgard_trace_kernel_launches()
+    kinds = {}
+    for r in trace:
+        kinds[r["kernel"]] = kinds.get(r["kernel"], 0.0) + r["total_ms"] / args.steps
     kernels = sorted(({"kernel": r["kernel"], "level": r["level"], "launches": r["launches"],
                        "ms_per_step": r["total_ms"] / args.steps,
                        "gbs": r["bytes"] / (r["total_ms"] * 1e-3) / 1e9} for r in trace),
@@ -443,6 +446,7 @@ def run_gpu(args, rank, world, local_rank):
         "fp64": fp64,
         "linf_over_tau": linf,
         "top_kernels": kernels,
+        "kinds_ms_per_step": {k: round(v, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1])},
         "src_hash": src_hash(),
     }
     print(json.dumps(line))

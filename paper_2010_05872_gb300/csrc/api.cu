@@ -242,7 +242,7 @@ int run_decompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
   }
   for (int l = L; l > stop; --l) {
     MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, status, s));
-    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, status, s));
   }
   for (int l = stop + 1; l <= L; ++l)
     MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, status, s));
@@ -265,7 +265,7 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
   for (int l = L; l > stop; --l)
     MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], l, status, s));
   for (int l = stop + 1; l <= L; ++l) {
-    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, l, s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, l, status, s));
     MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], l, status, s));
   }
   return MGARD_OK;

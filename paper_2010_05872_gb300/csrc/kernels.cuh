@@ -57,7 +57,7 @@ cudaError_t launch_load_vector_march(const LevelK<T>& lv, bool dec, const T* fin
 // last one applying its result to B as `mode` says.
 template <typename T>
 cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int level,
-                          cudaStream_t s);
+                          unsigned int* status, cudaStream_t s);
 
 // In-place finishing pass over the level-l grid `fine`:
 //   nodal nodes       : fine <- nodal_src[k]

@@ -7,12 +7,23 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "tma.cuh"
 #include "trace.hpp"
 
 namespace mgb {
 namespace {
 
-constexpr int kChunk = 8;  // elements of a line loaded together (independent loads)
+// Elements of a line loaded together (independent loads in flight).
+template <typename T>
+struct Chunk;
+template <>
+struct Chunk<float> {
+  static constexpr int value = 32;
+};
+template <>
+struct Chunk<double> {
+  static constexpr int value = 16;
+};
 
 template <typename T>
 __device__ __forceinline__ void apply_x(T* F, T* B, int64_t idx, T x, T old_b, int mode) {
@@ -34,6 +45,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 solve_strided_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t outer,
                      int64_t stride, int mode) {
+  constexpr int kChunk = Chunk<T>::value;
   const int64_t line = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (line >= outer * stride) return;
   const int64_t o = line / stride, in = line - o * stride;
@@ -153,13 +165,105 @@ solve_contig_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t n
   }
 }
 
+// Contiguous lines of odd length, staged by one 1D TMA bulk copy: the rows
+// lines of a CTA are one contiguous range, copied as its enclosing 16-byte-
+// aligned range (the at most 15 bytes past the last whole 16 bytes of the
+// array by plain loads); with an odd pitch the threads' lines fall on
+// distinct banks.  The Thomas factors come to shared memory too; one thread
+// per line solves in place, then the range is written back with coalesced
+// stores.  The wait on the copy gives up after 2 s and records the failure
+// in `status`.
+template <typename T>
+__global__ void __launch_bounds__(128)
+solve_contig_tma_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines,
+                        int rows, int mode, unsigned int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_shift;
+  const int nc = ax.nc;
+  T* s_ta = reinterpret_cast<T*>(smem_raw);  // nc each
+  T* s_tm = s_ta + nc;
+  T* s_tc = s_tm + nc;
+  const int tpad = ((3 * nc * static_cast<int>(sizeof(T)) + 15) / 16) * 16;
+  T* s = reinterpret_cast<T*>(smem_raw + tpad);
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * rows;
+  const int nr = static_cast<int>(min(static_cast<int64_t>(rows), nlines - first));
+  const int total = nr * nc;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    const uint64_t lim = (static_cast<uint64_t>(nlines) * nc * sizeof(T)) & ~15ull;
+    const uint64_t sb = static_cast<uint64_t>(first) * nc * sizeof(T);
+    const uint64_t eb = sb + static_cast<uint64_t>(total) * sizeof(T);
+    const uint64_t ab = sb & ~15ull;
+    uint64_t bb = (eb + 15) & ~15ull;
+    if (bb > lim) bb = lim;
+    const int shift = static_cast<int>((sb - ab) / sizeof(T));
+    s_shift = shift;
+    const unsigned bytes = bb > ab ? static_cast<unsigned>(bb - ab) : 0u;
+    mbar_arrive_expect_tx(&bar, bytes);
+    if (bytes) tma_bulk_g2s(s, reinterpret_cast<const char*>(F) + ab, bytes, &bar);
+    for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
+      s[shift + static_cast<int>((x - sb) / sizeof(T))] = F[x / sizeof(T)];
+  }
+  for (int k = tid; k < nc; k += blockDim.x) {
+    s_ta[k] = ax.ta[k];
+    s_tm[k] = ax.tm[k];
+    s_tc[k] = ax.tc[k];
+  }
+  __syncthreads();
+  const bool got = mbar_wait(&bar, 0u, kWaitLimitNs);
+  if (__syncthreads_or(!got)) {
+    if (tid == 0) *reinterpret_cast<volatile unsigned*>(status) = 1u;
+    mbar_wait(&bar, 0u, kWaitLimitNs);
+    return;
+  }
+  const int shift = s_shift;
+  if (tid < nr) {
+    T* l = s + shift + tid * nc;
+    T y = T(0);
+#pragma unroll 4
+    for (int k = 0; k < nc; ++k) {
+      y = (l[k] - s_ta[k] * y) * s_tm[k];
+      l[k] = y;
+    }
+    T x = T(0);
+#pragma unroll 4
+    for (int k = nc - 1; k >= 0; --k) {
+      x = l[k] - s_tc[k] * x;
+      l[k] = x;
+    }
+  }
+  __syncthreads();
+  T* dstF = F + first * nc;
+  T* dstB = B ? B + first * nc : nullptr;
+  for (int base = tid; base < total; base += 4 * blockDim.x) {
+    T bv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * blockDim.x;
+      bv[u] = (i < total && mode != kApplyNone) ? dstB[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < total) {
+        const T x = s[shift + i];
+        if (mode == kApplyNone) dstF[i] = x;
+        else apply_x(dstF, dstB, i, x, bv[u], mode);
+      }
+    }
+  }
+}
+
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int level,
-                          cudaStream_t s) {
+                          unsigned int* status, cudaStream_t s) {
   const int64_t c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   int last = 0;
   while (lv.ax[last].n == 1) ++last;  // lowest active axis is solved last
@@ -169,7 +273,17 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
     TraceScope ts(a == 2 ? kKSolveContig : kKSolveStrided, level,
                   sizeof(T) * passes * double(c0) * c1 * c2, s);
     const size_t per_row = sizeof(T) * static_cast<size_t>(c2 | 1);
-    if (a == 2 && per_row <= 112 * 1024) {
+    const size_t tpad = (3 * sizeof(T) * static_cast<size_t>(c2) + 15) / 16 * 16;
+    if (a == 2 && (c2 & 1) && per_row <= 32 * 1024 && c0 * c1 >= 1024) {
+      // Odd line length: TMA-staged lines, about 64 KB of lines per CTA.
+      const int64_t nlines = c0 * c1;
+      const int rows = static_cast<int>(std::max<size_t>(1, std::min<size_t>(128, (64 * 1024) / per_row)));
+      const size_t smem = tpad + per_row * rows + 32;
+      cudaFuncSetAttribute(solve_contig_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+      solve_contig_tma_kernel<T><<<ceil_div(nlines, rows), 128, smem, s>>>(lv.ax[2], F, B, nlines,
+                                                                            rows, m, status);
+    } else if (a == 2 && per_row <= 112 * 1024) {
       const int64_t nlines = c0 * c1;
       int rows = static_cast<int>(std::min<size_t>(128, (112 * 1024) / per_row));
       rows = std::max(rows, 1);
@@ -193,8 +307,8 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
 }
 
 template cudaError_t launch_solves<float>(const LevelK<float>&, float*, float*, ApplyMode, int,
-                                          cudaStream_t);
+                                          unsigned int*, cudaStream_t);
 template cudaError_t launch_solves<double>(const LevelK<double>&, double*, double*, ApplyMode, int,
-                                           cudaStream_t);
+                                           unsigned int*, cudaStream_t);
 
 }  // namespace mgb
