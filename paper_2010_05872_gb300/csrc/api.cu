@@ -73,6 +73,11 @@ void fill_levels(DevPlan& p, const std::vector<std::vector<size_t>>& offs, char*
       k.tc = reinterpret_cast<const T*>(base + o[5]);
       k.xd = reinterpret_cast<const T*>(base + o[6]);
       k.xr = reinterpret_cast<const T*>(base + o[7]);
+      k.sb = reinterpret_cast<const T*>(base + o[8]);
+      k.sg = reinterpret_cast<const T*>(base + o[9]);
+      k.sy = reinterpret_cast<const T*>(base + o[10]);
+      k.sh = reinterpret_cast<const T*>(base + o[11]);
+      k.seg_len = t.seg_len;
       k.n = t.n;
       k.nc = t.nc;
     }
@@ -96,6 +101,7 @@ int upload(DevPlan& p) {
       o.push_back(reserve(sizeof(T) * t.tc.size()));
       o.push_back(reserve(sizeof(T) * t.xd.size()));
       o.push_back(reserve(sizeof(T) * t.xr.size()));
+      for (const auto* v : {&t.sb, &t.sg, &t.sy, &t.sh}) o.push_back(reserve(sizeof(T) * v->size()));
     }
   size_t lev_off[3];
   for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
@@ -112,6 +118,7 @@ int upload(DevPlan& p) {
       put(o[0], t.iwl); put(o[1], t.iwr); put(o[2], t.rw);
       put(o[3], t.ta); put(o[4], t.tm); put(o[5], t.tc);
       put(o[6], t.xd); put(o[7], t.xr);
+      put(o[8], t.sb); put(o[9], t.sg); put(o[10], t.sy); put(o[11], t.sh);
     }
   for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
   std::memcpy(stage.data() + lev01_off, h.lev01.data(), h.lev01.size());

@@ -19,8 +19,13 @@ struct AxisK {
   const T* ta;   // [nc] Thomas: sub-diagonal
   const T* tm;   // [nc] Thomas: reciprocal pivot
   const T* tc;   // [nc] Thomas: eliminated super-diagonal
+  const T* sb;   // [nc] segmented forward recurrence: y_k = tm_k f_k + sb_k y_{k-1}
+  const T* sg;   // [nc] product of sb over the segment up to k
+  const T* sy;   // [nc] segmented backward recurrence: x_k = y_k + sy_k x_{k+1}
+  const T* sh;   // [nc] product of sy from k to the segment end
   int n;
   int nc;
+  int seg_len;   // rows per segment (the last may be shorter)
 };
 
 template <typename T>

@@ -114,6 +114,25 @@ void build_axis(const std::vector<double>& x, AxisTables& t) {
     cprev = t.tc[k];
   }
 
+  // Segmented recurrences: segments of at most 32 rows, as even as possible.
+  {
+    const int nseg = (nc + 31) / 32;
+    const int L = (nc + nseg - 1) / nseg;
+    t.seg_len = L;
+    t.sb.assign(nc, 0.0); t.sg.assign(nc, 0.0); t.sy.assign(nc, 0.0); t.sh.assign(nc, 0.0);
+    for (int k = 0; k < nc; ++k) {
+      t.sb[k] = -a[k] * t.tm[k];
+      t.sy[k] = -t.tc[k];
+    }
+    for (int k0 = 0; k0 < nc; k0 += L) {
+      const int k1 = std::min(k0 + L, nc) - 1;
+      double g = 1.0;
+      for (int k = k0; k <= k1; ++k) { g *= t.sb[k]; t.sg[k] = g; }
+      double h = 1.0;
+      for (int k = k1; k >= k0; --k) { h *= t.sy[k]; t.sh[k] = h; }
+    }
+  }
+
   // Row sums of |A| with A = M_c^{-1} P^T M_f: r over all fine columns,
   // s over the coarse (nodal) columns.  Row k of M_c^{-1} is found by a
   // Thomas solve of M_c y = e_k on a window of +-64 rows around k; the
@@ -165,6 +184,8 @@ void padded_axis(AxisTables& t) {
   t.xd = {0.0, 1.0, 0.0};
   t.xr = {0.0, 1.0, 0.0};
   t.ta.assign(1, 0.0); t.tm.assign(1, 1.0); t.tc.assign(1, 0.0);
+  t.sb.assign(1, 0.0); t.sg.assign(1, 0.0); t.sy.assign(1, 0.0); t.sh.assign(1, 0.0);
+  t.seg_len = 1;
   t.rmax = 1.0; t.smax = 1.0; t.dmax = 0.0;
 }
 

@@ -30,6 +30,12 @@ struct AxisTables {
   std::vector<double> rw;          // [nc * 5]
   std::vector<double> xd, xr;      // [nc * 3] R P and R S on coarse nodes k-1, k, k+1
   std::vector<double> ta, tm, tc;  // [nc]
+  // Segmented form of the two Thomas recurrences (segments of seg_len rows):
+  // forward y_k = tm_k f_k + sb_k y_{k-1}, backward x_k = y_k + sy_k x_{k+1},
+  // and the products sg_k (sb from the segment start to k) and sh_k (sy from
+  // k to the segment end) that carry a segment's boundary value inward.
+  std::vector<double> sb, sg, sy, sh;  // [nc]
+  int seg_len = 1;
   double rmax = 1, smax = 1, dmax = 0;  // row-sum maxima of |M_c^{-1} P^T M_f|
 };
 
