@@ -164,6 +164,36 @@ int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* co
 /* Free every cached plan (device tables included) of the current device. */
 int mgard_release_plans(void);
 
+/* Allocation-free decomposition (the paper has no counterpart; an interface
+ * choice).  Same result as mgard_decompose (Section 2, decomposition;
+ * Algorithm 1 lines 12-16) with the same kernels, for callers that must not
+ * allocate device memory while they compress -- e.g. an in-situ simulation
+ * that has reserved nearly all of HBM for its own state, where a cudaMalloc
+ * could fail and may wait for work in flight on other streams.
+ *  - No workspace argument: the level workspace and the plan tables live in
+ *    one static device array of 32 MiB per device.  Shapes whose tables plus
+ *    workspace (about 2/7 of the field in 3D) do not fit are rejected with
+ *    MGARD_ERR_WORKSPACE before any work is enqueued (e.g. up to ~110 MB of
+ *    FP32 field).
+ *  - Nothing is allocated: no cudaMalloc, cudaFree, pinned host memory or
+ *    allocating library.  The first call on a device looks up the array's
+ *    device address (cudaGetSymbolAddress, checked); a call with a new
+ *    (dims, coords, dtype) builds host tables and copies them into the array
+ *    with cudaMemcpyAsync from pageable memory.  Make the first call for a
+ *    shape outside any stream capture.
+ *  - Only the array's first word (the wait-timeout status) must start at
+ *    zero; each call clears it on `stream` before its kernels run.
+ *  - Calls share the one array per device: two calls whose work overlaps on
+ *    the device (other streams, other host threads, or a new shape while an
+ *    earlier call's kernels still run) race on it.  Order them on one stream
+ *    or synchronize between them.
+ *  - `timed_out` may be NULL (the call returns once the work is enqueued).
+ *    Otherwise the call waits for `stream`, sets *timed_out to 1 if a bounded
+ *    device-side wait gave up (then returns MGARD_ERR_TIMEOUT), else 0.
+ * Arguments, layout and the other errors are those of mgard_decompose. */
+int mgard_decompose_noalloc(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                            int stop_level, void* data, int* timed_out, void* stream);
+
 /* Kernel timing trace (host-side bookkeeping, no effect on results).
  * mgard_trace_enable(1) clears earlier records and starts bracketing every
  * kernel launch of this library with CUDA events on the launch stream;

@@ -56,6 +56,9 @@ _SIGNATURES = {
                                              ctypes.c_size_t, _VP]),
     "mgard_release_plans": (ctypes.c_int, []),
     "mgard_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mgard_decompose_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.c_void_p]),
     "mgard_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "mgard_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
@@ -151,6 +154,18 @@ def mgard_decompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes,
     s = _Shape(dims, coords)
     return lib().mgard_decompose(s.ndim, s.dims, s.coords, dtype, stop_level, data_ptr, ws_ptr,
                                  ws_bytes, stream)
+
+
+def mgard_decompose_noalloc(dims, coords, dtype, stop_level, data_ptr, stream,
+                            wait: bool = False):
+    """Allocation-free decomposition (static device scratch).  Returns
+    (rc, timed_out); with wait=False timed_out is None and the call does not
+    wait for the stream."""
+    s = _Shape(dims, coords)
+    flag = ctypes.c_int(0)
+    rc = lib().mgard_decompose_noalloc(s.ndim, s.dims, s.coords, dtype, stop_level, data_ptr,
+                                       ctypes.byref(flag) if wait else None, stream)
+    return rc, (bool(flag.value) if wait else None)
 
 
 def mgard_recompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:
@@ -290,6 +305,16 @@ def decompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
     rc = mgard_decompose(x.shape, coords, dtype_code(x), stop_level, x.data_ptr(), ws.data_ptr(),
                          ws.numel(), _stream(stream))
     _check(rc, "mgard_decompose")
+    return x
+
+
+def decompose_noalloc(x, coords=None, stop_level: int = 0, stream=None, wait: bool = False):
+    """In-place decomposition of a CUDA tensor without any allocation by the
+    library (static scratch; small fields only).  Returns x."""
+    _cuda_tensor(x, "x")
+    rc, _ = mgard_decompose_noalloc(x.shape, coords, dtype_code(x), stop_level, x.data_ptr(),
+                                    _stream(stream), wait)
+    _check(rc, "mgard_decompose_noalloc")
     return x
 
 

@@ -585,3 +585,156 @@ const char* mgard_error_string(int code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free decomposition.  The paper has no counterpart: this is an
+// interface for callers that must not allocate device memory while they
+// compress, e.g. an in-situ simulation that has reserved nearly all of HBM
+// for its own state (a cudaMalloc could fail there, and it may also wait for
+// work in flight on other streams).  The workspace and the plan tables live
+// in one file-scope __device__ array of kNoAllocBytes; no cudaMalloc,
+// cudaFree, pinned-host allocation or allocating library is called.
+// ---------------------------------------------------------------------------
+namespace mgb {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB per device
+// Layout: [0, 256) status word (wait timeouts; set to zero at each call),
+// then the plan tables, then the level workspace.  Nothing else needs to
+// start at zero: the workspace is fully written before it is read.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocState {
+  char* base = nullptr;   // device address of g_noalloc_scratch on this device
+  std::string key;        // plan whose tables are resident, empty if none
+  DevPlan plan;           // table pointers into the scratch (dmem stays null)
+  size_t ws_off = 0;      // workspace offset in the scratch
+};
+std::mutex g_noalloc_mu;
+std::map<int, std::unique_ptr<NoAllocState>> g_noalloc;
+
+// Stage the plan tables of `p.h` into host memory with the offsets that
+// fill_levels expects, then copy them to `dst` (device) on `s`.
+template <typename T>
+int noalloc_tables(DevPlan& p, char* dst, size_t cap, size_t* used, cudaStream_t s) {
+  const HostPlan& h = p.h;
+  std::vector<std::vector<size_t>> offs((h.L + 1) * 3);
+  size_t total = 0;
+  auto reserve = [&](size_t bytes) { const size_t o = total; total = align_up(total + bytes, 16); return o; };
+  for (int l = 1; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const AxisTables& t = h.ax[l][a];
+      auto& o = offs[l * 3 + a];
+      for (const auto* v : {&t.iwl, &t.iwr, &t.rw, &t.ta, &t.tm, &t.tc, &t.xd, &t.xr, &t.sb, &t.sg,
+                            &t.sy, &t.sh})
+        o.push_back(reserve(sizeof(T) * v->size()));
+    }
+  size_t lev_off[3];
+  for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
+  const size_t lev01_off = reserve(h.lev01.size());
+  total = align_up(total, kAlign);
+  if (total > cap) return MGARD_ERR_WORKSPACE;
+  std::vector<char> stage(total, 0);
+  auto put = [&](size_t off, const std::vector<double>& v) {
+    T* d = reinterpret_cast<T*>(stage.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) d[i] = static_cast<T>(v[i]);
+  };
+  for (int l = 1; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const AxisTables& t = h.ax[l][a];
+      const auto& o = offs[l * 3 + a];
+      int i = 0;
+      for (const auto* v : {&t.iwl, &t.iwr, &t.rw, &t.ta, &t.tm, &t.tc, &t.xd, &t.xr, &t.sb, &t.sg,
+                            &t.sy, &t.sh})
+        put(o[i++], *v);
+    }
+  for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
+  std::memcpy(stage.data() + lev01_off, h.lev01.data(), h.lev01.size());
+  // Pageable source: the copy has consumed `stage` when the call returns.
+  if (cudaMemcpyAsync(dst, stage.data(), total, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return MGARD_ERR_CUDA;
+  if constexpr (sizeof(T) == 4) fill_levels<float>(p, offs, dst, p.lvf);
+  else fill_levels<double>(p, offs, dst, p.lvd);
+  for (int a = 0; a < 3; ++a) p.lev[a] = reinterpret_cast<const uint8_t*>(dst + lev_off[a]);
+  p.lev01 = reinterpret_cast<const uint8_t*>(dst + lev01_off);
+  *used = total;
+  return MGARD_OK;
+}
+
+}  // namespace
+}  // namespace mgb
+
+extern "C" int mgard_decompose_noalloc(int ndim, const int64_t* dims, const double* const* coords,
+                                       int dtype, int stop_level, void* data, int* timed_out,
+                                       void* stream) {
+  using namespace mgb;
+  if (dtype != MGARD_F32 && dtype != MGARD_F64) return MGARD_ERR_ARG;
+  int rc = check_shape(ndim, dims);
+  if (rc != MGARD_OK) return rc;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return MGARD_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostPlan probe;
+  probe.ndim = ndim;
+  const int pad = 3 - ndim;
+  for (int d = 0; d < ndim; ++d) probe.dims3[pad + d] = dims[d];
+  for (int d = 0; d < ndim; ++d) {
+    const double* c = coords ? coords[d] : nullptr;
+    if (c) probe.coords_key.insert(probe.coords_key.end(), c, c + dims[d]);
+    probe.coords_key.push_back(c ? 1.0 : 0.0);
+  }
+  const std::string key = plan_key(device, dtype, probe);
+
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto& slot = g_noalloc[device];
+  if (!slot) {
+    // Set-up once per device: the device address of the scratch array.
+    auto st = std::make_unique<NoAllocState>();
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || addr == nullptr)
+      return MGARD_ERR_CUDA;
+    st->base = static_cast<char*>(addr);
+    slot = std::move(st);
+  }
+  NoAllocState& st = *slot;
+  if (st.key != key) {
+    // A new plan: build the host tables, check that tables and workspace fit,
+    // then copy the tables in.
+    HostPlan h;
+    rc = build_host_plan(ndim, dims, coords, h);
+    if (rc != MGARD_OK) return rc;
+    st.key.clear();
+    st.plan.h = std::move(h);
+    st.plan.dtype = dtype;
+    st.plan.device = device;
+    layout_workspace(st.plan);
+    const size_t avail = kNoAllocBytes - kAlign;
+    if (st.plan.ws_bytes > avail) return MGARD_ERR_WORKSPACE;
+    size_t used = 0;
+    char* tables = st.base + kAlign;
+    // The tables are copied only when tables and workspace both fit.
+    rc = (dtype == MGARD_F64)
+             ? noalloc_tables<double>(st.plan, tables, avail - st.plan.ws_bytes, &used, s)
+             : noalloc_tables<float>(st.plan, tables, avail - st.plan.ws_bytes, &used, s);
+    if (rc != MGARD_OK) return rc;
+    st.ws_off = kAlign + used;
+    st.key = key;
+  }
+  char* ws = st.base + st.ws_off;
+  rc = check_transform_args(st.plan, stop_level, data, ws, kNoAllocBytes - st.ws_off);
+  if (rc != MGARD_OK) return rc;
+  if (timed_out) *timed_out = 0;
+  if (stop_level == st.plan.h.L) return MGARD_OK;
+  unsigned int* status = reinterpret_cast<unsigned int*>(st.base);
+  if (cudaMemsetAsync(status, 0, sizeof(unsigned int), s) != cudaSuccess) return MGARD_ERR_CUDA;
+  rc = (dtype == MGARD_F64)
+           ? run_decompose<double>(st.plan, stop_level, static_cast<double*>(data), ws, status, s)
+           : run_decompose<float>(st.plan, stop_level, static_cast<float*>(data), ws, status, s);
+  if (rc != MGARD_OK || timed_out == nullptr) return rc;
+  unsigned int word = 0;
+  if (cudaMemcpyAsync(&word, status, sizeof word, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MGARD_ERR_CUDA;
+  *timed_out = word != 0;
+  return word != 0 ? MGARD_ERR_TIMEOUT : MGARD_OK;
+}
