@@ -164,6 +164,39 @@ int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* co
 /* Free every cached plan (device tables included) of the current device. */
 int mgard_release_plans(void);
 
+/* Batched form: many 3D FP32 fields of uneven shape on uniform grids,
+ * decomposed (or recomposed) at full depth in ONE persistent kernel launch
+ * replayed as a CUDA graph (Section 2's level loop for every field; the
+ * per-field kernels' tiles scheduled across the fields).  The paper runs
+ * fields one at a time; batching them is an interface choice of this
+ * library.
+ *  - dims3: host array of 3 * nfields sizes (n0, n1, n2 per field, C order,
+ *    n2 <= 288).  data: host array of nfields device pointers (FP32 fields,
+ *    transformed in place; same layout and result as mgard_decompose /
+ *    mgard_recompose with stop_level 0 and NULL coords).  workspace: device,
+ *    256-byte aligned, at least mgard_batch_workspace_size bytes (one
+ *    per-field workspace after another).
+ *  - The first call for a (shapes, data pointers, workspace) set builds the
+ *    schedule and the graph (device memory is allocated then, and plans are
+ *    cached as for the per-field calls); later calls only launch the graph on
+ *    `stream`.  Make the first call outside any stream capture.
+ *  - mgard_batch_autotune times candidate tile shapes (coarse planes per
+ *    load-vector tile, plane pairs per finish tile, lines per contiguous
+ *    solve tile) with decompose + recompose on a device copy of the fields
+ *    (the fields are restored), keeps the fastest for these shapes and writes
+ *    it to choice_out[3] (may be NULL).  It synchronizes `stream`.
+ *  - A device-side wait that gives up (2 s) is reported by the next
+ *    mgard_quantize / mgard_value_range as MGARD_ERR_TIMEOUT.
+ *  - mgard_batch_release frees every batched schedule and graph. */
+int mgard_batch_workspace_size(int nfields, const int64_t* dims3, size_t* bytes);
+int mgard_batch_decompose(int nfields, const int64_t* dims3, void* const* data, void* workspace,
+                          size_t ws_bytes, void* stream);
+int mgard_batch_recompose(int nfields, const int64_t* dims3, void* const* data, void* workspace,
+                          size_t ws_bytes, void* stream);
+int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, void* workspace,
+                         size_t ws_bytes, void* stream, int* choice_out);
+int mgard_batch_release(void);
+
 /* Allocation-free decomposition (the paper has no counterpart; an interface
  * choice).  Same result as mgard_decompose (Section 2, decomposition;
  * Algorithm 1 lines 12-16) with the same kernels, for callers that must not

@@ -59,6 +59,15 @@ _SIGNATURES = {
     "mgard_decompose_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                                ctypes.c_void_p]),
+    "mgard_batch_workspace_size": (ctypes.c_int, [ctypes.c_int, _I64P,
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "mgard_batch_decompose": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(_VP), _VP,
+                                             ctypes.c_size_t, _VP]),
+    "mgard_batch_recompose": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(_VP), _VP,
+                                             ctypes.c_size_t, _VP]),
+    "mgard_batch_autotune": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(_VP), _VP,
+                                            ctypes.c_size_t, _VP, ctypes.POINTER(ctypes.c_int)]),
+    "mgard_batch_release": (ctypes.c_int, []),
     "mgard_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "mgard_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
@@ -166,6 +175,47 @@ def mgard_decompose_noalloc(dims, coords, dtype, stop_level, data_ptr, stream,
     rc = lib().mgard_decompose_noalloc(s.ndim, s.dims, s.coords, dtype, stop_level, data_ptr,
                                        ctypes.byref(flag) if wait else None, stream)
     return rc, (bool(flag.value) if wait else None)
+
+
+class _Batch:
+    """Marshalled arguments of the batched calls: sizes and data pointers."""
+
+    def __init__(self, shapes, ptrs):
+        self.n = len(shapes)
+        flat = [int(v) for shp in shapes for v in shp]
+        if any(len(shp) != 3 for shp in shapes):
+            raise ValueError("batched fields are 3D")
+        self.dims = (ctypes.c_int64 * max(len(flat), 1))(*flat)
+        self.ptrs = (_VP * max(self.n, 1))(*[int(p) for p in ptrs])
+
+
+def mgard_batch_workspace_size(shapes) -> int:
+    b = _Batch(shapes, [0] * len(shapes))
+    out = ctypes.c_size_t()
+    _check(lib().mgard_batch_workspace_size(b.n, b.dims, ctypes.byref(out)),
+           "mgard_batch_workspace_size")
+    return out.value
+
+
+def mgard_batch_decompose(shapes, ptrs, ws_ptr, ws_bytes, stream) -> int:
+    b = _Batch(shapes, ptrs)
+    return lib().mgard_batch_decompose(b.n, b.dims, b.ptrs, ws_ptr, ws_bytes, stream)
+
+
+def mgard_batch_recompose(shapes, ptrs, ws_ptr, ws_bytes, stream) -> int:
+    b = _Batch(shapes, ptrs)
+    return lib().mgard_batch_recompose(b.n, b.dims, b.ptrs, ws_ptr, ws_bytes, stream)
+
+
+def mgard_batch_autotune(shapes, ptrs, ws_ptr, ws_bytes, stream):
+    b = _Batch(shapes, ptrs)
+    choice = (ctypes.c_int * 3)()
+    rc = lib().mgard_batch_autotune(b.n, b.dims, b.ptrs, ws_ptr, ws_bytes, stream, choice)
+    return rc, tuple(choice)
+
+
+def mgard_batch_release() -> int:
+    return lib().mgard_batch_release()
 
 
 def mgard_recompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:
@@ -316,6 +366,49 @@ def decompose_noalloc(x, coords=None, stop_level: int = 0, stream=None, wait: bo
                                     _stream(stream), wait)
     _check(rc, "mgard_decompose_noalloc")
     return x
+
+
+def batch_workspace(fields):
+    """A device workspace tensor for the batched calls on these fields."""
+    torch = _torch()
+    nbytes = mgard_batch_workspace_size([tuple(f.shape) for f in fields])
+    return torch.empty(nbytes, dtype=torch.uint8, device=fields[0].device)
+
+
+def _batch_args(fields):
+    for f in fields:
+        _cuda_tensor(f, "field")
+        if f.dtype != _torch().float32 or f.dim() != 3:
+            raise ValueError("batched fields are 3D float32 CUDA tensors")
+    return [tuple(f.shape) for f in fields], [f.data_ptr() for f in fields]
+
+
+def batch_decompose(fields, ws=None, stream=None):
+    """Decompose every tensor of `fields` in place in one persistent launch."""
+    shapes, ptrs = _batch_args(fields)
+    if ws is None:
+        ws = batch_workspace(fields)
+    _check(mgard_batch_decompose(shapes, ptrs, ws.data_ptr(), ws.numel(), _stream(stream)),
+           "mgard_batch_decompose")
+    return fields
+
+
+def batch_recompose(fields, ws=None, stream=None):
+    """Recompose every tensor of `fields` in place in one persistent launch."""
+    shapes, ptrs = _batch_args(fields)
+    if ws is None:
+        ws = batch_workspace(fields)
+    _check(mgard_batch_recompose(shapes, ptrs, ws.data_ptr(), ws.numel(), _stream(stream)),
+           "mgard_batch_recompose")
+    return fields
+
+
+def batch_autotune(fields, ws, stream=None):
+    """Pick the tile shapes for these fields (their contents are kept)."""
+    shapes, ptrs = _batch_args(fields)
+    rc, choice = mgard_batch_autotune(shapes, ptrs, ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(rc, "mgard_batch_autotune")
+    return choice
 
 
 def recompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):

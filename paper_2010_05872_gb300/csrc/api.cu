@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "devplan.hpp"
 #include "kernels.cuh"
 #include "mgard_gb.h"
 #include "plan.hpp"
@@ -18,39 +19,6 @@ namespace {
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-// Plan tables resident on one device in the element type of the transform.
-struct DevPlan {
-  HostPlan h;
-  int dtype = MGARD_F32;
-  int device = 0;
-  void* dmem = nullptr;
-  std::vector<LevelK<float>> lvf;   // [L+1], entry l = transition l -> l-1
-  std::vector<LevelK<double>> lvd;
-  const uint8_t* lev[3] = {nullptr, nullptr, nullptr};
-  const uint8_t* lev01 = nullptr;   // per-row level (quantizer)
-  std::vector<size_t> offB, offF;   // workspace offsets of the level-l grids / load vectors
-  size_t ws_bytes = 0;
-  ~DevPlan() {
-    if (dmem) {
-      int cur = 0;
-      cudaGetDevice(&cur);
-      cudaSetDevice(device);
-      cudaFree(dmem);
-      cudaSetDevice(cur);
-    }
-  }
-};
-
-// Small per-device scratch for flags and reductions (allocated once).
-struct DevCtx {
-  unsigned int* flags = nullptr;  // [4]
-  double* partial = nullptr;      // [2 * kMinmaxBlocks]
-  double* result = nullptr;       // [2]
-  unsigned int* h_flags = nullptr;  // pinned host mirrors
-  double* h_result = nullptr;
-  std::mutex mu;                  // serialises the calls that wait on these flags
-};
 
 std::mutex g_mu;
 std::map<std::string, std::unique_ptr<DevPlan>> g_plans;
@@ -158,6 +126,8 @@ std::string plan_key(int device, int dtype, const HostPlan& h) {
   return k;
 }
 
+}  // namespace
+
 // Look up (or build and upload) the plan of this shape/coords/dtype on the
 // current device.
 int get_plan(int ndim, const int64_t* dims, const double* const* coords, int dtype, DevPlan** out) {
@@ -231,6 +201,8 @@ template <>
 const std::vector<LevelK<float>>& levels<float>(const DevPlan& p) { return p.lvf; }
 template <>
 const std::vector<LevelK<double>>& levels<double>(const DevPlan& p) { return p.lvd; }
+
+namespace {
 
 // Decomposition, levels L .. l~+1: load vector (reads the level-l grid only),
 // solves with the correction applied to the gathered coarse values; then,

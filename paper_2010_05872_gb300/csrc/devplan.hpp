@@ -1,0 +1,61 @@
+// Device-resident plans and the per-device context, shared by the entry
+// points of api.cu and the batched form of batch.cu.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "mgard_gb.h"
+#include "plan.hpp"
+
+namespace mgb {
+
+// Plan tables resident on one device in the element type of the transform.
+struct DevPlan {
+  HostPlan h;
+  int dtype = MGARD_F32;
+  int device = 0;
+  void* dmem = nullptr;
+  std::vector<LevelK<float>> lvf;   // [L+1], entry l = transition l -> l-1
+  std::vector<LevelK<double>> lvd;
+  const uint8_t* lev[3] = {nullptr, nullptr, nullptr};
+  const uint8_t* lev01 = nullptr;   // per-row level (quantizer)
+  std::vector<size_t> offB, offF;   // workspace offsets of the level-l grids / load vectors
+  size_t ws_bytes = 0;
+  ~DevPlan() {
+    if (dmem) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(device);
+      cudaFree(dmem);
+      cudaSetDevice(cur);
+    }
+  }
+};
+
+// Small per-device scratch for flags and reductions (allocated once).
+struct DevCtx {
+  unsigned int* flags = nullptr;  // [4]
+  double* partial = nullptr;      // [2 * kMinmaxBlocks]
+  double* result = nullptr;       // [2]
+  unsigned int* h_flags = nullptr;  // pinned host mirrors
+  double* h_result = nullptr;
+  std::mutex mu;                  // serialises the calls that wait on these flags
+};
+
+// Look up (or build and upload) the plan of this shape/coords/dtype on the
+// current device.  The returned plan lives until mgard_release_plans().
+int get_plan(int ndim, const int64_t* dims, const double* const* coords, int dtype, DevPlan** out);
+
+// The per-device flag/reduction context (created on first use).
+DevCtx* get_ctx();
+
+template <typename T>
+const std::vector<LevelK<T>>& levels(const DevPlan& p);
+
+}  // namespace mgb

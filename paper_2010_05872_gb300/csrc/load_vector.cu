@@ -38,280 +38,20 @@
 #include <cstdint>
 
 #include "kernels.cuh"
-#include "tma.cuh"
+#include "lv_tile.cuh"
 #include "trace.hpp"
 
 namespace mgb {
 namespace {
 
-__device__ __forceinline__ int cpos(int k, int n) { return min(2 * k, n - 1); }
-__device__ __forceinline__ bool is_coef(int j, int n) { return (j & 1) && (j != n - 1); }
-__device__ __forceinline__ int nodal_k(int j, int n, int nc) { return j == n - 1 ? nc - 1 : (j >> 1); }
-
-constexpr int kMaxThreads = 512;  // one thread per coarse column of a row (chunk)
-
-struct MarchGeom {
-  int t1, tc2, t0;     // coarse rows / columns / planes per CTA
-  int nb2, nb1, nb0;   // CTAs along axes 2, 1, 0
-  int pitch;           // elements between staged rows (n2 in 3D; the tile width in 2D)
-  int BUF;             // elements of one plane buffer (16-byte multiple)
-  int threads;         // CTA size
-};
-
-// Pipeline depth and coarse rows per CTA along axis 1, per element type.
-template <typename T>
-struct MarchCfg;
-template <>
-struct MarchCfg<float> {
-  static constexpr int NS = 4, T1 = 4;
-};
-template <>
-struct MarchCfg<double> {
-  static constexpr int NS = 3, T1 = 4;
-};
-
 template <typename T, bool DEC, int NS, int T1C, bool THREE>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(kLvMaxThreads)
 load_vector_march_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict__ coarse,
                          T* __restrict__ F, MarchGeom g, uint64_t fine_count,
                          unsigned int* __restrict__ status) {
-  constexpr int S1M = THREE ? 2 * T1C + 3 : 1;  // staged rows
-  constexpr int TM = THREE ? T1C : 1;           // coarse rows per CTA
-  constexpr int VEC = 16 / sizeof(T);
-  constexpr int PADL = 2 * VEC;                 // zeroed elements before a tile
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[NS];
-  __shared__ int s_off[NS];   // buffer index of tile element (0, 0)
-  __shared__ T s_w1[S1M][3];  // R1 weight of row s for coarse row base(s) + i
-  __shared__ T s_y1[S1M][3];  // X1 weight of nodal row s for the same coarse rows
-  __shared__ int s_rown[S1M]; // coarse row of a nodal row s, or -1
-
-  const int tid = threadIdx.x;
-  const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
-  const int c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
-  const int b2 = blockIdx.x % g.nb2;
-  const int b1 = (blockIdx.x / g.nb2) % g.nb1;
-  const int b0 = blockIdx.x / (g.nb2 * g.nb1);
-  const int K2 = b2 * g.tc2, K1 = b1 * g.t1, K0 = b0 * g.t0;
-  const int T2 = min(g.tc2, c2 - K2), T1 = min(g.t1, c1 - K1), T0 = min(g.t0, c0 - K0);
-  const int rbase = THREE ? 2 * K1 - 2 : 0;  // fine row of tile row 0
-  const int cbase = 2 * K2 - 2;              // fine column of tile column 0
-  const int jr_lo = max(rbase, 0), jr_hi = THREE ? min(2 * K1 + 2 * T1, n1 - 1) : 0;
-  const int jc_lo = max(cbase, 0), jc_hi = min(2 * (K2 + T2 - 1) + 2, n2 - 1);
-  const int jlo = max(2 * K0 - 2, 0), jhi = min(2 * (K0 + T0 - 1) + 2, n0 - 1);
-  // Tile index of the first copied element and the copied length.
-  const int t_first = (jr_lo - rbase) * g.pitch + (jc_lo - cbase);
-  const int t_len = (jr_hi - jr_lo) * n2 + (jc_hi - jc_lo + 1);
-
-  T* vbuf = reinterpret_cast<T*>(smem_raw);  // NS x BUF
-
-  // Zero the buffers (virtual rows and pads must hold finite values) and
-  // build the row tables.
-  for (int i = tid; i < NS * g.BUF; i += blockDim.x) vbuf[i] = T(0);
-  for (int s = tid; s < S1M; s += blockDim.x) {
-    const int j1 = rbase + s;
-    const bool valid = j1 >= 0 && j1 < n1;
-    const bool nod = valid && !is_coef(j1, n1);
-    const int kr = nod ? nodal_k(j1, n1, c1) : -1;
-    s_rown[s] = kr;
-    const int base = (s & 1) ? (s - 3) / 2 : s / 2 - 2;
-    for (int i = 0; i < 3; ++i) {
-      const int t = base + i, k = K1 + t;
-      T w = T(0), y = T(0);
-      if (valid && t >= 0 && t < T1) {
-        const int off = j1 - cpos(k, n1) + 2;
-        if (off >= 0 && off <= 4) w = lv.ax[1].rw[5 * k + off];
-        const int d = kr - k + 1;
-        if (nod && d >= 0 && d <= 2) y = (DEC ? lv.ax[1].xd : lv.ax[1].xr)[3 * k + d];
-      }
-      s_w1[s][i] = w;
-      s_y1[s][i] = y;
-    }
-  }
-  if (tid == 0) {
-    for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
-    fence_mbar_init();
-  }
-
-  // Column of this thread: coarse k2, its fine centre and 5-tap weights.
-  const int k2 = K2 + tid;
-  const bool act = tid < T2;
-  const int ccol = act ? cpos(k2, n2) - cbase : 2;  // tile column of the centre
-  T rw2[5], x2[5];
-#pragma unroll
-  for (int o = 0; o < 5; ++o) rw2[o] = x2[o] = T(0);
-  if (act) {
-#pragma unroll
-    for (int o = 0; o < 5; ++o) rw2[o] = lv.ax[2].rw[5 * k2 + o];
-    const T* X = DEC ? lv.ax[2].xd : lv.ax[2].xr;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int kk = k2 - 1 + d;
-      if (kk >= 0 && kk < c2) {
-        const int o = cpos(kk, n2) - cpos(k2, n2) + 2;
-        const T xv = X[3 * k2 + d];
-#pragma unroll
-        for (int oo = 0; oo < 5; ++oo)
-          if (oo == o) x2[oo] = xv;
-      }
-    }
-  }
-  __syncthreads();
-
-  // Plane loader, thread 0 only: fine plane j into buffer `slot`.
-  const uint64_t lim = (fine_count * sizeof(T)) & ~15ull;
-  auto issue = [&](int j, int slot) {
-    const uint64_t e0 = (static_cast<uint64_t>(j) * n1 + jr_lo) * n2 + jc_lo;
-    const uint64_t sb = e0 * sizeof(T), eb = sb + static_cast<uint64_t>(t_len) * sizeof(T);
-    const uint64_t ab = sb & ~15ull;
-    uint64_t bb = (eb + 15) & ~15ull;
-    if (bb > lim) bb = lim;
-    const int shift = static_cast<int>((sb - ab) / sizeof(T));
-    const int dst_e = ((PADL + t_first - shift + VEC - 1) / VEC) * VEC;
-    T* dst = vbuf + static_cast<size_t>(slot) * g.BUF + dst_e;
-    s_off[slot] = dst_e + shift - t_first;
-    const unsigned bytes = bb > ab ? static_cast<unsigned>(bb - ab) : 0u;
-    mbar_arrive_expect_tx(&bars[slot], bytes);
-    if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(fine) + ab, bytes, &bars[slot]);
-    for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
-      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = fine[x / sizeof(T)];
-  };
-
-  T acc[3][TM];
-#pragma unroll
-  for (int t = 0; t < TM; ++t) acc[0][t] = acc[1][t] = acc[2][t] = T(0);
-  int kdone = K0;
-  auto store_done = [&](int upto_plane, bool all) {
-    while (kdone < K0 + T0 && (all || cpos(kdone, n0) + 2 <= upto_plane)) {
-#pragma unroll
-      for (int t = 0; t < TM; ++t) {
-        if (act && t < T1) F[(static_cast<int64_t>(kdone) * c1 + (K1 + t)) * c2 + k2] = acc[0][t];
-        acc[0][t] = acc[1][t];
-        acc[1][t] = acc[2][t];
-        acc[2][t] = T(0);
-      }
-      ++kdone;
-    }
-  };
-
-  unsigned phases = 0u;   // bit i: parity to wait for on bars[i]
-  unsigned pending = 0u;  // bit i: bars[i] has a copy in flight
-  if (tid == 0) fence_proxy_async();  // the zero fill precedes every bulk copy
-  for (int i = 0; i < NS - 1 && jlo + i <= jhi; ++i) {
-    if (tid == 0) issue(jlo + i, i);
-    pending |= 1u << i;
-  }
-  for (int j = jlo; j <= jhi; ++j) {
-    const int slot = (j - jlo) % NS;
-    const bool got = mbar_wait(&bars[slot], (phases >> slot) & 1u, kWaitLimitNs);
-    if (__syncthreads_or(!got)) {
-      // A copy did not land in time: record it, give every stage still in
-      // flight a second bounded wait so nothing lands after the CTA exits.
-      if (tid == 0) *reinterpret_cast<volatile unsigned*>(status) = 1u;
-      for (int i = 0; i < NS; ++i)
-        if ((pending >> i) & 1u) mbar_wait(&bars[i], (phases >> i) & 1u, kWaitLimitNs);
-      return;
-    }
-    phases ^= 1u << slot;
-    pending &= ~(1u << slot);
-    if (j + NS - 1 <= jhi) {
-      // The buffer refilled here was last read for plane j - 1.
-      const int ns = (j - jlo + NS - 1) % NS;
-      if (tid == 0) {
-        fence_proxy_async();
-        issue(j + NS - 1, ns);
-      }
-      pending |= 1u << ns;
-    }
-
-    const bool pn = !is_coef(j, n0);  // nodal plane
-    const int kj = pn ? nodal_k(j, n0, c0) : -1;
-    const bool gplane = pn && kj >= K0 && kj < K0 + T0;
-    const T* tile = vbuf + static_cast<size_t>(slot) * g.BUF + s_off[slot] + ccol;
-    T G1[TM], H1[TM];
-#pragma unroll
-    for (int t = 0; t < TM; ++t) G1[t] = H1[t] = T(0);
-#pragma unroll
-    for (int s = 0; s < S1M; ++s) {
-      const T* row = tile + s * g.pitch;
-      T f[5];
-#pragma unroll
-      for (int o = 0; o < 5; ++o) f[o] = row[o - 2];
-      T gs = T(0);
-#pragma unroll
-      for (int o = 0; o < 5; ++o) gs += rw2[o] * f[o];
-      const int base = (s & 1) ? (s - 3) / 2 : s / 2 - 2;
-      const int kr = THREE ? s_rown[s] : 0;
-      if (!THREE) {
-        G1[0] = gs;
-      } else {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int t = base + i;
-          if (t >= 0 && t < TM) G1[t] += s_w1[s][i] * gs;
-        }
-      }
-      if (pn && kr >= 0) {
-        T hs = T(0);
-#pragma unroll
-        for (int o = 0; o < 5; ++o) hs += x2[o] * f[o];
-        if (!THREE) {
-          H1[0] = hs;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const int t = base + i;
-            if (t >= 0 && t < TM) H1[t] += s_y1[s][i] * hs;
-          }
-        }
-        if (gplane && act && kr >= K1 && kr < K1 + T1)
-          coarse[(static_cast<int64_t>(kj) * c1 + kr) * c2 + k2] = f[2];
-      }
-    }
-    // Axis 0: plane j feeds the coarse planes kdone .. kdone + 2.
-    T wk[3], yk[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int kk = kdone + k;
-      wk[k] = yk[k] = T(0);
-      if (kk < K0 + T0) {
-        const int off = j - cpos(kk, n0) + 2;
-        if (off >= 0 && off <= 4) wk[k] = __ldg(lv.ax[0].rw + 5 * kk + off);
-        const int d = kj - kk + 1;
-        if (pn && d >= 0 && d <= 2) yk[k] = __ldg((DEC ? lv.ax[0].xd : lv.ax[0].xr) + 3 * kk + d);
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < TM; ++t)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) acc[k][t] += wk[k] * G1[t] - yk[k] * H1[t];
-    store_done(j, false);
-    __syncthreads();  // every read of this buffer is done
-  }
-  store_done(jhi, true);
-}
-
-template <typename T>
-bool plan_geometry(const LevelK<T>& lv, MarchGeom& g) {
-  using C = MarchCfg<T>;
-  const int n1 = lv.ax[1].n, n2 = lv.ax[2].n, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
-  const int vec = 16 / static_cast<int>(sizeof(T));
-  if (n1 > 1) {
-    if (c2 > kMaxThreads) return false;  // rows too wide for one CTA
-    g.t1 = C::T1;
-    g.tc2 = c2;
-    g.pitch = n2;
-    g.BUF = ((4 * vec + (2 * C::T1 + 3) * n2 + 4 + vec - 1) / vec) * vec;
-  } else {
-    g.t1 = 1;
-    g.tc2 = c2 <= kMaxThreads ? c2 : kMaxThreads / 2;
-    g.pitch = 2 * g.tc2 + 3;
-    g.BUF = ((4 * vec + g.pitch + 4 + vec - 1) / vec) * vec;
-  }
-  g.nb2 = (c2 + g.tc2 - 1) / g.tc2;
-  g.nb1 = (c1 + g.t1 - 1) / g.t1;
-  g.threads = 32 * ((g.tc2 + 31) / 32);
-  return g.threads <= kMaxThreads && sizeof(T) * static_cast<size_t>(C::NS) * g.BUF <= 200 * 1024;
+  load_vector_march_tile<T, DEC, NS, T1C, THREE>(lv, fine, coarse, F, g, fine_count, status,
+                                                 blockIdx.x, smem_raw);
 }
 
 }  // namespace
