@@ -182,12 +182,20 @@ int mgard_release_plans(void);
  *    `stream`.  Make the first call outside any stream capture.
  *  - mgard_batch_autotune times candidate tile shapes (coarse planes per
  *    load-vector tile, plane pairs per finish tile, lines per contiguous
- *    solve tile) with decompose + recompose on a device copy of the fields
- *    (the fields are restored), keeps the fastest for these shapes and writes
- *    it to choice_out[3] (may be NULL).  It synchronizes `stream`.
+ *    solve tile
+ *    and 32-line groups per segmented solve tile) with decompose + recompose
+ *    on the fields (restored afterwards from a device copy), keeps the
+ *    fastest for these shapes and writes it to choice_out[4] (may be NULL).
+ *    It synchronizes `stream`.
  *  - A device-side wait that gives up (2 s) is reported by the next
  *    mgard_quantize / mgard_value_range as MGARD_ERR_TIMEOUT.
- *  - mgard_batch_release frees every batched schedule and graph. */
+ *  - mgard_batch_release frees every batched schedule and graph.
+ *  - mgard_batch_stats waits for the device and copies, for the batched
+ *    launch issued last, per tile kind (load vector dec, load vector rec,
+ *    contiguous solve with bulk copy, contiguous solve, segmented solve,
+ *    finish) three counters: tiles run, SM cycles spent before a tile
+ *    started (waiting for its stage's dependency, taking the descriptor) and
+ *    SM cycles running tiles; `n` must be at least 18. */
 int mgard_batch_workspace_size(int nfields, const int64_t* dims3, size_t* bytes);
 int mgard_batch_decompose(int nfields, const int64_t* dims3, void* const* data, void* workspace,
                           size_t ws_bytes, void* stream);
@@ -196,6 +204,7 @@ int mgard_batch_recompose(int nfields, const int64_t* dims3, void* const* data, 
 int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, void* workspace,
                          size_t ws_bytes, void* stream, int* choice_out);
 int mgard_batch_release(void);
+int mgard_batch_stats(uint64_t* out, int n);
 
 /* Allocation-free decomposition (the paper has no counterpart; an interface
  * choice).  Same result as mgard_decompose (Section 2, decomposition;

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "mgard_batch_autotune": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(_VP), _VP,
                                             ctypes.c_size_t, _VP, ctypes.POINTER(ctypes.c_int)]),
     "mgard_batch_release": (ctypes.c_int, []),
+    "mgard_batch_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "mgard_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "mgard_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
@@ -209,9 +210,20 @@ def mgard_batch_recompose(shapes, ptrs, ws_ptr, ws_bytes, stream) -> int:
 
 def mgard_batch_autotune(shapes, ptrs, ws_ptr, ws_bytes, stream):
     b = _Batch(shapes, ptrs)
-    choice = (ctypes.c_int * 3)()
+    choice = (ctypes.c_int * 4)()
     rc = lib().mgard_batch_autotune(b.n, b.dims, b.ptrs, ws_ptr, ws_bytes, stream, choice)
     return rc, tuple(choice)
+
+
+BATCH_KINDS = ("load_vector_dec", "load_vector_rec", "solve_contig_bulk", "solve_contig",
+               "solve_segmented", "finish")
+
+
+def mgard_batch_stats():
+    """Per tile kind of the last batched launch: (tiles, wait cycles, run cycles)."""
+    out = (ctypes.c_uint64 * 18)()
+    _check(lib().mgard_batch_stats(out, 18), "mgard_batch_stats")
+    return {k: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, k in enumerate(BATCH_KINDS)}
 
 
 def mgard_batch_release() -> int:

@@ -17,8 +17,12 @@
 // quantize or value-range call) and ends the CTA.
 //
 // Tile shapes (coarse planes per load-vector tile, plane pairs per finish
-// tile, lines per contiguous-solve tile) are parameters of the plan, chosen
-// by the autotuner of mgard_batch_autotune.
+// tile, lines per contiguous-solve tile, line groups per segmented-solve
+// tile) are parameters of the plan, chosen by the autotuner of
+// mgard_batch_autotune.  Segmented solves of short lines put several
+// 32-line groups side by side in one CTA; the finish tiles use a 4-stage
+// ring.  Per tile kind, the kernel counts tiles, cycles spent before a tile
+// starts and cycles running tiles (mgard_batch_stats).
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -46,6 +50,7 @@ enum BatchKind : int {
   kBSolveContig,
   kBSolveSeg,
   kBFinish,
+  kBKinds
 };
 
 // One stage of one field (device side).
@@ -54,6 +59,8 @@ struct BatchStage {
   int ntiles;
   int mode;          // apply mode of a solve
   int rows;          // lines per contiguous-solve tile
+  int groups;        // 32-line groups per segmented-solve tile (a multiple of gpp)
+  int gpp;           // groups solved side by side per pass
   int64_t nlines;    // lines of a solve
   int64_t S;         // stride of a segmented solve
   int64_t block_stride;
@@ -73,12 +80,12 @@ struct BatchStage {
 
 constexpr int kBatchThreads = 288;
 constexpr int kLvNS = MarchCfg<float>::NS, kLvT1 = MarchCfg<float>::T1;
-constexpr int kFinNS = FinishCfg<float>::NS, kFinT1 = FinishCfg<float>::T1;
+constexpr int kFinNS = 4, kFinT1 = FinishCfg<float>::T1;
 
-__global__ void __launch_bounds__(kBatchThreads, 1)
+__global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ items, int nitems,
              unsigned int* __restrict__ head, unsigned int* __restrict__ done,
-             unsigned int* __restrict__ status) {
+             unsigned int* __restrict__ status, unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ int s_abort;
@@ -93,6 +100,7 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
     const int it = s_item;
     if (it >= nitems) break;
     const int4 item = items[it];  // x: stage, y: tile, z: stage it waits for, w: its tiles
+    const long long c_wait = clock64();
     if (tid == 0 && item.z >= 0) {
       const uint64_t t0 = global_ns();
       while (ld_acquire_gpu(done + item.z) < static_cast<unsigned>(item.w)) {
@@ -113,6 +121,7 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
     }
     __syncthreads();
     if (s_abort) break;
+    const long long c_run = clock64();
     switch (st.kind) {
       case kBLoadVecDec:
         load_vector_march_tile<float, true, kLvNS, kLvT1, true>(st.lv, st.fine, st.coarse, st.F,
@@ -132,10 +141,18 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
         solve_contig_tile<float>(st.lv.ax[2], st.F, st.B, st.nlines, st.rows, st.mode, item.y,
                                  smem_raw);
         break;
-      case kBSolveSeg:
-        solve_seg_tile<float>(st.lv.ax[st.axis], st.F, st.B, st.nlines, st.S, st.block_stride,
-                              st.mode, item.y, smem_raw);
+      case kBSolveSeg: {
+        // st.gpp groups of 32 lines side by side per pass, st.groups per tile.
+        const int passes = st.groups / st.gpp;
+        for (int q = 0; q < passes; ++q) {
+          const int64_t t = static_cast<int64_t>(item.y) * passes + q;
+          if (t * st.gpp * 32 >= st.nlines) break;
+          if (q > 0) __syncthreads();  // the previous pass's reads of shared memory are done
+          solve_seg_tile<float>(st.lv.ax[st.axis], st.F, st.B, st.nlines, st.S, st.block_stride,
+                                st.mode, static_cast<int>(t), smem_raw, st.gpp);
+        }
         break;
+      }
       default:
         finish_march_tile<float, kFinNS, kFinT1>(st.lv, st.nodal_src, st.interp_src, st.sign,
                                                  st.fine, st.fg, status, item.y, smem_raw);
@@ -143,6 +160,11 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
     }
     __syncthreads();
     if (tid == 0) {
+      // Per kind: tiles, cycles waiting (dependency + descriptor), cycles running.
+      const long long c_end = clock64();
+      atomicAdd(stats + 3 * st.kind, 1ull);
+      atomicAdd(stats + 3 * st.kind + 1, static_cast<unsigned long long>(c_run - c_wait));
+      atomicAdd(stats + 3 * st.kind + 2, static_cast<unsigned long long>(c_end - c_run));
       __threadfence();
       atomicAdd(done + item.x, 1u);
       if (*reinterpret_cast<volatile unsigned*>(status) != 0u) s_abort = 1;
@@ -155,9 +177,10 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
 // ------------------------------------------------------------- host side
 
 struct Tuning {
-  int lv_t0 = 8;       // coarse planes per load-vector tile
-  int fin_t0 = 4;      // plane pairs per finish tile
-  int rows = 64;       // lines per contiguous-solve tile
+  int lv_t0 = 16;      // coarse planes per load-vector tile
+  int fin_t0 = 8;      // plane pairs per finish tile
+  int rows = 128;      // lines per contiguous-solve tile
+  int groups = 4;      // 32-line groups per segmented-solve tile
 };
 
 struct BatchPlan {
@@ -169,6 +192,7 @@ struct BatchPlan {
   BatchStage* d_stages = nullptr;
   int4* d_items = nullptr;
   unsigned int* d_counters = nullptr;   // [0] head, [1 + s] done of stage s
+  unsigned long long* d_stats = nullptr;  // [3 * kinds] tiles, wait cycles, run cycles
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~BatchPlan() {
@@ -179,6 +203,7 @@ struct BatchPlan {
 };
 
 std::mutex g_bmu;
+BatchPlan* g_last = nullptr;  // the plan launched last (for mgard_batch_stats)
 std::map<std::string, std::unique_ptr<BatchPlan>> g_bplans;
 std::map<std::string, Tuning> g_tuned;  // by shape list
 
@@ -270,11 +295,14 @@ int field_stages(const DevPlan& p, float* data, char* ws, int dir, const Tuning&
       s.S = (a == 0) ? c1 * c2 : c2;
       s.nlines = (a == 0) ? s.S : c0 * s.S;
       s.block_stride = ax.nc * s.S;
-      s.ntiles = static_cast<int>((s.nlines + 31) / 32);
+      s.gpp = std::max(1, kBatchThreads / 32 / nseg);
+      s.groups = std::max(s.gpp, (std::max(1, tu.groups) + s.gpp - 1) / s.gpp * s.gpp);
+      s.ntiles = static_cast<int>((s.nlines + 32 * s.groups - 1) / (32 * s.groups));
       s.mode = (a == 0) ? mode : kApplyNone;
       s.F = F[l - 1];
       s.B = B[l - 1];
-      *smem = std::max(*smem, sizeof(float) * (5 * static_cast<size_t>(ax.nc) + 32 * nseg));
+      *smem = std::max(*smem, sizeof(float) * (5 * static_cast<size_t>(ax.nc) +
+                                               32 * static_cast<size_t>(nseg) * s.gpp));
       out.push_back(s);
     }
     return MGARD_OK;
@@ -360,11 +388,13 @@ int build_batch(int n, const int64_t* dims3, void* const* data, char* ws, size_t
   const size_t b_st = up(sizeof(BatchStage) * stages.size(), 256);
   const size_t b_it = up(sizeof(int4) * items.size(), 256);
   const size_t b_ct = up(sizeof(unsigned) * (1 + stages.size()), 256);
-  if (cudaMalloc(&bp.dmem, b_st + b_it + b_ct) != cudaSuccess) return MGARD_ERR_CUDA;
+  const size_t b_sx = up(sizeof(unsigned long long) * 3 * kBKinds, 256);
+  if (cudaMalloc(&bp.dmem, b_st + b_it + b_ct + b_sx) != cudaSuccess) return MGARD_ERR_CUDA;
   char* d = static_cast<char*>(bp.dmem);
   bp.d_stages = reinterpret_cast<BatchStage*>(d);
   bp.d_items = reinterpret_cast<int4*>(d + b_st);
   bp.d_counters = reinterpret_cast<unsigned*>(d + b_st + b_it);
+  bp.d_stats = reinterpret_cast<unsigned long long*>(d + b_st + b_it + b_ct);
   if (cudaMemcpy(bp.d_stages, stages.data(), sizeof(BatchStage) * stages.size(),
                  cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(bp.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
@@ -387,15 +417,19 @@ int build_batch(int n, const int64_t* dims3, void* const* data, char* ws, size_t
   mp.width = 1 + stages.size();
   mp.height = 1;
   mp.value = 0;
-  cudaGraphNode_t n_set = nullptr, n_run = nullptr;
+  cudaGraphNode_t n_set = nullptr, n_run = nullptr, n_sx = nullptr;
   if (cudaGraphAddMemsetNode(&n_set, bp.graph, nullptr, 0, &mp) != cudaSuccess) return MGARD_ERR_CUDA;
+  mp.dst = bp.d_stats;
+  mp.width = 2 * 3 * kBKinds;  // 64-bit words as pairs of 32-bit zeros
+  if (cudaGraphAddMemsetNode(&n_sx, bp.graph, &n_set, 1, &mp) != cudaSuccess) return MGARD_ERR_CUDA;
   const BatchStage* a_st = bp.d_stages;
   const int4* a_it = bp.d_items;
   int a_n = bp.nitems;
   unsigned* a_head = bp.d_counters;
   unsigned* a_done = bp.d_counters + 1;
   unsigned* a_status = status;
-  void* args[] = {&a_st, &a_it, &a_n, &a_head, &a_done, &a_status};
+  unsigned long long* a_stats = bp.d_stats;
+  void* args[] = {&a_st, &a_it, &a_n, &a_head, &a_done, &a_status, &a_stats};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof kp);
   kp.func = reinterpret_cast<void*>(batch_kernel);
@@ -403,7 +437,7 @@ int build_batch(int n, const int64_t* dims3, void* const* data, char* ws, size_t
   kp.blockDim = dim3(kBatchThreads);
   kp.sharedMemBytes = static_cast<unsigned>(smem);
   kp.kernelParams = args;
-  if (cudaGraphAddKernelNode(&n_run, bp.graph, &n_set, 1, &kp) != cudaSuccess) return MGARD_ERR_CUDA;
+  if (cudaGraphAddKernelNode(&n_run, bp.graph, &n_sx, 1, &kp) != cudaSuccess) return MGARD_ERR_CUDA;
   if (cudaGraphInstantiate(&bp.exec, bp.graph, 0) != cudaSuccess) return MGARD_ERR_CUDA;
   return MGARD_OK;
 }
@@ -447,6 +481,7 @@ int batch_run(int dir, int n, const int64_t* dims3, void* const* data, void* wor
     if (rc != MGARD_OK) return rc;
     it = g_bplans.emplace(key, std::move(bp)).first;
   }
+  g_last = it->second.get();
   return cudaGraphLaunch(it->second->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? MGARD_OK
              : MGARD_ERR_CUDA;
@@ -512,13 +547,15 @@ int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, v
   Tuning best;
   float best_ms = 1e30f;
   rc = MGARD_OK;
-  for (int lv_t0 : {4, 8, 16})
-    for (int fin_t0 : {2, 4, 8})
-      for (int rows : {32, 64}) {
+  for (int lv_t0 : {8, 16, 32})
+    for (int fin_t0 : {4, 8, 16})
+      for (int rows : {64, 128})
+        for (int groups : {1, 4, 8}) {
         Tuning tu;
         tu.lv_t0 = lv_t0;
         tu.fin_t0 = fin_t0;
         tu.rows = rows;
+        tu.groups = groups;
         float ms = 0.f;
         for (int rep = 0; rep < 2 && rc == MGARD_OK; ++rep) {  // the first run builds the plan
           cudaEventRecord(e0, s);
@@ -553,6 +590,7 @@ int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, v
     choice_out[0] = best.lv_t0;
     choice_out[1] = best.fin_t0;
     choice_out[2] = best.rows;
+    choice_out[3] = best.groups;
   }
   return MGARD_OK;
 }
@@ -560,7 +598,19 @@ int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, v
 int mgard_batch_release(void) {
   std::lock_guard<std::mutex> lk(g_bmu);
   g_bplans.clear();
+  g_last = nullptr;
   return MGARD_OK;
+}
+
+int mgard_batch_stats(uint64_t* out, int n) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  if (out == nullptr || n < 3 * kBKinds) return MGARD_ERR_ARG;
+  if (g_last == nullptr) return MGARD_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MGARD_ERR_CUDA;
+  return cudaMemcpy(out, g_last->d_stats, sizeof(uint64_t) * 3 * kBKinds, cudaMemcpyDeviceToHost) ==
+                 cudaSuccess
+             ? MGARD_OK
+             : MGARD_ERR_CUDA;
 }
 
 }  // extern "C"

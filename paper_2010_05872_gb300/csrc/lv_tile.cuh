@@ -194,6 +194,8 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
       pending |= 1u << ns;
     }
 
+    // Warps without a column of this tile skip the arithmetic.
+    if (tid < ((T2 + 31) & ~31)) {
     const bool pn = !is_coef(j, n0);  // nodal plane
     const int kj = pn ? nodal_k(j, n0, c0) : -1;
     const bool gplane = pn && kj >= K0 && kj < K0 + T0;
@@ -256,6 +258,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc[k][t] += wk[k] * G1[t] - yk[k] * H1[t];
     store_done(j, false);
+    }
     __syncthreads();  // every read of this buffer is done
   }
   store_done(jhi, true);

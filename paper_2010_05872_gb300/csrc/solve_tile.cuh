@@ -210,16 +210,20 @@ template <typename T>
 __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict__ F,
                                                T* __restrict__ B, int64_t nlines, int64_t S,
                                                int64_t block_stride, int mode, int tile,
-                                               unsigned char* smem_raw) {
+                                               unsigned char* smem_raw, int gpp = 1) {
+  // gpp groups of 32 lines side by side: warps [g nseg, (g + 1) nseg) take
+  // group g of the tile (tile gpp + g); warps beyond gpp nseg idle.
   const int nc = ax.nc, L = ax.seg_len;
-  const int nseg = (nc + L - 1) / L;  // warps beyond nseg idle (a larger block)
+  const int nseg = (nc + L - 1) / L;
   T* s_tm = reinterpret_cast<T*>(smem_raw);
   T* s_sb = s_tm + nc;
   T* s_sg = s_sb + nc;
   T* s_sy = s_sg + nc;
   T* s_sh = s_sy + nc;
-  T* s_c = s_sh + nc;  // nseg x 32 boundary values
-  const int tid = threadIdx.x, lane = tid & 31, sgi = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gslot = (tid >> 5) / nseg;
+  const int sgi = gslot < gpp ? (tid >> 5) - gslot * nseg : nseg;  // nseg: idle warp
+  T* s_c = s_sh + nc + static_cast<size_t>(min(gslot, gpp - 1)) * nseg * 32;  // nseg x 32 per group
   for (int k = tid; k < nc; k += blockDim.x) {
     s_tm[k] = ax.tm[k];
     s_sb[k] = ax.sb[k];
@@ -227,7 +231,7 @@ __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict
     s_sy[k] = ax.sy[k];
     s_sh[k] = ax.sh[k];
   }
-  const int64_t line = static_cast<int64_t>(tile) * 32 + lane;
+  const int64_t line = (static_cast<int64_t>(tile) * gpp + min(gslot, gpp - 1)) * 32 + lane;
   const bool valid = line < nlines;
   const int64_t o = valid ? line / S : 0, in = valid ? line - o * S : 0;
   const int64_t base = o * block_stride + in;

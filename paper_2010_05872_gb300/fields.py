@@ -105,6 +105,37 @@ def grf_field(dims, seed: int = SEED_LARGE, slope: float = -5.0 / 3.0,
     return u.astype(dtype)
 
 
+def grf_field_device(dims, seed: int, device="cuda", slope: float = -5.0 / 3.0):
+    """The k^-5/3 field recipe of ``grf_field`` generated on a CUDA device
+    (torch's seeded normal generator and FFTs in FP64), FP32 result: the
+    input generator of the batched and serving workloads, where hundreds of
+    fields are needed.  Its white noise is torch's, not numpy's, so the
+    values differ from ``grf_field`` for the same seed."""
+    import torch
+    dims = tuple(int(n) for n in dims)
+    ndim = len(dims)
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    white = torch.randn(dims, generator=g, device=device, dtype=torch.float64)
+    spec = torch.fft.rfftn(white)
+    del white
+    k2 = None
+    for d, n in enumerate(dims):
+        f = (torch.fft.rfftfreq(n, device=device) if d == ndim - 1
+             else torch.fft.fftfreq(n, device=device)).double() * n
+        shape = [1] * ndim
+        shape[d] = f.numel()
+        term = (f ** 2).reshape(shape)
+        k2 = term if k2 is None else k2 + term
+    amp = torch.where(k2 > 0, k2.clamp_min(1e-300) ** ((slope - ndim + 1) / 4.0),
+                      torch.zeros_like(k2))
+    spec *= amp
+    u = torch.fft.irfftn(spec, s=dims)
+    del spec
+    u -= u.mean()
+    u /= u.std()
+    return u.float()
+
+
 def front_field(dims, coords, seed: int = SEED_NONUNIFORM, n_modes: int = 3,
                 width_cells: float = 5.0, dtype=np.float32) -> np.ndarray:
     """Smooth sinusoid sum plus a sharp ``tanh`` front across the diagonal

@@ -74,7 +74,8 @@ def test_batch_autotune_keeps_fields(cuda):
     orig = [x.clone() for x in xs]
     ws = B.batch_workspace(xs)
     choice = B.batch_autotune(xs, ws)
-    assert choice[0] in (4, 8, 16) and choice[1] in (2, 4, 8) and choice[2] in (32, 64)
+    assert choice[0] in (8, 16, 32) and choice[1] in (4, 8, 16) and choice[2] in (64, 128)
+    assert choice[3] in (1, 4, 8)
     for x, o in zip(xs, orig):
         assert torch.equal(x, o)
     ref = [x.clone() for x in xs]
