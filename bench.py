@@ -48,8 +48,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
-                    help="single: the 513^3 field (default); batched: 256 uneven fields")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+                    help="single: the 513^3 field (default); batched: 256 uneven fields; "
+                         "serving: a Poisson request stream")
+    ap.add_argument("--serving-requests", type=int, default=2000, help=argparse.SUPPRESS)
     ap.add_argument("--case-dims", default="513x513x513", help=argparse.SUPPRESS)
     ap.add_argument("--batch-count", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", action="store_true",
@@ -656,6 +658,120 @@ def run_batched(args, rank, world, local_rank):
         }))
 
 
+def run_serving(args):
+    """Serving workload: a seeded Poisson stream (mean 200 requests/s) of
+    compress / decompress requests on FP32 k^-5/3 fields, 2D sides from
+    {1024, 1025, 2048, 2049, 4096} or 3D sides from {129, 257, 513}, bounds
+    from {1e-2, 1e-3, 1e-4} x range, admitted against a 120 GB HBM budget by
+    the library's serving loop; p50 / p99 latency and aggregate GB/s."""
+    import numpy as np
+    import torch
+    from paper_2010_05872_gb300 import binding as B
+    from paper_2010_05872_gb300 import build as build_mod
+    from paper_2010_05872_gb300 import fields as F
+    build_mod.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(F.SEED_SERVING)
+    shapes = [(s, s) for s in (1024, 1025, 2048, 2049, 4096)] + [(s, s, s) for s in (129, 257, 513)]
+    nreq = args.serving_requests
+    gaps = rng.exponential(1.0 / 200.0, size=nreq)
+    arrive = np.cumsum(gaps)
+    kinds = rng.random(nreq) < 0.5                     # True: compress
+    is3d = rng.random(nreq) < 0.5
+    pick = np.where(is3d, 5 + rng.integers(0, 3, nreq), rng.integers(0, 5, nreq))
+    rels = rng.choice([1e-2, 1e-3, 1e-4], size=nreq)
+    # One field per shape (pinned), compressed once beforehand: the inputs of
+    # the decompress requests.  Output buffers are recycled per shape.
+    fields, packed, pools = [], [], []
+    srv = B.Server(hbm_budget=120 << 30, slots=8)
+    for i, shp in enumerate(shapes):
+        f = F.grf_field_device(shp, F.SEED_SERVING + i).cpu().ravel().pin_memory()
+        fields.append(f)
+        lab = torch.empty(f.numel(), dtype=torch.int64).pin_memory()
+        srv.submit(B.OP_COMPRESS, shp, f, lab, rel_bound=1e-3)
+        srv.drain()
+        (_, st, _, tau), = srv.poll()
+        assert st == 0
+        packed.append((lab, tau))
+        pools.append([torch.empty(f.numel(), dtype=torch.int64).pin_memory() for _ in range(3)])
+    free = [list(range(3)) for _ in shapes]
+    inflight = {}
+    lat = {"compress": [], "decompress": []}
+    nbytes = 0
+    t0 = time.perf_counter()
+    k = 0
+    done_n = 0
+    first_arrival = None
+    last_done = None
+    while done_n < nreq:
+        now = time.perf_counter() - t0
+        while k < nreq and arrive[k] <= now and free[pick[k]]:
+            i = int(pick[k])
+            slot = free[i].pop()
+            buf = pools[i][slot]
+            if kinds[k]:
+                rid = srv.submit(B.OP_COMPRESS, shapes[i], fields[i], buf, rel_bound=float(rels[k]))
+            else:
+                rid = srv.submit(B.OP_DECOMPRESS, shapes[i], packed[i][0], buf.view(torch.float32)[
+                    :fields[i].numel()], tau=packed[i][1])
+            inflight[rid] = (i, slot, "compress" if kinds[k] else "decompress", arrive[k])
+            if first_arrival is None:
+                first_arrival = now
+            k += 1
+        for rid, st, l, _ in srv.poll():
+            i, slot, kind, a = inflight.pop(rid)
+            assert st == 0, st
+            free[i].append(slot)
+            # Latency from the request's scheduled arrival (queueing for a
+            # host buffer included) to completion.
+            lat[kind].append(time.perf_counter() - t0 - a)
+            nbytes += fields[i].numel() * 4
+            done_n += 1
+            last_done = time.perf_counter() - t0
+        time.sleep(0.0002)
+    wall = last_done - arrive[0]
+    counters = srv.counters()
+    # Mix vs alone: the first 16 request kinds again, one at a time.
+    same = True
+    for j in range(16):
+        i = int(pick[j])
+        if kinds[j]:
+            a = torch.empty(fields[i].numel(), dtype=torch.int64).pin_memory()
+            b = torch.empty_like(a).pin_memory()
+            srv.submit(B.OP_COMPRESS, shapes[i], fields[i], a, rel_bound=float(rels[j]))
+            srv.drain()
+            srv.poll()
+            srv2 = B.Server(hbm_budget=120 << 30, slots=1)
+            srv2.submit(B.OP_COMPRESS, shapes[i], fields[i], b, rel_bound=float(rels[j]))
+            srv2.drain()
+            srv2.poll()
+            srv2.close()
+            same = same and torch.equal(a, b)
+    srv.close()
+    allat = sorted(lat["compress"] + lat["decompress"])
+
+    def pct(v, q):
+        v = sorted(v)
+        return 1e3 * v[min(len(v) - 1, int(q * len(v)))] if v else None
+
+    print(json.dumps({
+        "metric": "serving aggregate GB/s (field bytes) with p50/p99 latency",
+        "value": nbytes / wall / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": nreq, "warmup": len(shapes),
+        "ms_per_step": 1e3 * wall / nreq, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Poisson 200 req/s, %d requests, 50%% compress / 50%% decompress, "
+                               "2D sides {1024,1025,2048,2049,4096} or 3D sides {129,257,513}, "
+                               "k^-5/3 FP32 fields, bounds {1e-2,1e-3,1e-4} x range" % nreq,
+                   "hbm_budget_gb": 120, "slots": 8},
+        "latency_ms": {"p50": pct(allat, 0.5), "p99": pct(allat, 0.99),
+                       "compress_p50": pct(lat["compress"], 0.5), "compress_p99": pct(lat["compress"], 0.99),
+                       "decompress_p50": pct(lat["decompress"], 0.5),
+                       "decompress_p99": pct(lat["decompress"], 0.99)},
+        "peak_running": counters["peak_running"], "peak_bytes_gb": counters["peak_bytes"] / 1e9,
+        "wall_s": wall, "same_alone_and_in_mix": same,
+    }))
+
+
 def main():
     args = parse_args()
     if args.kernel_case:
@@ -669,6 +785,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     if args.workload == "batched":
         if world > 1:

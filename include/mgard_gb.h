@@ -206,6 +206,52 @@ int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, v
 int mgard_batch_release(void);
 int mgard_batch_stats(uint64_t* out, int n);
 
+/* Serving: a request loop with continuous batching on the current device
+ * (an interface of this library; the paper compresses one field per call).
+ * A request is a whole compression (host field -> value range, decomposition
+ * at stop_level, level-wise quantization at rel_bound x range -> host
+ * labels; Section 2, Section 4.1) or a whole decompression (host labels and
+ * the absolute bound tau used at compression -> dequantization,
+ * recomposition -> host field), on uniform grids (NULL coords).
+ *  - mgard_server_create starts a scheduler thread owning `slots` streams.
+ *    Requests are admitted in arrival order as soon as a stream is free and
+ *    their device memory (field, labels, workspace; drawn from the device's
+ *    stream-ordered memory pool, kept for reuse up to the budget) fits in
+ *    `hbm_budget` bytes beside the admitted ones; admitted requests overlap
+ *    on the device.  Plans stay resident in the plan cache.
+ *  - mgard_server_submit queues a request (the host buffers must stay valid
+ *    until its completion is polled; pinned buffers let copies overlap) and
+ *    returns its id; a request that alone exceeds the budget is rejected with
+ *    MGARD_ERR_WORKSPACE.
+ *  - mgard_server_poll returns up to `max` completed requests in completion
+ *    order: id, status (MGARD_OK or an error code), latency in seconds from
+ *    submission to the scheduler seeing the last device work end, and the
+ *    absolute bound tau used (compression) or given (decompression).  Any
+ *    output array may be NULL.
+ *  - mgard_server_drain waits (up to timeout_s seconds) until no request is
+ *    queued or running; mgard_server_counters writes {queued, running, bytes
+ *    in use, peak running, peak bytes in use}; mgard_server_destroy drains and
+ *    stops the thread. */
+enum { MGARD_OP_COMPRESS = 1, MGARD_OP_DECOMPRESS = 2 };
+typedef struct {
+  int op;             /* MGARD_OP_COMPRESS or MGARD_OP_DECOMPRESS */
+  int ndim;
+  int64_t dims[3];    /* the first ndim entries are used */
+  int dtype;          /* MGARD_F32 or MGARD_F64 */
+  int stop_level;
+  double rel_bound;   /* compression: bound relative to max - min of the field */
+  double tau;         /* decompression: absolute bound used at compression */
+  const void* host_in;  /* compression: field; decompression: int64 labels */
+  void* host_out;       /* compression: int64 labels; decompression: field */
+} mgard_request;
+int mgard_server_create(size_t hbm_budget, int slots, void** server);
+int mgard_server_submit(void* server, const mgard_request* req, int64_t* id_out);
+int mgard_server_poll(void* server, int max, int64_t* ids, int* status, double* latency_s,
+                      double* tau, int* count_out);
+int mgard_server_drain(void* server, double timeout_s);
+int mgard_server_counters(void* server, int64_t* out5);
+int mgard_server_destroy(void* server);
+
 /* Allocation-free decomposition (the paper has no counterpart; an interface
  * choice).  Same result as mgard_decompose (Section 2, decomposition;
  * Algorithm 1 lines 12-16) with the same kernels, for callers that must not

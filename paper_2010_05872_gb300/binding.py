@@ -69,6 +69,16 @@ _SIGNATURES = {
                                             ctypes.c_size_t, _VP, ctypes.POINTER(ctypes.c_int)]),
     "mgard_batch_release": (ctypes.c_int, []),
     "mgard_batch_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
+    "mgard_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "mgard_server_submit": (ctypes.c_int, [_VP, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "mgard_server_poll": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "mgard_server_drain": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "mgard_server_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "mgard_server_destroy": (ctypes.c_int, [_VP]),
     "mgard_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "mgard_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
@@ -228,6 +238,75 @@ def mgard_batch_stats():
 
 def mgard_batch_release() -> int:
     return lib().mgard_batch_release()
+
+
+OP_COMPRESS, OP_DECOMPRESS = 1, 2
+
+
+class MgardRequest(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("ndim", ctypes.c_int), ("dims", ctypes.c_int64 * 3),
+                ("dtype", ctypes.c_int), ("stop_level", ctypes.c_int),
+                ("rel_bound", ctypes.c_double), ("tau", ctypes.c_double),
+                ("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p)]
+
+
+class Server:
+    """The serving loop of the library (continuous batching on one device).
+    Host buffers are tensors (pinned for overlapped copies) kept alive here
+    until their request completes."""
+
+    def __init__(self, hbm_budget: int, slots: int = 8):
+        self.h = _VP()
+        _check(lib().mgard_server_create(int(hbm_budget), int(slots), ctypes.byref(self.h)),
+               "mgard_server_create")
+        self._keep = {}
+
+    def submit(self, op, shape, host_in, host_out, rel_bound=0.0, tau=0.0, stop_level=0,
+               dtype=None):
+        req = MgardRequest()
+        req.op = op
+        req.ndim = len(shape)
+        for i, n in enumerate(shape):
+            req.dims[i] = int(n)
+        req.dtype = F32 if dtype is None else dtype
+        req.stop_level = stop_level
+        req.rel_bound = rel_bound
+        req.tau = tau
+        req.host_in = host_in.data_ptr()
+        req.host_out = host_out.data_ptr()
+        rid = ctypes.c_int64()
+        _check(lib().mgard_server_submit(self.h, ctypes.byref(req), ctypes.byref(rid)),
+               "mgard_server_submit")
+        self._keep[rid.value] = (host_in, host_out)
+        return rid.value
+
+    def poll(self, max_items: int = 4096):
+        """Completed requests: list of (id, status, latency_s, tau)."""
+        ids = (ctypes.c_int64 * max_items)()
+        st = (ctypes.c_int * max_items)()
+        lat = (ctypes.c_double * max_items)()
+        tau = (ctypes.c_double * max_items)()
+        n = ctypes.c_int()
+        _check(lib().mgard_server_poll(self.h, max_items, ids, st, lat, tau, ctypes.byref(n)),
+               "mgard_server_poll")
+        out = [(ids[i], st[i], lat[i], tau[i]) for i in range(n.value)]
+        for rid, *_ in out:
+            self._keep.pop(rid, None)
+        return out
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(lib().mgard_server_drain(self.h, float(timeout_s)), "mgard_server_drain")
+
+    def counters(self):
+        out = (ctypes.c_int64 * 5)()
+        _check(lib().mgard_server_counters(self.h, out), "mgard_server_counters")
+        return dict(queued=out[0], running=out[1], bytes_in_use=out[2], peak_running=out[3],
+                    peak_bytes=out[4])
+
+    def close(self):
+        if self.h:
+            lib().mgard_server_destroy(self.h)
+            self.h = _VP()
 
 
 def mgard_recompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:

@@ -289,6 +289,17 @@ int transform_host(bool dec, int ndim, const int64_t* dims, const double* const*
   return MGARD_OK;
 }
 
+}  // namespace
+
+int run_transform(bool dec, const DevPlan& p, int stop_level, void* data, char* ws,
+                  unsigned int* status, cudaStream_t s) {
+  if (p.dtype == MGARD_F64)
+    return dec ? run_decompose<double>(p, stop_level, static_cast<double*>(data), ws, status, s)
+               : run_recompose<double>(p, stop_level, static_cast<double*>(data), ws, status, s);
+  return dec ? run_decompose<float>(p, stop_level, static_cast<float*>(data), ws, status, s)
+             : run_recompose<float>(p, stop_level, static_cast<float*>(data), ws, status, s);
+}
+
 int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, double* tau_out) {
   if (!(tau > 0.0) || !std::isfinite(tau)) return MGARD_ERR_ARG;
   if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
@@ -319,7 +330,6 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
   return MGARD_OK;
 }
 
-}  // namespace
 }  // namespace mgb
 
 using namespace mgb;

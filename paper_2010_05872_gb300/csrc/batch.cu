@@ -124,17 +124,17 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
     const long long c_run = clock64();
     switch (st.kind) {
       case kBLoadVecDec:
-        load_vector_march_tile<float, true, kLvNS, kLvT1, true>(st.lv, st.fine, st.coarse, st.F,
+        load_vector_march_tile<float, true, kLvNS, kLvT1, true, true>(st.lv, st.fine, st.coarse, st.F,
                                                                 st.mg, st.fine_count, status,
                                                                 item.y, smem_raw);
         break;
       case kBLoadVecRec:
-        load_vector_march_tile<float, false, kLvNS, kLvT1, true>(st.lv, st.fine, st.coarse, st.F,
+        load_vector_march_tile<float, false, kLvNS, kLvT1, true, true>(st.lv, st.fine, st.coarse, st.F,
                                                                  st.mg, st.fine_count, status,
                                                                  item.y, smem_raw);
         break;
       case kBSolveContigTma:
-        solve_contig_tma_tile<float>(st.lv.ax[2], st.F, st.B, st.nlines, st.rows, st.mode, status,
+        solve_contig_tma_tile<float, true>(st.lv.ax[2], st.F, st.B, st.nlines, st.rows, st.mode, status,
                                      item.y, smem_raw);
         break;
       case kBSolveContig:
@@ -148,13 +148,13 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
           const int64_t t = static_cast<int64_t>(item.y) * passes + q;
           if (t * st.gpp * 32 >= st.nlines) break;
           if (q > 0) __syncthreads();  // the previous pass's reads of shared memory are done
-          solve_seg_tile<float>(st.lv.ax[st.axis], st.F, st.B, st.nlines, st.S, st.block_stride,
+          solve_seg_tile<float, true>(st.lv.ax[st.axis], st.F, st.B, st.nlines, st.S, st.block_stride,
                                 st.mode, static_cast<int>(t), smem_raw, st.gpp);
         }
         break;
       }
       default:
-        finish_march_tile<float, kFinNS, kFinT1>(st.lv, st.nodal_src, st.interp_src, st.sign,
+        finish_march_tile<float, kFinNS, kFinT1, true>(st.lv, st.nodal_src, st.interp_src, st.sign,
                                                  st.fine, st.fg, status, item.y, smem_raw);
         break;
     }

@@ -58,4 +58,14 @@ DevCtx* get_ctx();
 template <typename T>
 const std::vector<LevelK<T>>& levels(const DevPlan& p);
 
+// Enqueue the decomposition (dec) or recomposition of `data` on `s` with the
+// workspace `ws`; `status` receives wait timeouts.  No synchronization.
+int run_transform(bool dec, const DevPlan& p, int stop_level, void* data, char* ws,
+                  unsigned int* status, cudaStream_t s);
+
+// Bin widths of every level for the absolute bound `tau` (host FP64, Eq.
+// LinfTau), with the FP32 helpers of the quantizer's fast paths; tau_out
+// (L + 1 values, may be NULL) receives the level tolerances.
+int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, double* tau_out);
+
 }  // namespace mgb

@@ -51,13 +51,15 @@ struct FinishGeom {
 // `smem_raw` is the dynamic shared memory.  Any block of at least g.threads
 // threads runs it; a tile returns with its barriers invalidated so that the
 // next tile of a persistent CTA can set them up again.
-template <typename T, int NS, int T1C>
+template <typename T, int NS, int T1C, bool PERSIST = false>
 __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
                                                   const T* __restrict__ nodal_src,
                                                   const T* __restrict__ interp_src, T sign,
                                                   T* __restrict__ fine, const FinishGeom& g,
                                                   unsigned int* __restrict__ status, int tile,
-                                                  unsigned char* smem_raw) {
+                                                  unsigned char*) {
+  // The dynamic shared memory of the launch (every tile starts at its base).
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int NC = NS + 1;  // coarse ring
   constexpr int R1M = 2 * T1C, RCM = T1C + 1;
   __shared__ __align__(8) uint64_t bars[NS];
@@ -115,7 +117,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
     *shift_slot = shift;
     if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(src) + ab, bytes, bar);
     for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
-      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = __ldcg(src + x / sizeof(T));
+      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = PERSIST ? __ldcg(src + x / sizeof(T)) : src[x / sizeof(T)];
     return bytes;
   };
   // Stage for plane pair m: fine planes 2m, 2m + 1, coarse plane m + 1 and,
@@ -260,7 +262,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
     }
     __syncthreads();  // this stage's buffers may be refilled
   }
-  if (tid == 0)
+  if (PERSIST && tid == 0)
     for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
 }
 

@@ -35,17 +35,20 @@ struct MarchCfg<double> {
 };
 
 // One tile (CTA work unit) of the marching load vector; `tile` plays the
-// role of the block index and `smem_raw` is the dynamic shared memory.  Any
-// block of at least g.threads threads runs it; a tile returns with its
-// barriers invalidated so that the next tile of a persistent CTA can set
-// them up again.
-template <typename T, bool DEC, int NS, int T1C, bool THREE>
+// role of the block index.  Any block of at least g.threads threads runs
+// it.  PERSIST: the CTA runs further tiles in the same launch, so the tile
+// invalidates its barriers at the end (the next tile sets them up again) and
+// reads its few plain-loaded elements through L2 (other CTAs of the launch
+// may have written them).
+template <typename T, bool DEC, int NS, int T1C, bool THREE, bool PERSIST = false>
 __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
                                                        const T* __restrict__ fine,
                                                        T* __restrict__ coarse, T* __restrict__ F,
                                                        const MarchGeom& g, uint64_t fine_count,
                                                        unsigned int* __restrict__ status, int tile,
-                                                       unsigned char* smem_raw) {
+                                                       unsigned char*) {
+  // The dynamic shared memory of the launch (every tile starts at its base).
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int S1M = THREE ? 2 * T1C + 3 : 1;  // staged rows
   constexpr int TM = THREE ? T1C : 1;           // coarse rows per CTA
   constexpr int VEC = 16 / sizeof(T);
@@ -144,7 +147,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     mbar_arrive_expect_tx(&bars[slot], bytes);
     if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(fine) + ab, bytes, &bars[slot]);
     for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
-      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = __ldcg(fine + x / sizeof(T));
+      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = PERSIST ? __ldcg(fine + x / sizeof(T)) : fine[x / sizeof(T)];
   };
 
   T acc[3][TM];
@@ -262,7 +265,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     __syncthreads();  // every read of this buffer is done
   }
   store_done(jhi, true);
-  if (tid == 0)
+  if (PERSIST && tid == 0)
     for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
 }
 

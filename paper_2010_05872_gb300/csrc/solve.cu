@@ -95,12 +95,110 @@ solve_contig_tma_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64
   solve_contig_tma_tile<T>(ax, F, B, nlines, rows, mode, status, blockIdx.x, smem_raw);
 }
 
+// The per-level form keeps its own body (one 32-line group per CTA of
+// exactly nseg warps); solve_seg_tile is the same method for the persistent
+// batched kernel, with several groups side by side.
 template <typename T>
 __global__ void __launch_bounds__(32 * kSegWarps, 2)
 solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines, int64_t S,
                  int64_t block_stride, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  solve_seg_tile<T>(ax, F, B, nlines, S, block_stride, mode, blockIdx.x, smem_raw);
+  const int nc = ax.nc, L = ax.seg_len;
+  const int nseg = blockDim.x >> 5;
+  T* s_tm = reinterpret_cast<T*>(smem_raw);
+  T* s_sb = s_tm + nc;
+  T* s_sg = s_sb + nc;
+  T* s_sy = s_sg + nc;
+  T* s_sh = s_sy + nc;
+  T* s_c = s_sh + nc;  // nseg x 32 boundary values
+  const int tid = threadIdx.x, lane = tid & 31, sgi = tid >> 5;
+  for (int k = tid; k < nc; k += blockDim.x) {
+    s_tm[k] = ax.tm[k];
+    s_sb[k] = ax.sb[k];
+    s_sg[k] = ax.sg[k];
+    s_sy[k] = ax.sy[k];
+    s_sh[k] = ax.sh[k];
+  }
+  const int64_t line = static_cast<int64_t>(blockIdx.x) * 32 + lane;
+  const bool valid = line < nlines;
+  const int64_t o = valid ? line / S : 0, in = valid ? line - o * S : 0;
+  const int64_t base = o * block_stride + in;
+  const int k0 = sgi * L, len = max(0, min(L, nc - k0));
+  T v[kSegMax];
+  {
+    const T* p = F + base + static_cast<int64_t>(k0) * S;
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j) {
+      v[j] = (valid && j < len) ? *p : T(0);
+      p += S;
+    }
+  }
+  __syncthreads();
+  // Forward from a zero boundary value.
+  T y = T(0);
+#pragma unroll
+  for (int j = 0; j < kSegMax; ++j) {
+    if (j < len) {
+      y = s_tm[k0 + j] * v[j] + s_sb[k0 + j] * y;
+      v[j] = y;
+    }
+  }
+  s_c[sgi * 32 + lane] = y;
+  __syncthreads();
+  T Y = T(0);  // final y at the end of the previous segment
+  for (int q = 0; q < sgi; ++q) Y = s_c[q * 32 + lane] + s_sg[min(q * L + L, nc) - 1] * Y;
+#pragma unroll
+  for (int j = 0; j < kSegMax; ++j)
+    if (j < len) v[j] += s_sg[k0 + j] * Y;
+  __syncthreads();  // every read of the forward boundary values is done
+  // Backward from a zero boundary value.
+  T x = T(0);
+#pragma unroll
+  for (int j = kSegMax - 1; j >= 0; --j) {
+    if (j < len) {
+      x = v[j] + s_sy[k0 + j] * x;
+      v[j] = x;
+    }
+  }
+  s_c[sgi * 32 + lane] = x;
+  __syncthreads();
+  T X = T(0);  // final x at the start of the next segment
+  for (int q = nseg - 1; q > sgi; --q) X = s_c[q * 32 + lane] + s_sh[q * L] * X;
+  if (!valid) return;
+#pragma unroll
+  for (int j = 0; j < kSegMax; ++j)
+    if (j < len) v[j] += s_sh[k0 + j] * X;
+  T* pf = F + base + static_cast<int64_t>(k0) * S;
+  if (mode == kApplyNone) {
+#pragma unroll
+    for (int j = 0; j < kSegMax; ++j) {
+      if (j < len) *pf = v[j];
+      pf += S;
+    }
+    return;
+  }
+  // Apply in groups of 8 (B loads in flight together).
+  T* pb = B + base + static_cast<int64_t>(k0) * S;
+#pragma unroll
+  for (int j0 = 0; j0 < kSegMax; j0 += 8) {
+    T bv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) bv[u] = (j0 + u < len) ? pb[static_cast<int64_t>(u) * S] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (j0 + u < len) {
+        const int64_t off = static_cast<int64_t>(u) * S;
+        if (mode == kApplyDecompose) {
+          pb[off] = bv[u] + v[j0 + u];
+          pf[off] = bv[u];
+        } else {
+          pb[off] = bv[u] - v[j0 + u];
+        }
+      }
+    }
+    pb += 8 * S;
+    pf += 8 * S;
+  }
 }
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }

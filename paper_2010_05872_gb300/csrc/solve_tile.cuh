@@ -31,7 +31,9 @@ __device__ __forceinline__ void apply_x(T* F, T* B, int64_t idx, T x, T old_b, i
 template <typename T>
 __device__ __forceinline__ void solve_contig_tile(const AxisK<T>& ax, T* __restrict__ F,
                                                   T* __restrict__ B, int64_t nlines, int rows,
-                                                  int mode, int tile, unsigned char* smem_raw) {
+                                                  int mode, int tile, unsigned char*) {
+  // The dynamic shared memory of the launch (every tile starts at its base).
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int nc = ax.nc, pitch = nc | 1;
   const int64_t first = static_cast<int64_t>(tile) * rows;
@@ -107,11 +109,13 @@ __device__ __forceinline__ void solve_contig_tile(const AxisK<T>& ax, T* __restr
 // per line solves in place, then the range is written back with coalesced
 // stores.  The wait on the copy gives up after 2 s and records the failure
 // in `status`.
-template <typename T>
+template <typename T, bool PERSIST = false>
 __device__ __forceinline__ void solve_contig_tma_tile(const AxisK<T>& ax, T* __restrict__ F,
                                                       T* __restrict__ B, int64_t nlines, int rows,
                                                       int mode, unsigned int* __restrict__ status,
-                                                      int tile, unsigned char* smem_raw) {
+                                                      int tile, unsigned char*) {
+  // The dynamic shared memory of the launch (every tile starts at its base).
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_shift;
   const int nc = ax.nc;
@@ -139,7 +143,7 @@ __device__ __forceinline__ void solve_contig_tma_tile(const AxisK<T>& ax, T* __r
     mbar_arrive_expect_tx(&bar, bytes);
     if (bytes) tma_bulk_g2s(s, reinterpret_cast<const char*>(F) + ab, bytes, &bar);
     for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
-      s[shift + static_cast<int>((x - sb) / sizeof(T))] = __ldcg(F + x / sizeof(T));
+      s[shift + static_cast<int>((x - sb) / sizeof(T))] = PERSIST ? __ldcg(F + x / sizeof(T)) : F[x / sizeof(T)];
   }
   for (int k = tid; k < nc; k += blockDim.x) {
     s_ta[k] = ax.ta[k];
@@ -189,7 +193,7 @@ __device__ __forceinline__ void solve_contig_tma_tile(const AxisK<T>& ax, T* __r
       }
     }
   }
-  if (tid == 0) mbar_inval(&bar);
+  if (PERSIST && tid == 0) mbar_inval(&bar);
 }
 
 // Lines along a strided axis, split into segments of up to 32 rows: lane t
@@ -206,24 +210,29 @@ __device__ __forceinline__ void solve_contig_tma_tile(const AxisK<T>& ax, T* __r
 constexpr int kSegMax = 32;
 constexpr int kSegWarps = 9;  // lines of up to 288 rows
 
-template <typename T>
+template <typename T, bool MULTI = false>
 __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict__ F,
                                                T* __restrict__ B, int64_t nlines, int64_t S,
                                                int64_t block_stride, int mode, int tile,
-                                               unsigned char* smem_raw, int gpp = 1) {
+                                               unsigned char*, int gpp = 1) {
+  // The dynamic shared memory of the launch (every tile starts at its base).
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   // gpp groups of 32 lines side by side: warps [g nseg, (g + 1) nseg) take
   // group g of the tile (tile gpp + g); warps beyond gpp nseg idle.
   const int nc = ax.nc, L = ax.seg_len;
-  const int nseg = (nc + L - 1) / L;
+  const int nseg = MULTI ? (nc + L - 1) / L : static_cast<int>(blockDim.x >> 5);
   T* s_tm = reinterpret_cast<T*>(smem_raw);
   T* s_sb = s_tm + nc;
   T* s_sg = s_sb + nc;
   T* s_sy = s_sg + nc;
   T* s_sh = s_sy + nc;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int gslot = (tid >> 5) / nseg;
-  const int sgi = gslot < gpp ? (tid >> 5) - gslot * nseg : nseg;  // nseg: idle warp
-  T* s_c = s_sh + nc + static_cast<size_t>(min(gslot, gpp - 1)) * nseg * 32;  // nseg x 32 per group
+  // MULTI: gpp groups side by side (a persistent CTA); otherwise the block
+  // has exactly nseg warps and takes one group.
+  const int gslot = MULTI ? min((tid >> 5) / nseg, gpp) : 0;
+  const int sgi = !MULTI ? (tid >> 5) : gslot < gpp ? (tid >> 5) - gslot * nseg : nseg;
+  const int gsel = MULTI ? min(gslot, gpp - 1) : 0;
+  T* s_c = s_sh + nc + static_cast<size_t>(gsel) * nseg * 32;  // nseg x 32 per group
   for (int k = tid; k < nc; k += blockDim.x) {
     s_tm[k] = ax.tm[k];
     s_sb[k] = ax.sb[k];
@@ -231,7 +240,8 @@ __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict
     s_sy[k] = ax.sy[k];
     s_sh[k] = ax.sh[k];
   }
-  const int64_t line = (static_cast<int64_t>(tile) * gpp + min(gslot, gpp - 1)) * 32 + lane;
+  const int64_t line = MULTI ? (static_cast<int64_t>(tile) * gpp + gsel) * 32 + lane
+                             : static_cast<int64_t>(tile) * 32 + lane;
   const bool valid = line < nlines;
   const int64_t o = valid ? line / S : 0, in = valid ? line - o * S : 0;
   const int64_t base = o * block_stride + in;
@@ -255,10 +265,11 @@ __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict
       v[j] = y;
     }
   }
-  if (sgi < nseg) s_c[sgi * 32 + lane] = y;
+  if (!MULTI || sgi < nseg) s_c[sgi * 32 + lane] = y;
   __syncthreads();
   T Y = T(0);  // final y at the end of the previous segment
-  for (int q = 0; q < min(sgi, nseg); ++q) Y = s_c[q * 32 + lane] + s_sg[min(q * L + L, nc) - 1] * Y;
+  for (int q = 0; q < (MULTI ? min(sgi, nseg) : sgi); ++q)
+    Y = s_c[q * 32 + lane] + s_sg[min(q * L + L, nc) - 1] * Y;
 #pragma unroll
   for (int j = 0; j < kSegMax; ++j)
     if (j < len) v[j] += s_sg[k0 + j] * Y;
@@ -272,11 +283,11 @@ __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict
       v[j] = x;
     }
   }
-  if (sgi < nseg) s_c[sgi * 32 + lane] = x;
+  if (!MULTI || sgi < nseg) s_c[sgi * 32 + lane] = x;
   __syncthreads();
   T X = T(0);  // final x at the start of the next segment
   for (int q = nseg - 1; q > sgi; --q) X = s_c[q * 32 + lane] + s_sh[q * L] * X;
-  if (!valid || sgi >= nseg) return;
+  if (!valid || (MULTI && sgi >= nseg)) return;
 #pragma unroll
   for (int j = 0; j < kSegMax; ++j)
     if (j < len) v[j] += s_sh[k0 + j] * X;
