@@ -114,9 +114,9 @@ void build_axis(const std::vector<double>& x, AxisTables& t) {
     cprev = t.tc[k];
   }
 
-  // Segmented recurrences: segments of at most 32 rows, as even as possible.
+  // Segmented recurrences: segments of at most 16 rows, as even as possible.
   {
-    const int nseg = (nc + 31) / 32;
+    const int nseg = (nc + 15) / 16;
     const int L = (nc + nseg - 1) / nseg;
     t.seg_len = L;
     t.sb.assign(nc, 0.0); t.sg.assign(nc, 0.0); t.sy.assign(nc, 0.0); t.sh.assign(nc, 0.0);

@@ -207,8 +207,8 @@ __device__ __forceinline__ void solve_contig_tma_tile(const AxisK<T>& ax, T* __r
 // backward, the final x at the start of s is x_loc + sh_start * (final x at
 // the start of s + 1).  The boundary values pass between the warps through
 // shared memory.
-constexpr int kSegMax = 32;
-constexpr int kSegWarps = 9;  // lines of up to 288 rows
+constexpr int kSegMax = 16;
+constexpr int kSegWarps = 18;  // lines of up to 288 rows
 
 template <typename T, bool MULTI = false>
 __device__ __forceinline__ void solve_seg_tile(const AxisK<T>& ax, T* __restrict__ F,

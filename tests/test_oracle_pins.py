@@ -454,3 +454,34 @@ def test_worst_case_quantization_errors_within_bound():
         e = taus[lev] * rng.choice([-1.0, 1.0], size=dims)
         worst = max(worst, np.abs(O.recompose(e, H, 0)).max())
     assert worst <= tau
+
+
+# ------------------------------------------------ quantizer round trips ---
+
+def test_value_range_and_quantizer_hand_values():
+    """value_range, quantize and dequantize on hand-built values: bins of
+    width 2 tau around zero, labels and centres worked out by hand."""
+    u = np.array([-1.5, 0.25, 3.0, 2.0, -0.75])
+    assert O.value_range(u) == 4.5
+    assert O.value_range(np.float32([7.0, 7.0, 7.0])) == 0.0
+    H = O.Hierarchy((5,))
+    taus = np.full(H.L + 1, 0.25)       # every bin 0.5 wide
+    x = np.array([0.24, -0.25, 0.75, -1.26, 100.0])
+    # 0.48 -> 0; -0.5 -> -1 (tie away from zero); 1.5 -> 2 (tie); -2.52 -> -3; 200 -> 200
+    k = O.quantize(x, H, 0, taus)
+    assert k.tolist() == [0, -1, 2, -3, 200]
+    back = O.dequantize(k, H, 0, taus)
+    assert back.tolist() == [0.0, -0.5, 1.0, -1.5, 100.0]
+    assert np.abs(back - x).max() <= 0.25
+
+
+def test_dequantize_rounds_the_fp64_product_to_fp32():
+    """Centres in FP32 are the FP64 products k q rounded once to FP32 (the
+    value the label stands for), checked on products that need rounding."""
+    H = O.Hierarchy((5,))
+    q = 0.1  # tau = 0.05
+    taus = np.full(H.L + 1, q / 2)
+    k = np.array([1, 3, 7, -(2 ** 30) + 1, 123456789], dtype=np.int64)
+    got = O.dequantize(k, H, 0, taus, dtype=np.float32)
+    exp = np.array([np.float32(float(v) * 0.1) for v in k])
+    assert np.array_equal(got, exp)
