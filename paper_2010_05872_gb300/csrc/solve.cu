@@ -201,6 +201,105 @@ solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlin
   }
 }
 
+// Contiguous lines of odd length in a persistent, double-buffered form: a
+// CTA takes batches of `rows` lines (one contiguous range each) in turn; the
+// bulk copy of its next batch (thread 0, enclosing 16-byte-aligned range,
+// the at most 15 bytes past the array's last whole 16 bytes by plain loads)
+// runs while the current batch is solved (one thread per line, Thomas from
+// shared memory with the factors there too; an odd pitch keeps the lines on
+// distinct banks) and written back with coalesced stores.  Waits give up
+// after 2 s and record the failure in `status`.
+template <typename T>
+__global__ void __launch_bounds__(128)
+solve_contig_pipe_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines,
+                         int rows, int bufelems, int mode, unsigned int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_shift[2];
+  const int nc = ax.nc;
+  T* s_ta = reinterpret_cast<T*>(smem_raw);  // nc each
+  T* s_tm = s_ta + nc;
+  T* s_tc = s_tm + nc;
+  const int tpad = ((3 * nc * static_cast<int>(sizeof(T)) + 15) / 16) * 16;
+  T* buf0 = reinterpret_cast<T*>(smem_raw + tpad);  // 2 x bufelems
+  const int tid = threadIdx.x;
+  const int64_t nbatch = (nlines + rows - 1) / rows;
+  const uint64_t lim = (static_cast<uint64_t>(nlines) * nc * sizeof(T)) & ~15ull;
+  auto issue = [&](int64_t b, int slot) {  // thread 0
+    const int64_t first = b * rows;
+    const int nr = static_cast<int>(min(static_cast<int64_t>(rows), nlines - first));
+    const uint64_t sb = static_cast<uint64_t>(first) * nc * sizeof(T);
+    const uint64_t eb = sb + static_cast<uint64_t>(nr) * nc * sizeof(T);
+    const uint64_t ab = sb & ~15ull;
+    uint64_t bb = (eb + 15) & ~15ull;
+    if (bb > lim) bb = lim;
+    const int shift = static_cast<int>((sb - ab) / sizeof(T));
+    T* dst = buf0 + static_cast<size_t>(slot) * bufelems;
+    s_shift[slot] = shift;
+    const unsigned bytes = bb > ab ? static_cast<unsigned>(bb - ab) : 0u;
+    mbar_arrive_expect_tx(&bars[slot], bytes);
+    if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(F) + ab, bytes, &bars[slot]);
+    for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
+      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = F[x / sizeof(T)];
+  };
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+    if (blockIdx.x < nbatch) issue(blockIdx.x, 0);
+  }
+  for (int k = tid; k < nc; k += blockDim.x) {
+    s_ta[k] = ax.ta[k];
+    s_tm[k] = ax.tm[k];
+    s_tc[k] = ax.tc[k];
+  }
+  __syncthreads();
+  unsigned phase = 0u;
+  int it = 0;
+  for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+    const int slot = it & 1;
+    const int64_t nb = b + gridDim.x;
+    if (tid == 0 && nb < nbatch) {
+      fence_proxy_async();  // the other buffer's last reads (generic) precede the copy
+      issue(nb, slot ^ 1);
+    }
+    const bool got = mbar_wait(&bars[slot], (phase >> slot) & 1u, kWaitLimitNs);
+    if (__syncthreads_or(!got)) {
+      if (tid == 0) *reinterpret_cast<volatile unsigned*>(status) = 1u;
+      mbar_wait(&bars[slot], (phase >> slot) & 1u, kWaitLimitNs);
+      if (nb < nbatch) mbar_wait(&bars[slot ^ 1], (phase >> (slot ^ 1)) & 1u, kWaitLimitNs);
+      return;
+    }
+    phase ^= 1u << slot;
+    const int64_t first = b * rows;
+    const int nr = static_cast<int>(min(static_cast<int64_t>(rows), nlines - first));
+    const int total = nr * nc;
+    T* s = buf0 + static_cast<size_t>(slot) * bufelems + s_shift[slot];
+    if (tid < nr) thomas_smem(s + tid * nc, s_ta, s_tm, s_tc, nc);
+    __syncthreads();
+    T* dstF = F + first * nc;
+    T* dstB = B ? B + first * nc : nullptr;
+    for (int base = tid; base < total; base += 4 * blockDim.x) {
+      T bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = base + u * blockDim.x;
+        bv[u] = (i < total && mode != kApplyNone) ? dstB[i] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = base + u * blockDim.x;
+        if (i < total) {
+          const T x = s[i];
+          if (mode == kApplyNone) dstF[i] = x;
+          else apply_x(dstF, dstB, i, x, bv[u], mode);
+        }
+      }
+    }
+    __syncthreads();  // this buffer may be refilled
+  }
+}
+
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
 
 }  // namespace
@@ -218,15 +317,23 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
                   sizeof(T) * passes * double(c0) * c1 * c2, s);
     const size_t per_row = sizeof(T) * static_cast<size_t>(c2 | 1);
     const size_t tpad = (3 * sizeof(T) * static_cast<size_t>(c2) + 15) / 16 * 16;
-    if (a == 2 && (c2 & 1) && per_row <= 32 * 1024 && c0 * c1 >= 1024) {
-      // Odd line length: TMA-staged lines, about 64 KB of lines per CTA.
+    if (a == 2 && (c2 & 1) && per_row <= 16 * 1024 && c0 * c1 >= 1024) {
+      // Odd line length: persistent double-buffered TMA batches of about
+      // 32 KB of lines, three CTAs per SM.
       const int64_t nlines = c0 * c1;
-      const int rows = static_cast<int>(std::max<size_t>(1, std::min<size_t>(128, (64 * 1024) / per_row)));
-      const size_t smem = tpad + per_row * rows + 32;
-      cudaFuncSetAttribute(solve_contig_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      const int rows = static_cast<int>(std::max<size_t>(1, std::min<size_t>(128, (32 * 1024) / per_row)));
+      const int vec = 16 / static_cast<int>(sizeof(T));
+      const int bufelems = ((rows * static_cast<int>(c2) + 2 * vec) + vec - 1) / vec * vec;
+      const size_t smem = tpad + 2 * sizeof(T) * static_cast<size_t>(bufelems);
+      cudaFuncSetAttribute(solve_contig_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem));
-      solve_contig_tma_kernel<T><<<ceil_div(nlines, rows), 128, smem, s>>>(lv.ax[2], F, B, nlines,
-                                                                            rows, m, status);
+      int per_sm = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_contig_pipe_kernel<T>, 128, smem);
+      const int64_t nbatch = (nlines + rows - 1) / rows;
+      const unsigned grid = static_cast<unsigned>(std::max<int64_t>(
+          1, std::min<int64_t>(nbatch, 152 * static_cast<int64_t>(std::max(per_sm, 1)))));
+      solve_contig_pipe_kernel<T><<<grid, 128, smem, s>>>(lv.ax[2], F, B, nlines, rows, bufelems, m,
+                                                          status);
     } else if (a == 2 && per_row <= 112 * 1024) {
       const int64_t nlines = c0 * c1;
       int rows = static_cast<int>(std::min<size_t>(128, (112 * 1024) / per_row));

@@ -24,6 +24,53 @@ __device__ __forceinline__ void apply_x(T* F, T* B, int64_t idx, T x, T old_b, i
   }
 }
 
+// Thomas elimination of one line held in shared memory, in place: forward
+// y_k = (f_k - a_k y_{k-1}) m_k, backward x_k = y_k - c'_k x_{k+1}.  Values
+// and factors are read eight at a time ahead of the recurrence, so the chain
+// waits on arithmetic, not on shared-memory latency.
+template <typename T>
+__device__ __forceinline__ void thomas_smem(T* l, const T* ta, const T* tm, const T* tc, int nc) {
+  T y = T(0);
+  int k = 0;
+  for (; k + 8 <= nc; k += 8) {
+    T f[8], a[8], m[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      f[j] = l[k + j];
+      a[j] = ta[k + j];
+      m[j] = tm[k + j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      y = (f[j] - a[j] * y) * m[j];
+      l[k + j] = y;
+    }
+  }
+  for (; k < nc; ++k) {
+    y = (l[k] - ta[k] * y) * tm[k];
+    l[k] = y;
+  }
+  T x = T(0);
+  k = nc - 1;
+  for (; k >= 7; k -= 8) {
+    T v[8], c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[j] = l[k - j];
+      c[j] = tc[k - j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      x = v[j] - c[j] * x;
+      l[k - j] = x;
+    }
+  }
+  for (; k >= 0; --k) {
+    x = l[k] - tc[k] * x;
+    l[k] = x;
+  }
+}
+
 // Lines along the contiguous axis: a CTA stages `rows` whole lines in shared
 // memory (threads sweep each line, so loads and stores are coalesced), one
 // thread per line solves in place (row pitch nc|1 keeps the threads on
@@ -158,21 +205,7 @@ __device__ __forceinline__ void solve_contig_tma_tile(const AxisK<T>& ax, T* __r
     return;
   }
   const int shift = s_shift;
-  if (tid < nr) {
-    T* l = s + shift + tid * nc;
-    T y = T(0);
-#pragma unroll 4
-    for (int k = 0; k < nc; ++k) {
-      y = (l[k] - s_ta[k] * y) * s_tm[k];
-      l[k] = y;
-    }
-    T x = T(0);
-#pragma unroll 4
-    for (int k = nc - 1; k >= 0; --k) {
-      x = l[k] - s_tc[k] * x;
-      l[k] = x;
-    }
-  }
+  if (tid < nr) thomas_smem(s + shift + tid * nc, s_ta, s_tm, s_tc, nc);
   __syncthreads();
   T* dstF = F + first * nc;
   T* dstB = B ? B + first * nc : nullptr;
