@@ -208,6 +208,21 @@ namespace {
 // solves with the correction applied to the gathered coarse values; then,
 // coarsest first, the finishing pass writes each level's coefficients and the
 // final coarser values into the level-l grid.
+// The highest level ls (stop < ls <= L) whose grid and every grid below it
+// fit the one-CTA form of the coarsest levels, or stop if none does.
+template <typename T>
+int small_top(const DevPlan& p, int stop) {
+  const auto& lv = levels<T>(p);
+  int ls = stop;
+  for (int l = stop + 1; l <= p.h.L && l - stop <= kSmallMaxLevels; ++l) {
+    const auto& d = p.h.shape[l];
+    if (d[0] * d[1] * d[2] > kSmallMaxNodes) break;
+    if (small_levels_smem<T>(&lv[stop + 1], l - stop) > 200 * 1024) break;
+    ls = l;
+  }
+  return ls;
+}
+
 template <typename T>
 int run_decompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* status,
                   cudaStream_t s) {
@@ -219,11 +234,13 @@ int run_decompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
     B[l] = reinterpret_cast<T*>(ws + p.offB[l]);
     F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
   }
-  for (int l = L; l > stop; --l) {
+  const int ls = small_top<T>(p, stop);
+  for (int l = L; l > ls; --l) {
     MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, status, s));
     MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, status, s));
   }
-  for (int l = stop + 1; l <= L; ++l)
+  if (ls > stop) MGB_TRY(launch_small_levels<T>(&lv[stop + 1], ls - stop, true, B[ls], ls, s));
+  for (int l = ls + 1; l <= L; ++l)
     MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, status, s));
   return MGARD_OK;
 }
@@ -241,9 +258,11 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
     B[l] = reinterpret_cast<T*>(ws + p.offB[l]);
     F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
   }
-  for (int l = L; l > stop; --l)
+  const int ls = small_top<T>(p, stop);
+  for (int l = L; l > ls; --l)
     MGB_TRY(launch_load_vector<T>(lv[l], false, B[l], B[l - 1], F[l - 1], l, status, s));
-  for (int l = stop + 1; l <= L; ++l) {
+  if (ls > stop) MGB_TRY(launch_small_levels<T>(&lv[stop + 1], ls - stop, false, B[ls], ls, s));
+  for (int l = ls + 1; l <= L; ++l) {
     MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyRecompose, l, status, s));
     MGB_TRY(launch_finish<T>(lv[l], B[l - 1], B[l - 1], T(1), B[l], l, status, s));
   }

@@ -74,6 +74,17 @@ template <typename T>
 cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* interp_src, T sign,
                           T* fine, int level, unsigned int* status, cudaStream_t s);
 
+// The coarsest levels stop + 1 .. stop + nlev of a transform in one CTA
+// (small.cu): `data` is the level-(stop + nlev) grid, decomposed (dec) or
+// recomposed in place; lv[i] is the transition of level stop + 1 + i.
+constexpr int kSmallMaxLevels = 10;
+constexpr int64_t kSmallMaxNodes = 8192;  // nodes of the highest small level
+template <typename T>
+size_t small_levels_smem(const LevelK<T>* lv, int nlev);
+template <typename T>
+cudaError_t launch_small_levels(const LevelK<T>* lv, int nlev, bool dec, T* data, int level,
+                                cudaStream_t s);
+
 // Quantization / dequantization / value range (quantize.cu).  The field is
 // viewed as `rows` rows (j0, j1) of n2 contiguous elements; lev01 holds the
 // level of each row, lev2 that of each column.

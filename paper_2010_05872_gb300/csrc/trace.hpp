@@ -18,6 +18,7 @@ enum KernelKind : int {
   kKQuantize,
   kKDequantize,
   kKMinmax,
+  kKSmallLevels,
   kKNumKinds
 };
 
