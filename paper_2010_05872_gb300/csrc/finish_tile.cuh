@@ -68,6 +68,9 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
   __shared__ int s_nshift[NC];      // ring of nodal-source planes (decomposition)
 
   const int tid = threadIdx.x;
+  // The copies are issued by lane 0 of the last warp, which owns the fewest
+  // columns (often one), so the issue work stays off the busiest warps.
+  const int producer = static_cast<int>(blockDim.x) - 32;
   const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
   const int c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   const int b2 = tile % g.nb2;
@@ -92,7 +95,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
   // recomposition they are the interpolant's own coarse values.
   const bool sep = nodal_src != interp_src;
 
-  if (tid == 0) {
+  if (tid == producer) {
     for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
   }
@@ -188,7 +191,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
   unsigned phases = 0u;   // bit i: parity to wait for on bars[i]
   unsigned pending = 0u;  // bit i: bars[i] has copies in flight
   for (int i = 0; i < NS - 1 && M0 + i < M1; ++i) {
-    if (tid == 0) issue(M0 + i, i);
+    if (tid == producer) issue(M0 + i, i);
     pending |= 1u << i;
   }
   T A[R1M], B[R1M];
@@ -198,7 +201,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
     if (__syncthreads_or(!got)) {
       // A copy did not land in time: record it, give every stage still in
       // flight a second bounded wait so nothing lands after the CTA exits.
-      if (tid == 0) *reinterpret_cast<volatile unsigned*>(status) = 1u;
+      if (tid == producer) *reinterpret_cast<volatile unsigned*>(status) = 1u;
       for (int i = 0; i < NS; ++i)
         if ((pending >> i) & 1u) mbar_wait(&bars[i], (phases >> i) & 1u, kWaitLimitNs);
       return;
@@ -208,7 +211,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
     if (m + NS - 1 < M1) {
       // The stage refilled here was last read in the previous pair.
       const int st = (m - M0 + NS - 1) % NS;
-      if (tid == 0) {
+      if (tid == producer) {
         fence_proxy_async();
         issue(m + NS - 1, st);
       }
@@ -262,7 +265,7 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
     }
     __syncthreads();  // this stage's buffers may be refilled
   }
-  if (PERSIST && tid == 0)
+  if (PERSIST && tid == producer)
     for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
 }
 

@@ -60,6 +60,9 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
   __shared__ int s_rown[S1M]; // coarse row of a nodal row s, or -1
 
   const int tid = threadIdx.x;
+  // The copies are issued by lane 0 of the last warp, which owns the fewest
+  // columns (often one), so the issue work stays off the busiest warps.
+  const int producer = static_cast<int>(blockDim.x) - 32;
   const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
   const int c0 = lv.ax[0].nc, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   const int b2 = tile % g.nb2;
@@ -101,7 +104,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
       s_y1[s][i] = y;
     }
   }
-  if (tid == 0) {
+  if (tid == producer) {
     for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
   }
@@ -169,9 +172,9 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 
   unsigned phases = 0u;   // bit i: parity to wait for on bars[i]
   unsigned pending = 0u;  // bit i: bars[i] has a copy in flight
-  if (tid == 0) fence_proxy_async();  // the zero fill precedes every bulk copy
+  if (tid == producer) fence_proxy_async();  // the zero fill precedes every bulk copy
   for (int i = 0; i < NS - 1 && jlo + i <= jhi; ++i) {
-    if (tid == 0) issue(jlo + i, i);
+    if (tid == producer) issue(jlo + i, i);
     pending |= 1u << i;
   }
   for (int j = jlo; j <= jhi; ++j) {
@@ -180,7 +183,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     if (__syncthreads_or(!got)) {
       // A copy did not land in time: record it, give every stage still in
       // flight a second bounded wait so nothing lands after the CTA exits.
-      if (tid == 0) *reinterpret_cast<volatile unsigned*>(status) = 1u;
+      if (tid == producer) *reinterpret_cast<volatile unsigned*>(status) = 1u;
       for (int i = 0; i < NS; ++i)
         if ((pending >> i) & 1u) mbar_wait(&bars[i], (phases >> i) & 1u, kWaitLimitNs);
       return;
@@ -190,7 +193,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     if (j + NS - 1 <= jhi) {
       // The buffer refilled here was last read for plane j - 1.
       const int ns = (j - jlo + NS - 1) % NS;
-      if (tid == 0) {
+      if (tid == producer) {
         fence_proxy_async();
         issue(j + NS - 1, ns);
       }
@@ -210,8 +213,24 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     for (int s = 0; s < S1M; ++s) {
       const T* row = tile + s * g.pitch;
       T f[5];
+      if constexpr (sizeof(T) == 4) {
+        // Three aligned 8-byte loads cover the 5 taps (threads read 8-byte
+        // words, so a warp's loads are free of bank conflicts); the pair
+        // parity is that of the row start, the same for the whole warp but
+        // for the last node of an even axis.
+        const T* p0 = row - 2;
+        const int par = static_cast<int>((reinterpret_cast<uintptr_t>(p0) >> 2) & 1u);
+        const float2* q = reinterpret_cast<const float2*>(p0 - par);
+        const float2 a = q[0], b = q[1], c = q[2];
+        f[0] = par ? a.y : a.x;
+        f[1] = par ? b.x : a.y;
+        f[2] = par ? b.y : b.x;
+        f[3] = par ? c.x : b.y;
+        f[4] = par ? c.y : c.x;
+      } else {
 #pragma unroll
-      for (int o = 0; o < 5; ++o) f[o] = row[o - 2];
+        for (int o = 0; o < 5; ++o) f[o] = row[o - 2];
+      }
       T gs = T(0);
 #pragma unroll
       for (int o = 0; o < 5; ++o) gs += rw2[o] * f[o];
@@ -265,7 +284,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     __syncthreads();  // every read of this buffer is done
   }
   store_done(jhi, true);
-  if (PERSIST && tid == 0)
+  if (PERSIST && tid == producer)
     for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
 }
 
