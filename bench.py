@@ -23,6 +23,7 @@ import argparse
 import glob
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -208,9 +209,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------- GPU leg ---
 
-def src_hash():
+def src_hash(source=None):
+    """Hash of the kernel sources: every file under csrc/, or, given one
+    translation unit, that file and the local headers it includes."""
+    csrc = os.path.join(ROOT, "paper_2010_05872_gb300", "csrc")
+    if source is None:
+        files = sorted(glob.glob(os.path.join(csrc, "*")))
+    else:
+        seen, todo = set(), [source]
+        while todo:
+            name = todo.pop()
+            if name in seen or not os.path.exists(os.path.join(csrc, name)):
+                continue
+            seen.add(name)
+            with open(os.path.join(csrc, name)) as fh:
+                todo += re.findall(r'^\s*#include\s+"([^"]+)"', fh.read(), re.M)
+        files = [os.path.join(csrc, n) for n in sorted(seen)]
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2010_05872_gb300", "csrc", "*"))):
+    for f in files:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
@@ -233,7 +249,8 @@ def traffic_for(kernel, level):
     except (OSError, ValueError):
         return None
     for r in rows:
-        if r.get("kernel") == kernel and r.get("level") == level and r.get("src_hash") == src_hash():
+        if (r.get("kernel") == kernel and r.get("level") == level
+                and r.get("src_hash") == src_hash(r.get("source"))):
             return r.get("dram_bytes_per_launch")
     return None
 

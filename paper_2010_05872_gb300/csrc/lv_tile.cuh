@@ -12,7 +12,7 @@
 
 namespace mgb {
 
-constexpr int kLvMaxThreads = 512;  // one thread per coarse column of a row (chunk)
+constexpr int kLvMaxThreads = 256;  // CTA size limit (a thread owns CPT coarse columns of a row)
 
 struct MarchGeom {
   int t1, tc2, t0;     // coarse rows / columns / planes per CTA
@@ -27,7 +27,7 @@ template <typename T>
 struct MarchCfg;
 template <>
 struct MarchCfg<float> {
-  static constexpr int NS = 4, T1 = 4;
+  static constexpr int NS = 3, T1 = 4;
 };
 template <>
 struct MarchCfg<double> {
@@ -40,7 +40,7 @@ struct MarchCfg<double> {
 // invalidates its barriers at the end (the next tile sets them up again) and
 // reads its few plain-loaded elements through L2 (other CTAs of the launch
 // may have written them).
-template <typename T, bool DEC, int NS, int T1C, bool THREE, bool PERSIST = false>
+template <typename T, bool DEC, int NS, int T1C, bool THREE, bool PERSIST = false, int CPT = 2>
 __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
                                                        const T* __restrict__ fine,
                                                        T* __restrict__ coarse, T* __restrict__ F,
@@ -109,26 +109,43 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     fence_mbar_init();
   }
 
-  // Column of this thread: coarse k2, its fine centre and 5-tap weights.
-  const int k2 = K2 + tid;
-  const bool act = tid < T2;
-  const int ccol = act ? cpos(k2, n2) - cbase : 2;  // tile column of the centre
-  T rw2[5], x2[5];
-#pragma unroll
-  for (int o = 0; o < 5; ++o) rw2[o] = x2[o] = T(0);
-  if (act) {
-#pragma unroll
-    for (int o = 0; o < 5; ++o) rw2[o] = lv.ax[2].rw[5 * k2 + o];
+  // Columns of this thread: coarse kc0 = K2 + CPT tid and the CPT - 1 after
+  // it.  Fine taps are read from a window of W columns starting 2 left of
+  // kc0's node; column c's 5 taps sit at window dcol[c] .. dcol[c] + 4, with
+  // dcol[c] = cpos(kc0 + c) - cpos(kc0) (2c, or 2c - 1 when kc0 + c is the
+  // last node of an even axis).
+  constexpr int W = 2 * CPT + 3;
+  const int kc0 = K2 + CPT * tid;
+  const int ccol = CPT * tid < T2 ? cpos(kc0, n2) - cbase : 2;  // tile column of kc0's node
+  bool actc[CPT];
+  int dcol[CPT];
+  T rwc[CPT][W], xc[CPT][W];
+  {
     const T* X = DEC ? lv.ax[2].xd : lv.ax[2].xr;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int kk = k2 - 1 + d;
-      if (kk >= 0 && kk < c2) {
-        const int o = cpos(kk, n2) - cpos(k2, n2) + 2;
-        const T xv = X[3 * k2 + d];
+    for (int c = 0; c < CPT; ++c) {
+      const int k = kc0 + c;
+      actc[c] = CPT * tid + c < T2;
+      dcol[c] = actc[c] ? cpos(k, n2) - cpos(kc0, n2) : 2 * c;
 #pragma unroll
-        for (int oo = 0; oo < 5; ++oo)
-          if (oo == o) x2[oo] = xv;
+      for (int oo = 0; oo < W; ++oo) rwc[c][oo] = xc[c][oo] = T(0);
+      if (actc[c]) {
+#pragma unroll
+        for (int oo = 0; oo < W; ++oo) {
+          const int o = oo - dcol[c];
+          if (o >= 0 && o < 5) rwc[c][oo] = lv.ax[2].rw[5 * k + o];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int kk = k - 1 + d;
+          if (kk >= 0 && kk < c2) {
+            const int o = cpos(kk, n2) - cpos(kc0, n2) + 2;
+            const T xv = X[3 * k + d];
+#pragma unroll
+            for (int oo = 0; oo < W; ++oo)
+              if (oo == o) xc[c][oo] = xv;
+          }
+        }
       }
     }
   }
@@ -153,18 +170,26 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
       dst[shift + static_cast<int>((x - sb) / sizeof(T))] = PERSIST ? __ldcg(fine + x / sizeof(T)) : fine[x / sizeof(T)];
   };
 
-  T acc[3][TM];
+  T acc[CPT][3][TM];
 #pragma unroll
-  for (int t = 0; t < TM; ++t) acc[0][t] = acc[1][t] = acc[2][t] = T(0);
+  for (int c = 0; c < CPT; ++c)
+#pragma unroll
+    for (int t = 0; t < TM; ++t)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[c][k][t] = T(0);
   int kdone = K0;
   auto store_done = [&](int upto_plane, bool all) {
     while (kdone < K0 + T0 && (all || cpos(kdone, n0) + 2 <= upto_plane)) {
 #pragma unroll
       for (int t = 0; t < TM; ++t) {
-        if (act && t < T1) F[(static_cast<int64_t>(kdone) * c1 + (K1 + t)) * c2 + k2] = acc[0][t];
-        acc[0][t] = acc[1][t];
-        acc[1][t] = acc[2][t];
-        acc[2][t] = T(0);
+        T* dst = F + (static_cast<int64_t>(kdone) * c1 + (K1 + t)) * c2 + kc0;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          if (actc[c] && t < T1) dst[c] = acc[c][0][t];
+          acc[c][0][t] = acc[c][1][t];
+          acc[c][1][t] = acc[c][2][t];
+          acc[c][2][t] = T(0);
+        }
       }
       ++kdone;
     }
@@ -201,65 +226,84 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     }
 
     // Warps without a column of this tile skip the arithmetic.
-    if (tid < ((T2 + 31) & ~31)) {
+    if (CPT * (tid & ~31) < T2) {
     const bool pn = !is_coef(j, n0);  // nodal plane
     const int kj = pn ? nodal_k(j, n0, c0) : -1;
     const bool gplane = pn && kj >= K0 && kj < K0 + T0;
     const T* tile = vbuf + static_cast<size_t>(slot) * g.BUF + s_off[slot] + ccol;
-    T G1[TM], H1[TM];
+    T G1[CPT][TM], H1[CPT][TM];
 #pragma unroll
-    for (int t = 0; t < TM; ++t) G1[t] = H1[t] = T(0);
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+      for (int t = 0; t < TM; ++t) G1[c][t] = H1[c][t] = T(0);
 #pragma unroll
     for (int s = 0; s < S1M; ++s) {
       const T* row = tile + s * g.pitch;
-      T f[5];
+      T fe[W];  // window: tile columns ccol - 2 .. ccol + W - 3 of row s
       if constexpr (sizeof(T) == 4) {
-        // Three aligned 8-byte loads cover the 5 taps (threads read 8-byte
-        // words, so a warp's loads are free of bank conflicts); the pair
-        // parity is that of the row start, the same for the whole warp but
-        // for the last node of an even axis.
+        // Aligned 8-byte loads cover the window (8-byte words per thread: no
+        // bank conflicts); the pair parity is that of the row start, the
+        // same for the whole warp.
+        constexpr int NQ = (W + 1) / 2;
         const T* p0 = row - 2;
-        const int par = static_cast<int>((reinterpret_cast<uintptr_t>(p0) >> 2) & 1u);
+        const bool par = (reinterpret_cast<uintptr_t>(p0) >> 2) & 1u;
         const float2* q = reinterpret_cast<const float2*>(p0 - par);
-        const float2 a = q[0], b = q[1], c = q[2];
-        f[0] = par ? a.y : a.x;
-        f[1] = par ? b.x : a.y;
-        f[2] = par ? b.y : b.x;
-        f[3] = par ? c.x : b.y;
-        f[4] = par ? c.y : c.x;
+        float2 v[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) v[i] = q[i];
+#pragma unroll
+        for (int o = 0; o < W; ++o) {
+          const float lo = (o & 1) ? v[o / 2].y : v[o / 2].x;
+          const float hi = (o & 1) ? v[o / 2 + 1].x : v[o / 2].y;
+          fe[o] = par ? hi : lo;
+        }
       } else {
 #pragma unroll
-        for (int o = 0; o < 5; ++o) f[o] = row[o - 2];
+        for (int o = 0; o < W; ++o) fe[o] = row[o - 2];
       }
-      T gs = T(0);
+      T gs[CPT];
 #pragma unroll
-      for (int o = 0; o < 5; ++o) gs += rw2[o] * f[o];
+      for (int c = 0; c < CPT; ++c) {
+        gs[c] = T(0);
+#pragma unroll
+        for (int o = (c ? 2 * c - 1 : 0); o < W && o <= 2 * c + 4; ++o) gs[c] += rwc[c][o] * fe[o];
+      }
       const int base = (s & 1) ? (s - 3) / 2 : s / 2 - 2;
       const int kr = THREE ? s_rown[s] : 0;
-      if (!THREE) {
-        G1[0] = gs;
-      } else {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int t = base + i;
-          if (t >= 0 && t < TM) G1[t] += s_w1[s][i] * gs;
-        }
-      }
-      if (pn && kr >= 0) {
-        T hs = T(0);
-#pragma unroll
-        for (int o = 0; o < 5; ++o) hs += x2[o] * f[o];
+      for (int c = 0; c < CPT; ++c) {
         if (!THREE) {
-          H1[0] = hs;
+          G1[c][0] = gs[c];
         } else {
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const int t = base + i;
-            if (t >= 0 && t < TM) H1[t] += s_y1[s][i] * hs;
+            if (t >= 0 && t < TM) G1[c][t] += s_w1[s][i] * gs[c];
           }
         }
-        if (gplane && act && kr >= K1 && kr < K1 + T1)
-          coarse[(static_cast<int64_t>(kj) * c1 + kr) * c2 + k2] = f[2];
+      }
+      if (pn && kr >= 0) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          T hs = T(0);
+#pragma unroll
+          for (int o = 2 * c; o < W && o <= 2 * c + 4; ++o) hs += xc[c][o] * fe[o];
+          if (!THREE) {
+            H1[c][0] = hs;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              const int t = base + i;
+              if (t >= 0 && t < TM) H1[c][t] += s_y1[s][i] * hs;
+            }
+          }
+        }
+        if (gplane && kr >= K1 && kr < K1 + T1) {
+          T* dst = coarse + (static_cast<int64_t>(kj) * c1 + kr) * c2 + kc0;
+#pragma unroll
+          for (int c = 0; c < CPT; ++c)
+            if (actc[c]) dst[c] = (c == 0 || dcol[c] == 2 * c) ? fe[2 + 2 * c] : fe[1 + 2 * c];
+        }
       }
     }
     // Axis 0: plane j feeds the coarse planes kdone .. kdone + 2.
@@ -276,9 +320,11 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
       }
     }
 #pragma unroll
-    for (int t = 0; t < TM; ++t)
+    for (int c = 0; c < CPT; ++c)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) acc[k][t] += wk[k] * G1[t] - yk[k] * H1[t];
+      for (int t = 0; t < TM; ++t)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[c][k][t] += wk[k] * G1[c][t] - yk[k] * H1[c][t];
     store_done(j, false);
     }
     __syncthreads();  // every read of this buffer is done
@@ -288,26 +334,27 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
 }
 
+// Tile shape of a level for CPT coarse columns per thread.
 template <typename T>
-inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g) {
+inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g, int cpt = 2) {
   using C = MarchCfg<T>;
   const int n1 = lv.ax[1].n, n2 = lv.ax[2].n, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   const int vec = 16 / static_cast<int>(sizeof(T));
   if (n1 > 1) {
-    if (c2 > kLvMaxThreads) return false;  // rows too wide for one CTA
+    if (c2 > cpt * kLvMaxThreads) return false;  // rows too wide for one CTA
     g.t1 = C::T1;
     g.tc2 = c2;
     g.pitch = n2;
     g.BUF = ((4 * vec + (2 * C::T1 + 3) * n2 + 4 + vec - 1) / vec) * vec;
   } else {
     g.t1 = 1;
-    g.tc2 = c2 <= kLvMaxThreads ? c2 : kLvMaxThreads / 2;
+    g.tc2 = c2 <= cpt * kLvMaxThreads ? c2 : cpt * kLvMaxThreads / 2;
     g.pitch = 2 * g.tc2 + 3;
     g.BUF = ((4 * vec + g.pitch + 4 + vec - 1) / vec) * vec;
   }
   g.nb2 = (c2 + g.tc2 - 1) / g.tc2;
   g.nb1 = (c1 + g.t1 - 1) / g.t1;
-  g.threads = 32 * ((g.tc2 + 31) / 32);
+  g.threads = 32 * (((g.tc2 + cpt - 1) / cpt + 31) / 32);
   return g.threads <= kLvMaxThreads && sizeof(T) * static_cast<size_t>(C::NS) * g.BUF <= 200 * 1024;
 }
 
