@@ -58,6 +58,8 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
   __shared__ T s_w1[S1M][3];  // R1 weight of row s for coarse row base(s) + i
   __shared__ T s_y1[S1M][3];  // X1 weight of nodal row s for the same coarse rows
   __shared__ int s_rown[S1M]; // coarse row of a nodal row s, or -1
+  __shared__ T s_lg[S1M];     // row sums of the left-over column (see `lrows`)
+  __shared__ T s_lh[S1M];
 
   const int tid = threadIdx.x;
   // The copies are issued by lane 0 of the last warp, which owns the fewest
@@ -114,9 +116,23 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
   // kc0's node; column c's 5 taps sit at window dcol[c] .. dcol[c] + 4, with
   // dcol[c] = cpos(kc0 + c) - cpos(kc0) (2c, or 2c - 1 when kc0 + c is the
   // last node of an even axis).
+  //
+  // An odd column count whose pairs exactly fill whole warps (every level
+  // of a 2^k + 1 grid) leaves one column over.  A warp of its own would run
+  // the whole row loop for that one lane, so instead the last warp takes it
+  // with one lane per staged row (`lrows`, `lwarp`): lane s forms row s's
+  // sums of the column and lanes t < T1 combine them into coarse row t.  It
+  // keeps the column's weights in rwc[0] / xc[0] and its sums and
+  // accumulators in G1[0][0], H1[0][0], acc[0][.][0].
   constexpr int W = 2 * CPT + 3;
+  const bool lrows = CPT == 2 && S1M <= 32 && (T2 & 1) && (((T2 - 1) / 2) & 31) == 0;
+  const int TP = lrows ? T2 - 1 : T2;  // columns taken in pairs
+  const int lane = tid & 31;
+  const bool lwarp = lrows && (tid >> 5) == (TP / 2) >> 5;
+  const int kL = K2 + T2 - 1;          // the left-over column
   const int kc0 = K2 + CPT * tid;
-  const int ccol = CPT * tid < T2 ? cpos(kc0, n2) - cbase : 2;  // tile column of kc0's node
+  const int ccol = lwarp ? cpos(kL, n2) - cbase
+                         : (CPT * tid < TP ? cpos(kc0, n2) - cbase : 2);  // tile column of kc0's node
   bool actc[CPT];
   int dcol[CPT];
   T rwc[CPT][W], xc[CPT][W];
@@ -124,9 +140,9 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     const T* X = DEC ? lv.ax[2].xd : lv.ax[2].xr;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-      const int k = kc0 + c;
-      actc[c] = CPT * tid + c < T2;
-      dcol[c] = actc[c] ? cpos(k, n2) - cpos(kc0, n2) : 2 * c;
+      const int k = lwarp ? kL : kc0 + c;
+      actc[c] = lwarp ? c == 0 : CPT * tid + c < TP;
+      dcol[c] = actc[c] && !lwarp ? cpos(k, n2) - cpos(kc0, n2) : 2 * c;
 #pragma unroll
       for (int oo = 0; oo < W; ++oo) rwc[c][oo] = xc[c][oo] = T(0);
       if (actc[c]) {
@@ -139,7 +155,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
         for (int d = 0; d < 3; ++d) {
           const int kk = k - 1 + d;
           if (kk >= 0 && kk < c2) {
-            const int o = cpos(kk, n2) - cpos(kc0, n2) + 2;
+            const int o = cpos(kk, n2) - cpos(lwarp ? kL : kc0, n2) + 2;
             const T xv = X[3 * k + d];
 #pragma unroll
             for (int oo = 0; oo < W; ++oo)
@@ -183,9 +199,11 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 #pragma unroll
       for (int t = 0; t < TM; ++t) {
         T* dst = F + (static_cast<int64_t>(kdone) * c1 + (K1 + t)) * c2 + kc0;
+        if (lwarp && t == 0 && lane < T1)
+          F[(static_cast<int64_t>(kdone) * c1 + (K1 + lane)) * c2 + kL] = acc[0][0][0];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-          if (actc[c] && t < T1) dst[c] = acc[c][0][t];
+          if (!lwarp && actc[c] && t < T1) dst[c] = acc[c][0][t];
           acc[c][0][t] = acc[c][1][t];
           acc[c][1][t] = acc[c][2][t];
           acc[c][2][t] = T(0);
@@ -226,7 +244,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     }
 
     // Warps without a column of this tile skip the arithmetic.
-    if (CPT * (tid & ~31) < T2) {
+    if (CPT * (tid & ~31) < TP || lwarp) {
     const bool pn = !is_coef(j, n0);  // nodal plane
     const int kj = pn ? nodal_k(j, n0, c0) : -1;
     const bool gplane = pn && kj >= K0 && kj < K0 + T0;
@@ -236,6 +254,43 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     for (int c = 0; c < CPT; ++c)
 #pragma unroll
       for (int t = 0; t < TM; ++t) G1[c][t] = H1[c][t] = T(0);
+    if (lwarp) {
+      if (lane < S1M) {
+        const T* row = tile + lane * g.pitch;
+        T fe[5];
+#pragma unroll
+        for (int o = 0; o < 5; ++o) fe[o] = row[o - 2];
+        T gs = T(0), hs = T(0);
+#pragma unroll
+        for (int o = 0; o < 5; ++o) gs += rwc[0][o] * fe[o];
+        const int kr = THREE ? s_rown[lane] : 0;
+        if (pn && kr >= 0) {
+#pragma unroll
+          for (int o = 0; o < 5; ++o) hs += xc[0][o] * fe[o];
+          if (gplane && kr >= K1 && kr < K1 + T1)
+            coarse[(static_cast<int64_t>(kj) * c1 + kr) * c2 + kL] = fe[2];
+        }
+        s_lg[lane] = gs;
+        s_lh[lane] = hs;
+      }
+      __syncwarp();
+      if (!THREE) {
+        G1[0][0] = s_lg[0];
+        H1[0][0] = s_lh[0];
+      } else if (lane < T1) {
+        T gsum = T(0), hsum = T(0);
+#pragma unroll
+        for (int s = 0; s < S1M; ++s) {
+          const int i = lane - ((s & 1) ? (s - 3) / 2 : s / 2 - 2);
+          if (i >= 0 && i <= 2) {
+            gsum += s_w1[s][i] * s_lg[s];
+            hsum += s_y1[s][i] * s_lh[s];
+          }
+        }
+        G1[0][0] = gsum;
+        H1[0][0] = hsum;
+      }
+    } else {
 #pragma unroll
     for (int s = 0; s < S1M; ++s) {
       const T* row = tile + s * g.pitch;
@@ -305,6 +360,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
             if (actc[c]) dst[c] = (c == 0 || dcol[c] == 2 * c) ? fe[2 + 2 * c] : fe[1 + 2 * c];
         }
       }
+    }
     }
     // Axis 0: plane j feeds the coarse planes kdone .. kdone + 2.
     T wk[3], yk[3];

@@ -68,6 +68,9 @@ CASES = [
     # Levels of at least 2^17 nodes take the marching kernels: 2D with rows
     # in one chunk and in several, 3D with even axes, rows too wide to march.
     ((400, 1500), "g", 0), ((1030, 258), "u", 0), ((66, 64, 62), "g", 0), ((34, 40, 600), "u", 1),
+    # 2^k + 1 rows (257 and 129 coarse columns): the left-over column of the
+    # paired load-vector rows is taken one staged row per lane.
+    ((129, 65, 257), "g", 0), ((300, 513), "z", 0),
 ]
 
 
