@@ -294,8 +294,14 @@ int mgard_decompose_noalloc(int ndim, const int64_t* dims, const double* const* 
  * that kind (a call can launch more than one kernel).
  * mgard_trace_kernel_name names a kind.  mgard_trace_kernel_launches returns
  * the number of kernels this library launched while tracing was on since the
- * last mgard_trace_enable(1). */
+ * last mgard_trace_enable(1).
+ * mgard_trace_select(kind, level, any_level) limits the bracketing to the
+ * launches of one kernel kind (and, unless any_level is nonzero, of one
+ * level), so that the events of the other launches do not perturb a timed
+ * region; kind < 0 brackets every launch again (the default).  Launches of
+ * every kind are still counted.  Returns MGARD_ERR_ARG for an unknown kind. */
 int mgard_trace_enable(int on);
+int mgard_trace_select(int kind, int level, int any_level);
 int64_t mgard_trace_kernel_launches(void);
 int mgard_trace_read(int max_rows, int* kind, int* level, int64_t* launches, double* total_ms,
                      double* bytes, int* rows_out);

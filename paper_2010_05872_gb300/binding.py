@@ -80,6 +80,7 @@ _SIGNATURES = {
     "mgard_server_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "mgard_server_destroy": (ctypes.c_int, [_VP]),
     "mgard_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mgard_trace_select": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mgard_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), _I64P, _DP, _DP,
                                         ctypes.POINTER(ctypes.c_int)]),
@@ -373,6 +374,15 @@ def mgard_release_plans() -> int:
 
 def mgard_trace_enable(on: bool) -> int:
     return lib().mgard_trace_enable(1 if on else 0)
+
+
+def mgard_trace_select(kind=-1, level=None) -> int:
+    """Bracket only the launches of one kernel kind (and level, unless None)
+    with events; kind < 0 brackets every launch."""
+    rc = lib().mgard_trace_select(int(kind), 0 if level is None else int(level),
+                                  1 if level is None else 0)
+    _check(rc, "mgard_trace_select")
+    return rc
 
 
 def mgard_trace_kernel_launches() -> int:

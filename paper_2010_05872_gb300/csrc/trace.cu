@@ -20,6 +20,9 @@ struct Rec {
 };
 
 std::atomic<bool> g_on{false};
+std::atomic<int> g_sel_kind{-1};  // bracket only this kind (-1: every kind)
+std::atomic<int> g_sel_level{0};
+std::atomic<bool> g_sel_any_level{true};
 std::atomic<int64_t> g_kernels{0};
 std::mutex g_tmu;
 std::vector<Rec> g_recs;
@@ -59,6 +62,10 @@ TraceScope::TraceScope(int kind, int level, double bytes, cudaStream_t s) : s_(s
   if (!g_on.load(std::memory_order_relaxed)) return;
   on_ = true;
   g_kernels.fetch_add(1, std::memory_order_relaxed);
+  const int sk = g_sel_kind.load(std::memory_order_relaxed);
+  if (sk >= 0 && (kind != sk || (!g_sel_any_level.load(std::memory_order_relaxed) &&
+                                 level != g_sel_level.load(std::memory_order_relaxed))))
+    return;
   std::lock_guard<std::mutex> lk(g_tmu);
   Rec r{kind, level, bytes, take_event(), take_event()};
   if (r.a == nullptr || r.b == nullptr) return;
@@ -93,6 +100,14 @@ int mgard_trace_enable(int on) {
     g_kernels.store(0);
   }
   g_on.store(on != 0);
+  return MGARD_OK;
+}
+
+int mgard_trace_select(int kind, int level, int any_level) {
+  if (kind >= kKNumKinds) return MGARD_ERR_ARG;
+  g_sel_level.store(level);
+  g_sel_any_level.store(any_level != 0);
+  g_sel_kind.store(kind < 0 ? -1 : kind);
   return MGARD_OK;
 }
 

@@ -1,7 +1,9 @@
-// Kernel timing trace: while enabled, every kernel launch of the library is
-// bracketed by CUDA events recorded on its own stream, tagged with the kernel
-// kind, the level it worked on and its algorithmic bytes (each input read
-// once, each output written once).  mgard_trace_read() aggregates them.
+// Kernel timing trace: while enabled, every kernel launch of the library
+// (or, after mgard_trace_select, every launch of one kind) is bracketed by
+// CUDA events recorded on its own stream, tagged with the kernel kind, the
+// level it worked on and its algorithmic bytes (each input read once, each
+// output written once).  mgard_trace_read() aggregates them.  Launches are
+// counted whether or not they are bracketed.
 #pragma once
 
 #include <cuda_runtime.h>
