@@ -402,10 +402,15 @@ def run_gpu(args, rank, world, local_rank):
     kinds = {}
     for r in trace:
         kinds[r["kernel"]] = kinds.get(r["kernel"], 0.0) + r["total_ms"] / kb
-    kernels = sorted(({"kernel": r["kernel"], "level": r["level"], "launches": r["launches"],
-                       "ms_per_step": r["total_ms"] / kb,
-                       "gbs": r["bytes"] / (r["total_ms"] * 1e-3) / 1e9} for r in trace),
-                     key=lambda d: -d["ms_per_step"])[:12]
+    all_kernels = sorted(({"kernel": r["kernel"], "level": r["level"], "launches": r["launches"],
+                           "ms_per_step": r["total_ms"] / kb,
+                           "gbs": r["bytes"] / (r["total_ms"] * 1e-3) / 1e9} for r in trace),
+                         key=lambda d: -d["ms_per_step"])
+    kernels = all_kernels[:12]
+    # The whole breakdown, one row per (kernel, level), on stderr.
+    for d in all_kernels:
+        print(f"# {d['kernel']:26s} L{d['level']:3d} launches/step {d['launches'] / kb:5.2f} "
+              f"{d['ms_per_step'] * 1e3:8.1f} us/step {d['gbs']:7.0f} GB/s", file=sys.stderr)
 
     # Plain FP64 GPU path on the same input.
     del labels

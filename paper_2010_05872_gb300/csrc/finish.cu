@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "finish_tile.cuh"
 #include "grid.cuh"
 #include "kernels.cuh"
@@ -32,6 +33,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaxThreads)
 finish_kernel(LevelK<T> lv, const T* __restrict__ nodal_src, const T* __restrict__ interp_src,
               T sign, T* __restrict__ fine) {
+  grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* crow = reinterpret_cast<T*>(smem_raw);  // kRows x kCW
   __shared__ int64_t s_nodal[kRows];         // coarse row offset (fully nodal rows) or -1
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(kFMaxThreads, sizeof(T) == 4 ? 2 : 1)
 finish_march_kernel(LevelK<T> lv, const T* __restrict__ nodal_src,
                     const T* __restrict__ interp_src, T sign, T* __restrict__ fine,
                     FinishGeom g, unsigned int* __restrict__ status) {
+  grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   finish_march_tile<T, NS, T1C>(lv, nodal_src, interp_src, sign, fine, g, status, blockIdx.x,
                                 smem_raw);
@@ -202,8 +205,8 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
       }
       g.t0 = best_t0;
       g.nb0 = (npairs + g.t0 - 1) / g.t0;
-      kernel<<<static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2), g.threads, smem, s>>>(
-          mv, nodal_src, interp_src, sign, fine, g, status);
+      launch_pdl(kernel, dim3(static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2)), dim3(g.threads), smem,
+                 s, mv, nodal_src, interp_src, sign, fine, g, status);
       return cudaGetLastError();
     }
   }
@@ -219,7 +222,8 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
                 sizeof(T) * (2 * nf + (nodal_src == interp_src ? 1 : 2) * ncs), s);
   cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(smem));
-  finish_kernel<T><<<grid, threads, smem, s>>>(lv, nodal_src, interp_src, sign, fine);
+  launch_pdl(finish_kernel<T>, dim3(grid), dim3(threads), smem, s, lv, nodal_src, interp_src, sign,
+             fine);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "kernels.cuh"
 #include "lv_tile.cuh"
 #include "trace.hpp"
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kLvMaxThreads)
 load_vector_march_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict__ coarse,
                          T* __restrict__ F, MarchGeom g, uint64_t fine_count,
                          unsigned int* __restrict__ status) {
+  grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   load_vector_march_tile<T, DEC, NS, T1C, THREE>(lv, fine, coarse, F, g, fine_count, status,
                                                  blockIdx.x, smem_raw);
@@ -110,7 +112,7 @@ cudaError_t launch_load_vector_march(const LevelK<T>& lv_in, bool dec, const T* 
   g.nb0 = (c0 + g.t0 - 1) / g.t0;
   const uint64_t count = uint64_t(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
   const unsigned grid = static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2);
-  kernel<<<grid, g.threads, smem, s>>>(lv, fine, coarse, F, g, count, status);
+  launch_pdl(kernel, dim3(grid), dim3(g.threads), smem, s, lv, fine, coarse, F, g, count, status);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "kernels.cuh"
 #include "trace.hpp"
 
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(kQCols)
 quantize_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
                 const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2, int64_t n2,
                 int64_t nrows, int stop, LevelTable tab, unsigned int* __restrict__ flags) {
+  grid_dep_enter();
   __shared__ SmemTable st;
   load_table(tab, st);
   const int64_t ngroups = (nrows + kQRows - 1) / kQRows;
@@ -281,6 +283,7 @@ __global__ void __launch_bounds__(kQCols)
 dequantize_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
                   const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2, int64_t n2,
                   int64_t nrows, int stop, LevelTable tab) {
+  grid_dep_enter();
   __shared__ SmemTable st;
   load_table(tab, st);
   const int64_t ngroups = (nrows + kQRows - 1) / kQRows;
@@ -336,6 +339,7 @@ quantize_flat_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
                      const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
                      uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab,
                      unsigned int* __restrict__ flags) {
+  grid_dep_enter();
   __shared__ SmemTable st;
   load_table(tab, st);
   unsigned bad = 0;
@@ -371,6 +375,7 @@ __global__ void __launch_bounds__(kQThreads)
 dequantize_flat_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
                        const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
                        uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab) {
+  grid_dep_enter();
   __shared__ SmemTable st;
   load_table(tab, st);
   const uint64_t step = static_cast<uint64_t>(gridDim.x) * kQThreads * kQU;
@@ -419,6 +424,7 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 minmax_partial_kernel(const T* __restrict__ data, uint64_t count, double* __restrict__ partial,
                       unsigned int* __restrict__ flags) {
+  grid_dep_enter();
   __shared__ T smin[kThreads], smax[kThreads];
   T mn = Lim<T>::max(), mx = -Lim<T>::max();
   bool bad = false;
@@ -479,6 +485,7 @@ minmax_partial_kernel(const T* __restrict__ data, uint64_t count, double* __rest
 
 __global__ void __launch_bounds__(kThreads)
 minmax_final_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ result) {
+  grid_dep_enter();
   __shared__ double smin[kThreads], smax[kThreads];
   double mn = DBL_MAX, mx = -DBL_MAX;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
@@ -555,22 +562,21 @@ cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev
   if (aligned16(coeffs) && aligned16(labels) && flat_magic(count, n2, magic)) {
     const uint64_t nvec = count / 4;
     if (nvec > 0)
-      quantize_flat_kernel<T><<<flat_blocks(quantize_flat_kernel<T>, nvec), kQThreads, 0, s>>>(
-          coeffs, labels, lev01, lev2, nvec, static_cast<uint32_t>(n2), magic, stop_level, tab,
-          flags);
+      launch_pdl(quantize_flat_kernel<T>, dim3(flat_blocks(quantize_flat_kernel<T>, nvec)),
+                 dim3(kQThreads), 0, s, coeffs, labels, lev01, lev2, nvec,
+                 static_cast<uint32_t>(n2), magic, stop_level, tab, flags);
     if (count % 4 == 0) return cudaGetLastError();
     // The last count % 4 elements: one row-tile pass over the last row
     // would redo work, so the row-tile kernel takes the whole last row.
     const int64_t r_last = rows - 1;
     ts.more_kernels(1);
-    quantize_kernel<T><<<1, row_threads(n2), 0, s>>>(coeffs + r_last * n2, labels + r_last * n2,
-                                                    lev01 + r_last, lev2, n2, 1, stop_level, tab,
-                                                    flags);
+    launch_pdl(quantize_kernel<T>, dim3(1), dim3(row_threads(n2)), 0, s, coeffs + r_last * n2,
+               labels + r_last * n2, lev01 + r_last, lev2, n2, 1, stop_level, tab, flags);
     return cudaGetLastError();
   }
   const int threads = row_threads(n2);
-  quantize_kernel<T><<<row_blocks(quantize_kernel<T>, rows, n2, threads), threads, 0, s>>>(
-      coeffs, labels, lev01, lev2, n2, rows, stop_level, tab, flags);
+  launch_pdl(quantize_kernel<T>, dim3(row_blocks(quantize_kernel<T>, rows, n2, threads)),
+             dim3(threads), 0, s, coeffs, labels, lev01, lev2, n2, rows, stop_level, tab, flags);
   return cudaGetLastError();
 }
 
@@ -584,18 +590,19 @@ cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* l
   if (aligned16(coeffs) && aligned16(labels) && flat_magic(count, n2, magic)) {
     const uint64_t nvec = count / 4;
     if (nvec > 0)
-      dequantize_flat_kernel<T><<<flat_blocks(dequantize_flat_kernel<T>, nvec), kQThreads, 0, s>>>(
-          labels, coeffs, lev01, lev2, nvec, static_cast<uint32_t>(n2), magic, stop_level, tab);
+      launch_pdl(dequantize_flat_kernel<T>, dim3(flat_blocks(dequantize_flat_kernel<T>, nvec)),
+                 dim3(kQThreads), 0, s, labels, coeffs, lev01, lev2, nvec,
+                 static_cast<uint32_t>(n2), magic, stop_level, tab);
     if (count % 4 == 0) return cudaGetLastError();
     const int64_t r_last = rows - 1;
     ts.more_kernels(1);
-    dequantize_kernel<T><<<1, row_threads(n2), 0, s>>>(labels + r_last * n2, coeffs + r_last * n2,
-                                                      lev01 + r_last, lev2, n2, 1, stop_level, tab);
+    launch_pdl(dequantize_kernel<T>, dim3(1), dim3(row_threads(n2)), 0, s, labels + r_last * n2,
+               coeffs + r_last * n2, lev01 + r_last, lev2, n2, 1, stop_level, tab);
     return cudaGetLastError();
   }
   const int threads = row_threads(n2);
-  dequantize_kernel<T><<<row_blocks(dequantize_kernel<T>, rows, n2, threads), threads, 0, s>>>(
-      labels, coeffs, lev01, lev2, n2, rows, stop_level, tab);
+  launch_pdl(dequantize_kernel<T>, dim3(row_blocks(dequantize_kernel<T>, rows, n2, threads)),
+             dim3(threads), 0, s, labels, coeffs, lev01, lev2, n2, rows, stop_level, tab);
   return cudaGetLastError();
 }
 
@@ -607,13 +614,14 @@ cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigne
   if (blocks < 1) blocks = 1;
   TraceScope ts(kKMinmax, -1, double(count) * sizeof(T), s);
   if (aligned16(data))
-    minmax_partial_kernel<T, true><<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(
-        data, static_cast<uint64_t>(count), partial, flags);
+    launch_pdl(minmax_partial_kernel<T, true>, dim3(static_cast<unsigned>(blocks)), dim3(kThreads),
+               0, s, data, static_cast<uint64_t>(count), partial, flags);
   else
-    minmax_partial_kernel<T, false><<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(
-        data, static_cast<uint64_t>(count), partial, flags);
+    launch_pdl(minmax_partial_kernel<T, false>, dim3(static_cast<unsigned>(blocks)), dim3(kThreads),
+               0, s, data, static_cast<uint64_t>(count), partial, flags);
   ts.more_kernels(1);
-  minmax_final_kernel<<<1, kThreads, 0, s>>>(partial, static_cast<int>(blocks), result);
+  launch_pdl(minmax_final_kernel, dim3(1), dim3(kThreads), 0, s, partial, static_cast<int>(blocks),
+             result);
   return cudaGetLastError();
 }
 

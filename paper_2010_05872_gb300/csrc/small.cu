@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "grid.cuh"
 #include "kernels.cuh"
 #include "trace.hpp"
@@ -164,6 +165,7 @@ __device__ __forceinline__ T interp_small(const LevelK<T>& L, const T* cv, bool 
 template <typename T, bool DEC>
 __global__ void __launch_bounds__(kSmallThreads)
 small_levels_kernel(SmallLevels<T> sl, int nlev, T* __restrict__ data) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* base = reinterpret_cast<T*>(smem_raw);
   // Grids G[i], i = 0..nlev (G[nlev] the top), then the load-vector scratch.
@@ -293,7 +295,7 @@ cudaError_t launch_small_levels(const LevelK<T>* lv, int nlev, bool dec, T* data
   TraceScope ts(kKSmallLevels, level, 2.0 * sizeof(T) * double(ntop), s);
   auto kernel = dec ? small_levels_kernel<T, true> : small_levels_kernel<T, false>;
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  kernel<<<1, kSmallThreads, smem, s>>>(sl, nlev, data);
+  launch_pdl(kernel, dim3(1), dim3(kSmallThreads), smem, s, sl, nlev, data);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "kernels.cuh"
 #include "solve_tile.cuh"
 #include "tma.cuh"
@@ -35,6 +36,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 solve_strided_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t outer,
                      int64_t stride, int mode) {
+  grid_dep_enter();
   constexpr int kChunk = Chunk<T>::value;
   const int64_t line = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (line >= outer * stride) return;
@@ -83,6 +85,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 solve_contig_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines, int rows,
                     int mode) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   solve_contig_tile<T>(ax, F, B, nlines, rows, mode, blockIdx.x, smem_raw);
 }
@@ -91,6 +94,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 solve_contig_tma_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines,
                         int rows, int mode, unsigned int* __restrict__ status) {
+  grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   solve_contig_tma_tile<T>(ax, F, B, nlines, rows, mode, status, blockIdx.x, smem_raw);
 }
@@ -102,6 +106,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kSegWarps, 2)
 solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines, int64_t S,
                  int64_t block_stride, int mode) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = ax.nc, L = ax.seg_len;
   const int nseg = blockDim.x >> 5;
@@ -213,6 +218,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 solve_contig_pipe_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines,
                          int rows, int bufelems, int mode, unsigned int* __restrict__ status) {
+  grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_shift[2];
@@ -332,8 +338,8 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
       const int64_t nbatch = (nlines + rows - 1) / rows;
       const unsigned grid = static_cast<unsigned>(std::max<int64_t>(
           1, std::min<int64_t>(nbatch, 152 * static_cast<int64_t>(std::max(per_sm, 1)))));
-      solve_contig_pipe_kernel<T><<<grid, 128, smem, s>>>(lv.ax[2], F, B, nlines, rows, bufelems, m,
-                                                          status);
+      launch_pdl(solve_contig_pipe_kernel<T>, dim3(grid), dim3(128), smem, s, lv.ax[2], F, B,
+                 nlines, rows, bufelems, m, status);
     } else if (a == 2 && per_row <= 112 * 1024) {
       const int64_t nlines = c0 * c1;
       int rows = static_cast<int>(std::min<size_t>(128, (112 * 1024) / per_row));
@@ -341,8 +347,8 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
       const size_t smem = per_row * rows;
       cudaFuncSetAttribute(solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem));
-      solve_contig_kernel<T><<<ceil_div(nlines, rows), 128, smem, s>>>(lv.ax[2], F, B, nlines,
-                                                                        rows, m);
+      launch_pdl(solve_contig_kernel<T>, dim3(ceil_div(nlines, rows)), dim3(128), smem, s, lv.ax[2],
+                 F, B, nlines, rows, m);
     } else if (a != 2 && (lv.ax[a].nc + lv.ax[a].seg_len - 1) / lv.ax[a].seg_len <= kSegWarps) {
       // Strided lines in register-resident segments.
       const int nc = lv.ax[a].nc;
@@ -350,15 +356,15 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
       const int64_t S = (a == 0) ? c1 * c2 : c2;
       const int64_t nlines = (a == 0) ? S : c0 * S;
       const size_t smem = sizeof(T) * (5 * static_cast<size_t>(nc) + 32 * static_cast<size_t>(nseg));
-      solve_seg_kernel<T><<<ceil_div(nlines, 32), 32 * nseg, smem, s>>>(lv.ax[a], F, B, nlines, S,
-                                                                         nc * S, m);
+      launch_pdl(solve_seg_kernel<T>, dim3(ceil_div(nlines, 32)), dim3(32 * nseg), smem, s,
+                 lv.ax[a], F, B, nlines, S, nc * S, m);
     } else {
       // Strided lines; contiguous lines too long for shared memory go here
       // too, as lines of stride 1.
       const int64_t outer = (a == 0) ? 1 : (a == 1) ? c0 : c0 * c1;
       const int64_t stride = (a == 0) ? c1 * c2 : (a == 1) ? c2 : 1;
-      solve_strided_kernel<T><<<ceil_div(outer * stride, 256), 256, 0, s>>>(lv.ax[a], F, B, outer,
-                                                                            stride, m);
+      launch_pdl(solve_strided_kernel<T>, dim3(ceil_div(outer * stride, 256)), dim3(256), 0, s,
+                 lv.ax[a], F, B, outer, stride, m);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

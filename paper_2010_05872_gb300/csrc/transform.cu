@@ -4,6 +4,7 @@
 // too small or too wide for the marching kernel of load_vector.cu.
 #include <algorithm>
 
+#include "pdl.cuh"
 #include "kernels.cuh"
 #include "trace.hpp"
 
@@ -40,6 +41,7 @@ template <typename T, bool DEC>
 __global__ void __launch_bounds__(kThreads)
 load_vector_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict__ coarse,
                    T* __restrict__ F, int tk0, int tk1, int tk2) {
+  grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int n0 = lv.ax[0].n, n1 = lv.ax[1].n, n2 = lv.ax[2].n;
@@ -189,11 +191,13 @@ cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* 
   if (dec) {
     cudaFuncSetAttribute(load_vector_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
-    load_vector_kernel<T, true><<<grid, kThreads, smem, s>>>(lv, fine, coarse, F, tk0, tk1, tk2);
+    launch_pdl(load_vector_kernel<T, true>, dim3(grid), dim3(kThreads), smem, s, lv, fine, coarse,
+               F, tk0, tk1, tk2);
   } else {
     cudaFuncSetAttribute(load_vector_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
-    load_vector_kernel<T, false><<<grid, kThreads, smem, s>>>(lv, fine, coarse, F, tk0, tk1, tk2);
+    launch_pdl(load_vector_kernel<T, false>, dim3(grid), dim3(kThreads), smem, s, lv, fine, coarse,
+               F, tk0, tk1, tk2);
   }
   return cudaGetLastError();
 }
