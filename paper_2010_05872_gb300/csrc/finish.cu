@@ -193,17 +193,8 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
       per_sm = std::max(per_sm, 1);
       const int npairs = (mv.ax[0].n + 1) / 2;
-      const int cols = g.nb1 * g.nb2, slots = 152 * per_sm;
-      int best_t0 = npairs, best_score = 1 << 30;
-      for (int waves = 1; waves <= 16; ++waves) {
-        const int chunks = std::max(1, (slots * waves + cols - 1) / cols);
-        const int t0 = std::min(std::max(4, (npairs + chunks - 1) / chunks), npairs);
-        const int ctas = ((npairs + t0 - 1) / t0) * cols;
-        const int used = (ctas + slots - 1) / slots;
-        const int score = used * slots - ctas + 4 * waves * per_sm;
-        if (score < best_score) { best_score = score; best_t0 = t0; }
-      }
-      g.t0 = best_t0;
+      g.t0 = march_chunk(npairs, g.nb1 * g.nb2, 152 * per_sm, 4, 1,
+                         nf_all * sizeof(T) <= kL2ResidentBytes);
       g.nb0 = (npairs + g.t0 - 1) / g.t0;
       launch_pdl(kernel, dim3(static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2)), dim3(g.threads), smem,
                  s, mv, nodal_src, interp_src, sign, fine, g, status);

@@ -4,6 +4,9 @@
 // padded leading axes have n = nc = 1 and identity tables.
 #pragma once
 
+#include <algorithm>
+#include <climits>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -106,5 +109,36 @@ template <typename T>
 cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigned int* flags,
                           double* result, cudaStream_t s);
 constexpr int kMinmaxBlocks = 1216;  // 8 x 152 SMs
+
+// Planes (or plane pairs) per CTA of a marching kernel over `units` planes
+// with `cols` CTAs per plane chunk and `slots` resident CTAs on the GPU.
+// A large level keeps chunks of at least `big_min` (a chunk's halo planes
+// are read again from DRAM) and picks the chunk that leaves the fewest slots
+// idle; a level small enough to stay in L2 takes the chunk that minimises
+// the longest march, waves x (chunk + halo), which gives small levels many
+// short marches instead of a few long ones.
+inline int march_chunk(int units, int cols, int slots, int big_min, int halo, bool l2_resident) {
+  int best = units;
+  if (l2_resident) {
+    int64_t best_t = INT64_MAX;
+    for (int t0 = 1; t0 <= units; ++t0) {
+      const int64_t ctas = int64_t((units + t0 - 1) / t0) * cols;
+      const int64_t t = ((ctas + slots - 1) / slots) * (t0 + halo);
+      if (t < best_t) { best_t = t; best = t0; }
+    }
+    return best;
+  }
+  int best_score = 1 << 30;
+  for (int waves = 1; waves <= 16; ++waves) {
+    const int chunks = std::max(1, (slots * waves + cols - 1) / cols);
+    const int t0 = std::min(std::max(big_min, (units + chunks - 1) / chunks), units);
+    const int ctas = ((units + t0 - 1) / t0) * cols;
+    const int used = (ctas + slots - 1) / slots;
+    const int score = used * slots - ctas + 4 * waves * (slots / 152);
+    if (score < best_score) { best_score = score; best = t0; }
+  }
+  return best;
+}
+constexpr size_t kL2ResidentBytes = size_t(96) << 20;  // levels below this march in short chunks
 
 }  // namespace mgb

@@ -95,22 +95,14 @@ cudaError_t launch_load_vector_march(const LevelK<T>& lv_in, bool dec, const T* 
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
   per_sm = std::max(per_sm, 1);
-  // Coarse planes per CTA: aim at whole waves over the 152 SMs, with at
-  // least 8 per CTA so the 3 halo planes stay a small overhead.
-  const int cols = g.nb2 * g.nb1;
-  const int slots = 152 * per_sm;
-  int best_t0 = c0, best_score = 1 << 30;
-  for (int waves = 1; waves <= 16; ++waves) {
-    const int chunks = std::max(1, (slots * waves + cols - 1) / cols);
-    const int t0 = std::min(std::max(8, (c0 + chunks - 1) / chunks), c0);
-    const int ctas = ((c0 + t0 - 1) / t0) * cols;
-    const int used = (ctas + slots - 1) / slots;
-    const int score = used * slots - ctas + 4 * waves * per_sm;  // idle slots; prefer fewer CTAs
-    if (score < best_score) { best_score = score; best_t0 = t0; }
-  }
-  g.t0 = best_t0;
-  g.nb0 = (c0 + g.t0 - 1) / g.t0;
+  // Coarse planes per CTA: whole waves over the 152 SMs with at least 8
+  // planes per CTA (the 3 halo planes stay a small overhead), or, for a level
+  // that stays in L2, the shortest longest march (a CTA marches 2 t0 + 3
+  // fine planes).
   const uint64_t count = uint64_t(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
+  g.t0 = march_chunk(c0, g.nb2 * g.nb1, 152 * per_sm, 8, 2,
+                     count * sizeof(T) <= kL2ResidentBytes);
+  g.nb0 = (c0 + g.t0 - 1) / g.t0;
   const unsigned grid = static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2);
   launch_pdl(kernel, dim3(grid), dim3(g.threads), smem, s, lv, fine, coarse, F, g, count, status);
   return cudaGetLastError();
