@@ -34,6 +34,9 @@ explicit finite-element operators assembled from the grid coordinates:
   ``tau_l = k tau_{l-1}``, ``k = sqrt(2^d)``.
 * Quantizer (Section 4.1): zero-centred bins of width ``q_l = 2 tau_l``,
   label ``round(x / q_l)`` with ties away from zero, value ``label * q_l``.
+* Adaptive stopping level (Section 4.2, Algorithm 1 lines 1-16): sampled
+  sums of the Lorenzo and interpolation prediction errors with the paper's
+  penalty factors, level by level from the finest.
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
 non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
@@ -43,7 +46,9 @@ Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
 (exact rationals from the finite-element definition, quadrature-based
 orthogonality, Lemma 1 and the printed mass matrix of Section 5.4, the
 interpolation stencils of Eq. (multilinear_interp), dense Kronecker brute
-force, invariants and bounds).  ``linf_constant`` is a reading (the paper
+force, invariants and bounds; the adaptive stopping level by hand-derived
+sums in tests/golden/prediction_errors.txt and exactness properties of the
+two predictors).  ``linf_constant`` is a reading (the paper
 gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
 worst-case error amplification, and its exact value is "parity unpinned" with
 respect to the paper.
@@ -62,6 +67,8 @@ __all__ = [
     "project_axis", "project", "interpolate", "decompose", "recompose",
     "linf_constant", "level_tolerances", "node_levels", "llround",
     "quantize", "dequantize", "value_range",
+    "LORENZO_PENALTY", "INTERP_PENALTY", "sampled_blocks", "prediction_errors",
+    "adaptive_stop_level",
 ]
 
 
@@ -411,3 +418,104 @@ def value_range(u: np.ndarray) -> float:
     """``max u - min u`` in FP64: the scale of a relative error bound."""
     u = np.asarray(u, dtype=np.float64)
     return float(u.max() - u.min())
+
+
+# --------------------------------------------------------------------------
+# Adaptive stopping level (Section 4.2, Algorithm 1 lines 1-16)
+# --------------------------------------------------------------------------
+
+# Penalty factors, in units of the level's tolerance tau_0 (Section 4.2): the
+# 3D Lorenzo predictor (Eq. (lorenzo)) and multilinear interpolation at edge,
+# plane and cube nodes (Eq. (interp)), keyed by the number of axes along
+# which the node is a cell midpoint.  The paper derives them for 3D only.
+LORENZO_PENALTY = 1.22
+INTERP_PENALTY = {1: 0.369, 2: 0.259, 3: 0.182}
+
+
+def sampled_blocks(H: Hierarchy, l: int):
+    """The sampled ``3^d`` blocks of the level-l grid (Section 4.2): a block
+    is a cell of the level-(l-1) grid, spanning level-l indices
+    ``keep[b] .. keep[b+1]`` on every axis (3 nodes, or 2 for the last cell
+    of an even axis); one cell in four is taken along each axis (``b`` a
+    multiple of 4).  Returns per-axis lists of (first, last) index pairs."""
+    out = []
+    for op in H.ops(l):
+        keep = op.keep
+        out.append([(int(keep[b]), int(keep[b + 1])) for b in range(0, len(keep) - 1, 4)])
+    return out
+
+
+def _lorenzo(v: np.ndarray, idx) -> float:
+    """Lorenzo prediction at ``idx`` (Eq. (lorenzo)): the signed sum over the
+    2^d - 1 neighbours with some indices decreased by one, ``+`` for an odd
+    number of decreased indices; neighbours outside the grid count as 0."""
+    d = v.ndim
+    pred = 0.0
+    for mask in range(1, 1 << d):
+        nb = list(idx)
+        inside = True
+        for a in range(d):
+            if mask >> a & 1:
+                nb[a] -= 1
+                inside = inside and nb[a] >= 0
+        if inside:
+            sign = 1.0 if bin(mask).count("1") % 2 == 1 else -1.0
+            pred += sign * float(v[tuple(nb)])
+    return pred
+
+
+def prediction_errors(v: np.ndarray, H: Hierarchy, l: int, tau0: float):
+    """``(E_Lorenzo, E_interp)`` of Algorithm 1 lines 5-9 for the level-l
+    grid ``v``: over every coefficient node (a node outside ``N_{l-1}``) of
+    the sampled blocks, ``|Lorenzo prediction - v| + 1.22 tau0`` and
+    ``|Pi_{l-1} v - v| + p tau0`` with ``p`` the edge / plane / cube penalty
+    of the node (Eqs. (lorenzo), (interp)).  Interpolation uses the grid's
+    own coordinates (the uniform-grid stencils of Eq. (multilinear_interp)
+    are its special case).  Sums run over the blocks in C order and over the
+    nodes of a block in C order.  3D only."""
+    if H.ndim != 3:
+        raise ValueError("the penalty factors of Section 4.2 are for 3D grids")
+    v = np.asarray(v, dtype=np.float64)
+    if v.shape != H.levels[l]:
+        raise ValueError("array shape does not match level l")
+    keep = [o.keep for o in H.ops(l)]
+    pred_i = interpolate(v[np.ix_(*keep)], H, l)
+    is_nodal = [np.isin(np.arange(n), k) for n, k in zip(v.shape, keep)]
+    blocks = sampled_blocks(H, l)
+    e_lor = 0.0
+    e_int = 0.0
+    for b0 in blocks[0]:
+        for b1 in blocks[1]:
+            for b2 in blocks[2]:
+                for i in range(b0[0], b0[1] + 1):
+                    for j in range(b1[0], b1[1] + 1):
+                        for k in range(b2[0], b2[1] + 1):
+                            mids = (int(not is_nodal[0][i]) + int(not is_nodal[1][j]) +
+                                    int(not is_nodal[2][k]))
+                            if mids == 0:
+                                continue
+                            x = float(v[i, j, k])
+                            e_lor += abs(_lorenzo(v, (i, j, k)) - x) + LORENZO_PENALTY * tau0
+                            e_int += abs(float(pred_i[i, j, k]) - x) + INTERP_PENALTY[mids] * tau0
+    return e_lor, e_int
+
+
+def adaptive_stop_level(u: np.ndarray, H: Hierarchy, tau: float):
+    """Algorithm 1 lines 1-16: for ``l = L, L-1, ..``, with ``tau_0`` the
+    tolerance of level ``l`` were it the stopping level (line 3), sample
+    ``Q_l u`` and stop at ``l`` when the Lorenzo estimate is below the
+    interpolation estimate; otherwise project to ``Q_{l-1} u`` and go on.
+    Reading: the loop ends at level 1 (a level-0 grid has no coarser grid to
+    interpolate from), so the stopping level is 0 when no level stops it.
+    Returns the stopping level and ``{l: (E_Lorenzo, E_interp)}`` for every
+    sampled level."""
+    v = np.asarray(u, dtype=np.float64)
+    sums = {}
+    for l in range(H.L, 0, -1):
+        tau0 = float(level_tolerances(H, l, tau)[l])
+        e = prediction_errors(v, H, l, tau0)
+        sums[l] = e
+        if e[0] < e[1]:
+            return l, sums
+        v = project(v, H, l)
+    return 0, sums

@@ -485,3 +485,95 @@ def test_dequantize_rounds_the_fp64_product_to_fp32():
     got = O.dequantize(k, H, 0, taus, dtype=np.float32)
     exp = np.array([np.float32(float(v) * 0.1) for v in k])
     assert np.array_equal(got, exp)
+
+
+# ------------------------------------------- adaptive stopping level ---
+
+def _pe_cases():
+    cases = []
+    with open(os.path.join(GOLDEN, "prediction_errors.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            dims_s, field_s, l_s, tau_s, el_s, ei_s = [p.strip() for p in line.split("|")]
+            cases.append((tuple(int(v) for v in dims_s.split("x")), field_s, int(l_s),
+                          float(tau_s), float(el_s), float(ei_s)))
+    return cases
+
+
+def _pe_field(dims, spec):
+    if spec.startswith("spike"):
+        v = np.zeros(dims)
+        v[tuple(int(t) for t in spec.split()[1].split(","))] = 1.0
+        return v
+    assert spec == "xsq"
+    i = np.arange(dims[0], dtype=np.float64)
+    return np.broadcast_to((i * i)[:, None, None], dims).copy()
+
+
+@pytest.mark.parametrize("case", _pe_cases())
+def test_prediction_errors_hand_sums(case):
+    dims, spec, l, tau0, e_lor, e_int = case
+    H = O.Hierarchy(dims)
+    got = O.prediction_errors(_pe_field(dims, spec), H, l, tau0)
+    assert got[0] == pytest.approx(e_lor, rel=1e-12)
+    assert got[1] == pytest.approx(e_int, rel=1e-12)
+
+
+def test_sampled_blocks_one_in_four():
+    # 17 nodes: cells [0,2], [2,4], .. [14,16]; cells 0 and 4 are sampled.
+    # 10 nodes (even): coarse nodes 0,2,4,6,8,9; cells 0 and 4, the latter
+    # the 2-node end cell [8,9].
+    H = O.Hierarchy((17, 10, 5))
+    b = O.sampled_blocks(H, H.L)
+    assert b[0] == [(0, 2), (8, 10)]
+    assert b[1] == [(0, 2), (8, 9)]
+    assert b[2] == [(0, 2)]
+
+
+def test_lorenzo_exact_where_mixed_difference_vanishes():
+    # The 3D Lorenzo prediction error is the mixed third difference of u, so
+    # it vanishes at interior nodes for any sum of functions each missing one
+    # axis; there the estimate reduces to the penalties.  A product x*y*z
+    # has mixed difference 1 and misses by exactly 1 everywhere inside.
+    rng = _rng(5)
+    dims = (9, 9, 9)
+    f, g, h = rng.standard_normal((3, 9, 9))
+    i, j, k = np.meshgrid(*[np.arange(9)] * 3, indexing="ij")
+    u = f[i, j] + g[j, k] + h[i, k]
+    xyz = (i * j * k).astype(np.float64)
+    for x in range(1, 9):
+        for y in range(1, 9):
+            for z in range(1, 9):
+                assert abs(O._lorenzo(u, (x, y, z)) - u[x, y, z]) < 1e-12
+                assert abs(O._lorenzo(xyz, (x, y, z)) - xyz[x, y, z]) == pytest.approx(1.0)
+
+
+def test_interp_estimate_of_multilinear_field_is_penalties_only():
+    # Multilinear interpolation reproduces a multilinear field, so E_interp
+    # is the penalty sum: per full block 12 edge, 6 plane, 1 cube nodes.
+    dims = (17, 9, 13)
+    coords = [F.geometric_coords(n, 1.05) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    X, Y, Z = np.meshgrid(*coords, indexing="ij")
+    u = 1.0 + 2.0 * X - Y + 0.5 * Z + 3.0 * X * Y - X * Y * Z
+    tau0 = 0.3
+    nblocks = np.prod([len(b) for b in O.sampled_blocks(H, H.L)])
+    _, e_int = O.prediction_errors(u, H, H.L, tau0)
+    assert e_int == pytest.approx(nblocks * (12 * 0.369 + 6 * 0.259 + 0.182) * tau0, rel=1e-10)
+
+
+def test_adaptive_stop_level_decisions():
+    H = O.Hierarchy((9, 9, 9))
+    u = _pe_field((9, 9, 9), "xsq")
+    # Small tau: Lorenzo (1 + 23.18 tau0) beats interpolation (9 + 6.16 tau0)
+    # on the finest level, which becomes the stopping level.
+    stop, sums = O.adaptive_stop_level(u, H, 1e-3)
+    assert stop == H.L and list(sums) == [H.L]
+    # Large tau: the Lorenzo penalty dominates; the finest level is decomposed.
+    stop, sums = O.adaptive_stop_level(u, H, 1e3)
+    assert stop < H.L and sums[H.L][0] > sums[H.L][1]
+    # A 2D grid has no penalty factors in the paper.
+    with pytest.raises(ValueError):
+        O.prediction_errors(np.zeros((9, 9)), O.Hierarchy((9, 9)), 2, 1.0)
