@@ -95,6 +95,28 @@ int mgard_decompose(int ndim, const int64_t* dims, const double* const* coords, 
                     int stop_level, void* data, void* workspace, size_t ws_bytes,
                     void* stream);
 
+/* Adaptive decomposition, in place (Section 4.2, Algorithm 1 lines 1-16):
+ * for l = L, L-1, .., 1 the level-l grid is sampled (the cells of the
+ * level-(l-1) grid with every index a multiple of 4, i.e. one 3^3 block in
+ * four per dimension) and, over the coefficient nodes of the sampled blocks,
+ * E_Lorenzo = sum |Lorenzo prediction - u| + 1.22 tau_0 (Eq. lorenzo) and
+ * E_interp = sum |multilinear interpolation - u| + p tau_0 (Eq. interp;
+ * p = 0.369 / 0.259 / 0.182 at edge / plane / cube nodes) are formed in
+ * FP64, with tau_0 the tolerance of level l were it the stopping level
+ * (line 3; tau_linf absolute, > 0) and Lorenzo neighbours outside the grid
+ * taken as 0.  If E_Lorenzo < E_interp the decomposition stops at l~ = l;
+ * otherwise level l is decomposed and the loop goes on; l~ = 0 when no level
+ * stops it.  On return *stop_out = l~ and `data` equals mgard_decompose with
+ * stop_level = l~ (up to FP rounding order); recompose and quantize it with
+ * that stop level.  sums_out (host, may be NULL) receives 2 (L + 1) doubles:
+ * (E_Lorenzo, E_interp) of level l at [2l], [2l + 1], NaN for levels not
+ * sampled.  3D grids only (the paper's penalty factors are for 3D):
+ * MGARD_ERR_SHAPE otherwise.  Synchronizes `stream` once per sampled level.
+ * Workspace and other errors as mgard_decompose. */
+int mgard_decompose_adaptive(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                             double tau_linf, void* data, void* workspace, size_t ws_bytes,
+                             int* stop_out, double* sums_out, void* stream);
+
 /* Multilevel recomposition, in place: the exact inverse of mgard_decompose
  * with the same dims, coords, dtype and stop_level (Section 2, recomposition
  * steps 1-5).  Same workspace rule. */

@@ -39,6 +39,10 @@ _SIGNATURES = {
                                        _VP, _VP, ctypes.c_size_t, _VP]),
     "mgard_recompose": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                        _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_decompose_adaptive": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
+                                                ctypes.c_double, _VP, _VP, ctypes.c_size_t,
+                                                ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_double), _VP]),
     "mgard_quantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, _VP, _VP, _DP, _VP]),
     "mgard_dequantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
@@ -175,6 +179,18 @@ def mgard_decompose(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes,
     s = _Shape(dims, coords)
     return lib().mgard_decompose(s.ndim, s.dims, s.coords, dtype, stop_level, data_ptr, ws_ptr,
                                  ws_bytes, stream)
+
+
+def mgard_decompose_adaptive(dims, coords, dtype, tau_linf, data_ptr, ws_ptr, ws_bytes, stream):
+    """Adaptive decomposition.  Returns (rc, stop_level, sums) with sums an
+    (L + 1) x 2 array of (E_Lorenzo, E_interp) per level (NaN: not sampled)."""
+    s = _Shape(dims, coords)
+    L = mgard_num_levels(dims)
+    stop = ctypes.c_int(-1)
+    sums = (ctypes.c_double * (2 * (L + 1)))()
+    rc = lib().mgard_decompose_adaptive(s.ndim, s.dims, s.coords, dtype, float(tau_linf), data_ptr,
+                                        ws_ptr, ws_bytes, ctypes.byref(stop), sums, stream)
+    return rc, stop.value, np.array(sums[:], dtype=np.float64).reshape(L + 1, 2)
 
 
 def mgard_decompose_noalloc(dims, coords, dtype, stop_level, data_ptr, stream,
@@ -457,6 +473,19 @@ def decompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
                          ws.numel(), _stream(stream))
     _check(rc, "mgard_decompose")
     return x
+
+
+def decompose_adaptive(x, tau_linf: float, coords=None, ws=None, stream=None):
+    """In-place adaptive decomposition of a 3D CUDA tensor (Algorithm 1):
+    returns (stop_level, sums) with the chosen stopping level and the sampled
+    (E_Lorenzo, E_interp) per level."""
+    _cuda_tensor(x, "x")
+    if ws is None:
+        ws = workspace(x.shape, x.dtype, x.device)
+    rc, stop, sums = mgard_decompose_adaptive(x.shape, coords, dtype_code(x), tau_linf, x.data_ptr(),
+                                              ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(rc, "mgard_decompose_adaptive")
+    return stop, sums
 
 
 def decompose_noalloc(x, coords=None, stop_level: int = 0, stream=None, wait: bool = False):

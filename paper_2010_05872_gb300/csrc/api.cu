@@ -269,6 +269,47 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
   return MGARD_OK;
 }
 
+// Adaptive decomposition (Algorithm 1, lines 1-16): from the finest level
+// down, the sampled prediction-error sums of the level-l grid decide between
+// stopping at l and decomposing it; then the finish passes of the decomposed
+// levels.  One host synchronization per sampled level.
+template <typename T>
+int run_adaptive(const DevPlan& p, double tau, T* data, char* ws, DevCtx* c, cudaStream_t s,
+                 int* stop_out, double* sums) {
+  const int L = p.h.L;
+  const auto& lv = levels<T>(p);
+  std::vector<T*> B(L + 1), F(L + 1);
+  B[L] = data;
+  for (int l = 0; l < L; ++l) {
+    B[l] = reinterpret_cast<T*>(ws + p.offB[l]);
+    F[l] = reinterpret_cast<T*>(ws + p.offF[l]);
+  }
+  unsigned int* status = c->flags + 1;
+  double t[kMaxLevels];
+  int stop = 0;
+  for (int l = L; l >= 1; --l) {
+    level_tolerances(p.h, l, tau, t);  // t[l]: tau_0 were l the stopping level (line 3)
+    MGB_TRY(launch_prediction_errors<T>(lv[l], B[l], t[l], c->partial, c->result, l, s));
+    MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MGB_TRY(cudaStreamSynchronize(s));
+    const double e_lor = c->h_result[0], e_int = c->h_result[1];
+    if (sums) {
+      sums[2 * l] = e_lor;
+      sums[2 * l + 1] = e_int;
+    }
+    if (e_lor < e_int) {
+      stop = l;
+      break;
+    }
+    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, status, s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, status, s));
+  }
+  for (int l = stop + 1; l <= L; ++l)
+    MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, status, s));
+  *stop_out = stop;
+  return MGARD_OK;
+}
+
 int transform(bool dec, int ndim, const int64_t* dims, const double* const* coords, int dtype,
               int stop_level, void* data, void* workspace, size_t ws_bytes, void* stream) {
   DevPlan* p = nullptr;
@@ -401,6 +442,31 @@ int mgard_decompose(int ndim, const int64_t* dims, const double* const* coords, 
 int mgard_recompose(int ndim, const int64_t* dims, const double* const* coords, int dtype,
                     int stop_level, void* data, void* workspace, size_t ws_bytes, void* stream) {
   return transform(false, ndim, dims, coords, dtype, stop_level, data, workspace, ws_bytes, stream);
+}
+
+int mgard_decompose_adaptive(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                             double tau_linf, void* data, void* workspace, size_t ws_bytes,
+                             int* stop_out, double* sums_out, void* stream) {
+  if (stop_out == nullptr) return MGARD_ERR_ARG;
+  if (!(tau_linf > 0.0) || !std::isfinite(tau_linf)) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  if (p->h.ndim != 3) return MGARD_ERR_SHAPE;
+  rc = check_transform_args(*p, 0, data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  if (sums_out)
+    for (int i = 0; i < 2 * (p->h.L + 1); ++i) sums_out[i] = std::nan("");
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  return dtype == MGARD_F64
+             ? run_adaptive<double>(*p, tau_linf, static_cast<double*>(data), ws, c, s, stop_out,
+                                    sums_out)
+             : run_adaptive<float>(*p, tau_linf, static_cast<float*>(data), ws, c, s, stop_out,
+                                   sums_out);
 }
 
 int mgard_decompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,

@@ -110,6 +110,14 @@ cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigne
                           double* result, cudaStream_t s);
 constexpr int kMinmaxBlocks = 1216;  // 8 x 152 SMs
 
+// Sampled sums (E_Lorenzo, E_interp) of the adaptive stopping level over the
+// level-l grid `v` (the n of lv's axes; 3D), with the level tolerance tau0,
+// written to result[0..1] (device); `partial` holds 2 x kMinmaxBlocks
+// doubles of scratch.
+template <typename T>
+cudaError_t launch_prediction_errors(const LevelK<T>& lv, const T* v, double tau0, double* partial,
+                                     double* result, int level, cudaStream_t s);
+
 // Planes (or plane pairs) per CTA of a marching kernel over `units` planes
 // with `cols` CTAs per plane chunk and `slots` resident CTAs on the GPU.
 // A large level keeps chunks of at least `big_min` (a chunk's halo planes

@@ -21,6 +21,7 @@ enum KernelKind : int {
   kKDequantize,
   kKMinmax,
   kKSmallLevels,
+  kKPredErr,
   kKNumKinds
 };
 
