@@ -439,6 +439,56 @@ def run_gpu(args, rank, world, local_rank):
     }
     del x64, u64, labels
 
+    # Adaptive stopping level (Algorithm 1): the level chosen per bound, and
+    # at 1e-3 x range the time of the adaptive decomposition against the
+    # plain one at that level and the sampled-error kernels' share.
+    ws = B.workspace(DIMS, torch.float32, dev)
+    rng_lo, rng_hi = B.value_range(u)
+    adaptive = {"stop_level": {}}
+    for rel in BOUNDS:
+        x.copy_(u)
+        stop_a, _ = B.decompose_adaptive(x, rel * (rng_hi - rng_lo), None, ws)
+        adaptive["stop_level"][f"{rel:g}"] = stop_a
+    tau_a = 1e-3 * (rng_hi - rng_lo)
+    ka = max(3, min(args.steps // 40, 10))
+    t_ad, t_pl = [], []
+    for i in range(ka):
+        x.copy_(u)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        stop_a, sums_a = B.decompose_adaptive(x, tau_a, None, ws)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        t_ad.append(ea.elapsed_time(eb))
+    # The sampling kernels' own time, from a traced run of the same calls.
+    B.mgard_trace_select(-1)
+    B.mgard_trace_enable(True)
+    for i in range(ka):
+        x.copy_(u)
+        B.decompose_adaptive(x, tau_a, None, ws)
+    torch.cuda.synchronize()
+    B.mgard_trace_enable(False)
+    pe = [r for r in B.mgard_trace_read() if r["kernel"] == "prediction_errors_kernel"]
+    for i in range(ka):
+        x.copy_(u)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        B.decompose(x, None, stop_a, ws)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        t_pl.append(ea.elapsed_time(eb))
+    adaptive.update({
+        "bound_rel": 1e-3, "stop": stop_a,
+        "adaptive_ms": statistics.median(t_ad), "plain_at_stop_ms": statistics.median(t_pl),
+        "sampling_ms": sum(r["total_ms"] for r in pe) / ka,
+        "sampling_ms_by_level": {str(r["level"]): r["total_ms"] / ka for r in pe},
+        "sampled_levels": int(sum(r["launches"] for r in pe) / ka),
+        "note": ("median of %d untraced runs each; sampling_ms from traced runs (event pairs "
+                 "inflate the small levels); the adaptive call waits on the host once per level "
+                 "above 2e7 nodes and once for all smaller levels" % ka),
+    })
+    x.copy_(u)
+
     # End to end through the host-buffer entry points.
     ws = B.workspace(DIMS, torch.float32, dev)
     labels = torch.empty(DIMS, dtype=torch.int64, device=dev)
@@ -498,6 +548,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clocks.summary(t0, t1),
         "fp64": fp64,
+        "adaptive": adaptive,
         "linf_over_tau": linf,
         "top_kernels": kernels,
         "kinds_ms_per_step": {k: round(v, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1])},

@@ -101,8 +101,9 @@ int mgard_decompose(int ndim, const int64_t* dims, const double* const* coords, 
  * four per dimension) and, over the coefficient nodes of the sampled blocks,
  * E_Lorenzo = sum |Lorenzo prediction - u| + 1.22 tau_0 (Eq. lorenzo) and
  * E_interp = sum |multilinear interpolation - u| + p tau_0 (Eq. interp;
- * p = 0.369 / 0.259 / 0.182 at edge / plane / cube nodes) are formed in
- * FP64, with tau_0 the tolerance of level l were it the stopping level
+ * p = 0.369 / 0.259 / 0.182 at edge / plane / cube nodes) are summed in
+ * FP64 (the per-node residuals in the grid's precision), with tau_0 the
+ * tolerance of level l were it the stopping level
  * (line 3; tau_linf absolute, > 0) and Lorenzo neighbours outside the grid
  * taken as 0.  If E_Lorenzo < E_interp the decomposition stops at l~ = l;
  * otherwise level l is decomposed and the loop goes on; l~ = 0 when no level

@@ -176,6 +176,8 @@ DevCtx* get_ctx() {
   if (cudaMalloc(&c->result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
   if (cudaMallocHost(&c->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
   if (cudaMallocHost(&c->h_result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&c->sums, 2 * kMaxLevels * sizeof(double)) != cudaSuccess) return nullptr;
+  if (cudaMallocHost(&c->h_sums, 2 * kMaxLevels * sizeof(double)) != cudaSuccess) return nullptr;
   DevCtx* raw = c.get();
   g_ctx.emplace(device, std::move(c));
   return raw;
@@ -269,6 +271,11 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
   return MGARD_OK;
 }
 
+// Levels of more nodes than this are decided one at a time (decomposing one
+// in vain would cost more than the wait); the smaller ones are decomposed
+// ahead of their decisions.
+constexpr int64_t kAdaptiveAheadNodes = 20000000;
+
 // Adaptive decomposition (Algorithm 1, lines 1-16): from the finest level
 // down, the sampled prediction-error sums of the level-l grid decide between
 // stopping at l and decomposing it; then the finish passes of the decomposed
@@ -286,23 +293,59 @@ int run_adaptive(const DevPlan& p, double tau, T* data, char* ws, DevCtx* c, cud
   }
   unsigned int* status = c->flags + 1;
   double t[kMaxLevels];
-  int stop = 0;
-  for (int l = L; l >= 1; --l) {
-    level_tolerances(p.h, l, tau, t);  // t[l]: tau_0 were l the stopping level (line 3)
-    MGB_TRY(launch_prediction_errors<T>(lv[l], B[l], t[l], c->partial, c->result, l, s));
-    MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    MGB_TRY(cudaStreamSynchronize(s));
-    const double e_lor = c->h_result[0], e_int = c->h_result[1];
+  auto nodes = [&](int l) { return p.h.shape[l][0] * p.h.shape[l][1] * p.h.shape[l][2]; };
+  auto decompose_level = [&](int l) -> int {
+    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, status, s));
+    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, status, s));
+    return MGARD_OK;
+  };
+  auto record = [&](int l) {
     if (sums) {
-      sums[2 * l] = e_lor;
-      sums[2 * l + 1] = e_int;
+      sums[2 * l] = c->h_sums[2 * l];
+      sums[2 * l + 1] = c->h_sums[2 * l + 1];
     }
-    if (e_lor < e_int) {
+    return c->h_sums[2 * l] < c->h_sums[2 * l + 1];  // Lorenzo wins: stop here
+  };
+  int stop = -1;
+  int l = L;
+  // Large levels one at a time: sample, wait for the sums, decide.
+  for (; l >= 1 && nodes(l) > kAdaptiveAheadNodes; --l) {
+    level_tolerances(p.h, l, tau, t);  // t[l]: tau_0 were l the stopping level (line 3)
+    MGB_TRY(launch_prediction_errors<T>(lv[l], B[l], t[l], c->partial, c->sums + 2 * l, l, s));
+    MGB_TRY(cudaMemcpyAsync(c->h_sums + 2 * l, c->sums + 2 * l, 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    MGB_TRY(cudaStreamSynchronize(s));
+    if (record(l)) {
       stop = l;
       break;
     }
-    MGB_TRY(launch_load_vector<T>(lv[l], true, B[l], B[l - 1], F[l - 1], l, status, s));
-    MGB_TRY(launch_solves<T>(lv[l], F[l - 1], B[l - 1], kApplyDecompose, l, status, s));
+    const int rc = decompose_level(l);
+    if (rc != MGARD_OK) return rc;
+  }
+  if (stop < 0) {
+    // The smaller levels all at once: each is sampled and decomposed without
+    // a wait (the load vector and solves of a level write only coarser
+    // arrays, so work below the stopping level changes nothing that is
+    // kept); one read of their sums then gives the stopping level, the first
+    // from the finest whose Lorenzo sum is below its interpolation sum.
+    const int top = l;
+    for (int m = top; m >= 1; --m) {
+      level_tolerances(p.h, m, tau, t);
+      MGB_TRY(launch_prediction_errors<T>(lv[m], B[m], t[m], c->partial, c->sums + 2 * m, m, s));
+      const int rc = decompose_level(m);
+      if (rc != MGARD_OK) return rc;
+    }
+    if (top >= 1) {
+      MGB_TRY(cudaMemcpyAsync(c->h_sums + 2, c->sums + 2, 2 * top * sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+      MGB_TRY(cudaStreamSynchronize(s));
+    }
+    stop = 0;
+    for (int m = top; m >= 1; --m)
+      if (record(m)) {
+        stop = m;
+        break;
+      }
   }
   for (int l = stop + 1; l <= L; ++l)
     MGB_TRY(launch_finish<T>(lv[l], B[l - 1], F[l - 1], T(-1), B[l], l, status, s));

@@ -45,6 +45,8 @@ struct DevCtx {
   double* result = nullptr;       // [2]
   unsigned int* h_flags = nullptr;  // pinned host mirrors
   double* h_result = nullptr;
+  double* sums = nullptr;         // [2 * kMaxLevels] per-level sums of the adaptive decomposition
+  double* h_sums = nullptr;       // pinned host mirror
   std::mutex mu;                  // serialises the calls that wait on these flags
 };
 

@@ -4,7 +4,8 @@ sampled level, and the decomposed array.
 
 Tolerances: the sums are FP64 on both sides; with FP64 data the level grids
 agree to ~1e-14 (relative 1e-10 asserted); with FP32 data the GPU's level
-grids carry FP32 rounding (relative 1e-4 asserted).  The decision is an
+grids and its per-node residuals carry FP32 rounding (relative 1e-4
+asserted).  The decision is an
 integer taken from two FP64 sums: each case is chosen so that the oracle's
 margin |E_Lorenzo - E_interp| / max is far above the sums' tolerance, and the
 test checks that before comparing levels.
