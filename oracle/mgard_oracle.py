@@ -37,6 +37,9 @@ explicit finite-element operators assembled from the grid coordinates:
 * Adaptive stopping level (Section 4.2, Algorithm 1 lines 1-16): sampled
   sums of the Lorenzo and interpolation prediction errors with the paper's
   penalty factors, level by level from the finest.
+* Progressive recomposition (Section 1, data refactoring): ``Q_k u`` on the
+  level-k grid from the decomposed array; and the iso-surface area of a 3D
+  grid function (Section 6.2.2's analysis) by marching tetrahedra.
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
 non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
@@ -48,7 +51,9 @@ orthogonality, Lemma 1 and the printed mass matrix of Section 5.4, the
 interpolation stencils of Eq. (multilinear_interp), dense Kronecker brute
 force, invariants and bounds; the adaptive stopping level by hand-derived
 sums in tests/golden/prediction_errors.txt and exactness properties of the
-two predictors).  ``linf_constant`` is a reading (the paper
+two predictors; partial recomposition by the projection chain; the iso
+area by planar surfaces, exact, and a sphere's convergence).
+``linf_constant`` is a reading (the paper
 gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
 worst-case error amplification, and its exact value is "parity unpinned" with
 respect to the paper.
@@ -68,7 +73,7 @@ __all__ = [
     "linf_constant", "level_tolerances", "node_levels", "llround",
     "quantize", "dequantize", "value_range",
     "LORENZO_PENALTY", "INTERP_PENALTY", "sampled_blocks", "prediction_errors",
-    "adaptive_stop_level",
+    "adaptive_stop_level", "recompose_partial", "iso_area",
 ]
 
 
@@ -519,3 +524,90 @@ def adaptive_stop_level(u: np.ndarray, H: Hierarchy, tau: float):
             return l, sums
         v = project(v, H, l)
     return 0, sums
+
+
+# --------------------------------------------------------------------------
+# Progressive recomposition and iso-surface area (Section 1; Section 6.2.2)
+# --------------------------------------------------------------------------
+
+def recompose_partial(umc: np.ndarray, H: Hierarchy, stop_level: int, level: int) -> np.ndarray:
+    """``Q_k u`` on the level-k grid from the decomposed array ``umc``
+    (stopping level ``stop_level`` <= k = ``level`` <= L): the refactored
+    reconstruction of reduced size that Section 1 describes, obtained by
+    summing the components of levels ``stop_level .. k`` only, i.e. the
+    recomposition of the levels up to k (Section 2, recomposition steps
+    1-5, stopped at level k)."""
+    _check_stop(H, stop_level)
+    if not stop_level <= level <= H.L:
+        raise ValueError("target level outside [stop level, L]")
+    umc = np.asarray(umc, dtype=np.float64)
+    v = umc[np.ix_(*H.index[stop_level])].copy()
+    for l in range(stop_level + 1, level + 1):
+        w = umc[np.ix_(*H.index[l])].copy()
+        w[H.nodal_mask(l)] = 0.0
+        z = project(w, H, l)
+        v = interpolate(v - z, H, l) + w
+    return v
+
+
+# The 6 tetrahedra of a cell around its main diagonal (corner 0 to corner 7);
+# corner c has offsets ((c >> 2) & 1, (c >> 1) & 1, c & 1) along axes 0, 1, 2.
+TETS = ((0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7), (0, 2, 6, 7), (0, 4, 5, 7), (0, 4, 6, 7))
+
+
+def _tri_area(a, b, c) -> float:
+    return 0.5 * float(np.linalg.norm(np.cross(np.subtract(b, a), np.subtract(c, a))))
+
+
+def _tet_area(p, f, iso) -> float:
+    """Area of the piece of the iso-surface f = iso inside one tetrahedron
+    with vertex positions ``p`` and values ``f`` (f linear in the
+    tetrahedron).  A vertex is above when f > iso.  The surface crosses each
+    edge joining an above and a below vertex at the linear interpolant's
+    root; one vertex apart gives a triangle, two apart a quadrilateral,
+    split along the diagonal from the (below 0, above 0) edge point to the
+    (below 1, above 1) one."""
+    up = [i for i in range(4) if f[i] > iso]
+    dn = [i for i in range(4) if not f[i] > iso]
+    if not up or not dn:
+        return 0.0
+
+    def cross(a, b):
+        t = (iso - f[a]) / (f[b] - f[a])
+        return tuple(p[a][d] + t * (p[b][d] - p[a][d]) for d in range(3))
+
+    if len(up) == 1 or len(dn) == 1:
+        one, rest = (up[0], dn) if len(up) == 1 else (dn[0], up)
+        return _tri_area(*[cross(one, r) for r in rest])
+    a, b = dn
+    c, d = up
+    q0, q1, q2, q3 = cross(a, c), cross(a, d), cross(b, d), cross(b, c)
+    return _tri_area(q0, q1, q2) + _tri_area(q0, q2, q3)
+
+
+def iso_area(v: np.ndarray, coords, iso: float) -> float:
+    """Area of the iso-surface ``v = iso`` of the 3D grid function ``v`` with
+    axis coordinates ``coords`` (None: the node index), the analysis of the
+    use case in Section 6.2.2.  The paper names the quantity, not the
+    method; here every cell is split into the 6 tetrahedra around its main
+    diagonal and ``v`` is taken linear on each (marching tetrahedra), which
+    reproduces planar iso-surfaces exactly.  Cells are visited in C order;
+    the sum is in FP64."""
+    v = np.asarray(v, dtype=np.float64)
+    if v.ndim != 3:
+        raise ValueError("iso-surface area is defined for 3D grids")
+    xs = [np.arange(n, dtype=np.float64) if (coords is None or coords[d] is None)
+          else np.asarray(coords[d], dtype=np.float64) for d, n in enumerate(v.shape)]
+    total = 0.0
+    n0, n1, n2 = v.shape
+    for i in range(n0 - 1):
+        for j in range(n1 - 1):
+            for k in range(n2 - 1):
+                cf = [float(v[i + (c >> 2 & 1), j + (c >> 1 & 1), k + (c & 1)]) for c in range(8)]
+                if min(cf) > iso or max(cf) <= iso:
+                    continue
+                cp = [(xs[0][i + (c >> 2 & 1)], xs[1][j + (c >> 1 & 1)], xs[2][k + (c & 1)])
+                      for c in range(8)]
+                for t in TETS:
+                    total += _tet_area([cp[c] for c in t], [cf[c] for c in t], iso)
+    return total

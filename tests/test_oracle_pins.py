@@ -577,3 +577,50 @@ def test_adaptive_stop_level_decisions():
     # A 2D grid has no penalty factors in the paper.
     with pytest.raises(ValueError):
         O.prediction_errors(np.zeros((9, 9)), O.Hierarchy((9, 9)), 2, 1.0)
+
+
+# --------------------------------- progressive recomposition, iso area ---
+
+@pytest.mark.parametrize("dims,kind", [((17, 9, 12), "u"), ((10, 17, 9), "g")])
+def test_recompose_partial_is_the_projection_chain(dims, kind):
+    # Q_k u directly: the L2 projection applied level by level from the
+    # finest grid (no decomposition involved).
+    coords = None if kind == "u" else [F.geometric_coords(n, 1.04) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    u = _rng(11).standard_normal(dims)
+    for stop in (0, 1):
+        umc = O.decompose(u, H, stop)
+        v = u.copy()
+        for k in range(H.L, stop - 1, -1):
+            got = O.recompose_partial(umc, H, stop, k)
+            np.testing.assert_allclose(got, v, atol=1e-12 * np.abs(u).max())
+            if k > stop:
+                v = O.project(v, H, k)
+
+
+def test_iso_area_planes_exact():
+    # Marching tetrahedra reproduce planar iso-surfaces exactly.
+    n = (8, 6, 5)
+    i, j, k = np.meshgrid(*[np.arange(m, dtype=np.float64) for m in n], indexing="ij")
+    assert O.iso_area(i, None, 3.5) == pytest.approx(5.0 * 4.0, rel=1e-13)
+    n = (8, 8, 5)
+    i, j, k = np.meshgrid(*[np.arange(m, dtype=np.float64) for m in n], indexing="ij")
+    # i + j = 4.3 cuts the (i, j) square along a segment of length 4.3 sqrt(2).
+    assert O.iso_area(i + j, None, 4.3) == pytest.approx(4.3 * np.sqrt(2.0) * 4.0, rel=1e-13)
+    # Nonuniform coordinates: the plane x = 0.37 spans the (y, z) extent.
+    dims = (9, 7, 6)
+    coords = [F.geometric_coords(n, 1.1) for n in dims]
+    X, Y, Z = np.meshgrid(*coords, indexing="ij")
+    ext = (coords[1][-1] - coords[1][0]) * (coords[2][-1] - coords[2][0])
+    assert O.iso_area(X, coords, 0.37) == pytest.approx(ext, rel=1e-12)
+
+
+def test_iso_area_sphere_converges():
+    # r^2 = R^2 on grids of growing resolution approaches 4 pi R^2.
+    errs = []
+    for n, R in ((17, 6.0), (33, 12.0)):
+        c = (n - 1) / 2
+        i, j, k = np.meshgrid(*[np.arange(n, dtype=np.float64)] * 3, indexing="ij")
+        r2 = (i - c) ** 2 + (j - c) ** 2 + (k - c) ** 2
+        errs.append(abs(O.iso_area(r2, None, R * R) / (4 * np.pi * R * R) - 1))
+    assert errs[0] < 0.02 and errs[1] < errs[0]
