@@ -118,6 +118,39 @@ int mgard_decompose_adaptive(int ndim, const int64_t* dims, const double* const*
                              double tau_linf, void* data, void* workspace, size_t ws_bytes,
                              int* stop_out, double* sums_out, void* stream);
 
+/* The level-`level` grid of the hierarchy of `dims` (0 <= level <= L): its
+ * shape (ndim values into shape_out) and, when coords_out is not NULL, the
+ * coordinates of its nodes, axis after axis (sum of the shape entries
+ * doubles; uniform axes give the finest node indices).  Host only.
+ * MGARD_ERR_LEVEL for a level outside [0, L]. */
+int mgard_level_grid(int ndim, const int64_t* dims, const double* const* coords, int level,
+                     int64_t* shape_out, double* coords_out);
+
+/* Progressive recomposition (Section 1, data refactoring): from `data`, the
+ * decomposition of a field with `stop_level` (finest layout, device,
+ * read-only), write Q_k u, the field's projection onto the level-k grid
+ * (k = level, stop_level <= k <= L), to `out` (device, the compact level-k
+ * grid of mgard_level_grid's shape, C order).  Only the components of
+ * levels stop_level .. k are read and recomposed, so the cost is that of the
+ * level-k grid.  The workspace needs mgard_workspace_size of the level-k
+ * shape (at most that of the field); `out` must not overlap `data`.
+ * MGARD_ERR_LEVEL for k outside [stop_level, L]; other errors as
+ * mgard_recompose. */
+int mgard_recompose_partial(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                            int stop_level, int level, const void* data, void* out, void* workspace,
+                            size_t ws_bytes, void* stream);
+
+/* Area of the iso-surface data = iso of a 3D grid function (Section 6.2.2's
+ * analysis on reduced representations), with the grid's coordinates (NULL:
+ * node indices): every cell is split into the 6 tetrahedra around its main
+ * diagonal and the function taken linear on each (marching tetrahedra; a
+ * vertex counts as above when its value exceeds iso), planar surfaces are
+ * measured exactly.  Geometry in the data's precision, sum in FP64, fixed
+ * summation order.  Waits for `stream`; *area_out receives the area.
+ * MGARD_ERR_SHAPE unless ndim = 3; MGARD_ERR_ARG for a non-finite iso. */
+int mgard_iso_area(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                   const void* data, double iso, double* area_out, void* stream);
+
 /* Multilevel recomposition, in place: the exact inverse of mgard_decompose
  * with the same dims, coords, dtype and stop_level (Section 2, recomposition
  * steps 1-5).  Same workspace rule. */

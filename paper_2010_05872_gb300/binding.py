@@ -39,6 +39,12 @@ _SIGNATURES = {
                                        _VP, _VP, ctypes.c_size_t, _VP]),
     "mgard_recompose": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                        _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_level_grid": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, _I64P,
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "mgard_recompose_partial": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_iso_area": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, _VP, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_double), _VP]),
     "mgard_decompose_adaptive": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
                                                 ctypes.c_double, _VP, _VP, ctypes.c_size_t,
                                                 ctypes.POINTER(ctypes.c_int),
@@ -473,6 +479,51 @@ def decompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
                          ws.numel(), _stream(stream))
     _check(rc, "mgard_decompose")
     return x
+
+
+def level_grid(dims, coords, level: int):
+    """(shape, coords) of the level-`level` grid of the hierarchy of `dims`:
+    the shape tuple and a list of per-axis coordinate arrays."""
+    s = _Shape(dims, coords)
+    shape = (ctypes.c_int64 * s.ndim)()
+    rc = lib().mgard_level_grid(s.ndim, s.dims, s.coords, int(level), shape, None)
+    _check(rc, "mgard_level_grid")
+    out = (ctypes.c_double * int(sum(shape[:])))()
+    rc = lib().mgard_level_grid(s.ndim, s.dims, s.coords, int(level), shape, out)
+    _check(rc, "mgard_level_grid")
+    vals, o, axes = np.array(out[:], dtype=np.float64), 0, []
+    for n in shape[:]:
+        axes.append(vals[o:o + n].copy())
+        o += n
+    return tuple(int(n) for n in shape[:]), axes
+
+
+def recompose_partial(x, level: int, coords=None, stop_level: int = 0, ws=None, stream=None):
+    """Q_k u on the level-k grid (a new CUDA tensor) from the decomposed CUDA
+    tensor x (left unchanged)."""
+    _cuda_tensor(x, "x")
+    torch = _torch()
+    shape, _ = level_grid(x.shape, coords, level)
+    out = torch.empty(shape, dtype=x.dtype, device=x.device)
+    if ws is None:
+        ws = workspace(shape, x.dtype, x.device)
+    s = _Shape(x.shape, coords)
+    rc = lib().mgard_recompose_partial(s.ndim, s.dims, s.coords, dtype_code(x), int(stop_level),
+                                       int(level), x.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                       ws.numel(), _stream(stream))
+    _check(rc, "mgard_recompose_partial")
+    return out
+
+
+def iso_area(x, iso: float, coords=None, stream=None) -> float:
+    """Iso-surface area of the 3D CUDA tensor x at `iso` (marching tetrahedra)."""
+    _cuda_tensor(x, "x")
+    s = _Shape(x.shape, coords)
+    a = ctypes.c_double()
+    rc = lib().mgard_iso_area(s.ndim, s.dims, s.coords, dtype_code(x), x.data_ptr(), float(iso),
+                              ctypes.byref(a), _stream(stream))
+    _check(rc, "mgard_iso_area")
+    return a.value
 
 
 def decompose_adaptive(x, tau_linf: float, coords=None, ws=None, stream=None):

@@ -74,6 +74,11 @@ int upload(DevPlan& p) {
   size_t lev_off[3];
   for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
   const size_t lev01_off = reserve(h.lev01.size());
+  std::vector<std::array<size_t, 3>> pos_off(h.L + 1);
+  for (int l = 0; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) pos_off[l][a] = reserve(sizeof(int32_t) * h.idx[l][a].size());
+  size_t x_off[3];
+  for (int a = 0; a < 3; ++a) x_off[a] = reserve(sizeof(double) * h.x[a].size());
   std::vector<char> stage(total, 0);
   auto put = [&](size_t off, const std::vector<double>& v) {
     T* dst = reinterpret_cast<T*>(stage.data() + off);
@@ -90,6 +95,13 @@ int upload(DevPlan& p) {
     }
   for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
   std::memcpy(stage.data() + lev01_off, h.lev01.data(), h.lev01.size());
+  for (int l = 0; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      int32_t* dst = reinterpret_cast<int32_t*>(stage.data() + pos_off[l][a]);
+      for (size_t j = 0; j < h.idx[l][a].size(); ++j) dst[j] = static_cast<int32_t>(h.idx[l][a][j]);
+    }
+  for (int a = 0; a < 3; ++a)
+    std::memcpy(stage.data() + x_off[a], h.x[a].data(), sizeof(double) * h.x[a].size());
   if (cudaMalloc(&p.dmem, total) != cudaSuccess) return MGARD_ERR_CUDA;
   if (cudaMemcpy(p.dmem, stage.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) return MGARD_ERR_CUDA;
   char* base = static_cast<char*>(p.dmem);
@@ -97,6 +109,10 @@ int upload(DevPlan& p) {
   else fill_levels<double>(p, offs, base, p.lvd);
   for (int a = 0; a < 3; ++a) p.lev[a] = reinterpret_cast<const uint8_t*>(base + lev_off[a]);
   p.lev01 = reinterpret_cast<const uint8_t*>(base + lev01_off);
+  p.pos.resize(h.L + 1);
+  for (int l = 0; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) p.pos[l][a] = reinterpret_cast<const int32_t*>(base + pos_off[l][a]);
+  for (int a = 0; a < 3; ++a) p.xc[a] = reinterpret_cast<const double*>(base + x_off[a]);
   return MGARD_OK;
 }
 
@@ -512,6 +528,93 @@ int mgard_decompose_adaptive(int ndim, const int64_t* dims, const double* const*
                                    sums_out);
 }
 
+int mgard_level_grid(int ndim, const int64_t* dims, const double* const* coords, int level,
+                     int64_t* shape_out, double* coords_out) {
+  if (shape_out == nullptr) return MGARD_ERR_ARG;
+  HostPlan h;
+  const int rc = build_host_plan(ndim, dims, coords, h);
+  if (rc != MGARD_OK) return rc;
+  if (level < 0 || level > h.L) return MGARD_ERR_LEVEL;
+  const int pad = 3 - ndim;
+  size_t o = 0;
+  for (int d = 0; d < ndim; ++d) {
+    const auto& ix = h.idx[level][pad + d];
+    shape_out[d] = static_cast<int64_t>(ix.size());
+    if (coords_out)
+      for (int64_t j : ix) coords_out[o++] = h.x[pad + d][j];
+  }
+  return MGARD_OK;
+}
+
+int mgard_recompose_partial(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                            int stop_level, int level, const void* data, void* out, void* workspace,
+                            size_t ws_bytes, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  if (stop_level < 0 || stop_level > p->h.L || level < stop_level || level > p->h.L)
+    return MGARD_ERR_LEVEL;
+  const size_t es = elem_size(dtype);
+  if (data == nullptr || out == nullptr || reinterpret_cast<uintptr_t>(data) % es ||
+      reinterpret_cast<uintptr_t>(out) % es)
+    return MGARD_ERR_ARG;
+  // The level-k grid is a hierarchy of its own (the coarser levels of this
+  // one), with the coordinates of its nodes.
+  const int pad = 3 - ndim;
+  int64_t dk[3];
+  std::vector<std::vector<double>> ck(ndim);
+  std::vector<const double*> cptr(ndim);
+  for (int d = 0; d < ndim; ++d) {
+    const auto& ix = p->h.idx[level][pad + d];
+    dk[d] = static_cast<int64_t>(ix.size());
+    for (int64_t j : ix) ck[d].push_back(p->h.x[pad + d][j]);
+    cptr[d] = ck[d].data();
+  }
+  DevPlan* pk = nullptr;
+  rc = get_plan(ndim, dk, cptr.data(), dtype, &pk);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*pk, stop_level, out, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int32_t* pos[3] = {p->pos[level][0], p->pos[level][1], p->pos[level][2]};
+  const int64_t* shape3 = p->h.shape[level].data();
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_gather_level<double>(static_cast<const double*>(data), p->h.dims3.data(), pos,
+                                        shape3, static_cast<double*>(out), s));
+  else
+    MGB_TRY(launch_gather_level<float>(static_cast<const float*>(data), p->h.dims3.data(), pos,
+                                       shape3, static_cast<float*>(out), s));
+  if (stop_level == level) return MGARD_OK;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  return run_transform(false, *pk, stop_level, out, static_cast<char*>(workspace), c->flags + 1, s);
+}
+
+int mgard_iso_area(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                   const void* data, double iso, double* area_out, void* stream) {
+  if (area_out == nullptr || !std::isfinite(iso)) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  if (p->h.ndim != 3) return MGARD_ERR_SHAPE;
+  if (data == nullptr || reinterpret_cast<uintptr_t>(data) % elem_size(dtype)) return MGARD_ERR_ARG;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double* x[3] = {p->xc[0], p->xc[1], p->xc[2]};
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_iso_area<double>(static_cast<const double*>(data), p->h.dims3.data(), x, iso,
+                                    c->partial, c->result, s));
+  else
+    MGB_TRY(launch_iso_area<float>(static_cast<const float*>(data), p->h.dims3.data(), x, iso,
+                                   c->partial, c->result, s));
+  MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  *area_out = c->h_result[0];
+  return MGARD_OK;
+}
+
 int mgard_decompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
                          int stop_level, const void* host_in, void* host_out, void* dev_data,
                          void* workspace, size_t ws_bytes, void* stream) {
@@ -742,6 +845,11 @@ int noalloc_tables(DevPlan& p, char* dst, size_t cap, size_t* used, cudaStream_t
   size_t lev_off[3];
   for (int a = 0; a < 3; ++a) lev_off[a] = reserve(h.lev[a].size());
   const size_t lev01_off = reserve(h.lev01.size());
+  std::vector<std::array<size_t, 3>> pos_off(h.L + 1);
+  for (int l = 0; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) pos_off[l][a] = reserve(sizeof(int32_t) * h.idx[l][a].size());
+  size_t x_off[3];
+  for (int a = 0; a < 3; ++a) x_off[a] = reserve(sizeof(double) * h.x[a].size());
   total = align_up(total, kAlign);
   if (total > cap) return MGARD_ERR_WORKSPACE;
   std::vector<char> stage(total, 0);
@@ -760,6 +868,13 @@ int noalloc_tables(DevPlan& p, char* dst, size_t cap, size_t* used, cudaStream_t
     }
   for (int a = 0; a < 3; ++a) std::memcpy(stage.data() + lev_off[a], h.lev[a].data(), h.lev[a].size());
   std::memcpy(stage.data() + lev01_off, h.lev01.data(), h.lev01.size());
+  for (int l = 0; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) {
+      int32_t* dst = reinterpret_cast<int32_t*>(stage.data() + pos_off[l][a]);
+      for (size_t j = 0; j < h.idx[l][a].size(); ++j) dst[j] = static_cast<int32_t>(h.idx[l][a][j]);
+    }
+  for (int a = 0; a < 3; ++a)
+    std::memcpy(stage.data() + x_off[a], h.x[a].data(), sizeof(double) * h.x[a].size());
   // Pageable source: the copy has consumed `stage` when the call returns.
   if (cudaMemcpyAsync(dst, stage.data(), total, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return MGARD_ERR_CUDA;

@@ -2,6 +2,7 @@
 // points of api.cu and the batched form of batch.cu.
 #pragma once
 
+#include <array>
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
@@ -25,6 +26,8 @@ struct DevPlan {
   std::vector<LevelK<double>> lvd;
   const uint8_t* lev[3] = {nullptr, nullptr, nullptr};
   const uint8_t* lev01 = nullptr;   // per-row level (quantizer)
+  std::vector<std::array<const int32_t*, 3>> pos;  // [L+1] level-l node positions per axis
+  std::array<const double*, 3> xc{};               // finest coordinates per axis
   std::vector<size_t> offB, offF;   // workspace offsets of the level-l grids / load vectors
   size_t ws_bytes = 0;
   ~DevPlan() {

@@ -114,6 +114,18 @@ constexpr int kMinmaxBlocks = 1216;  // 8 x 152 SMs
 // level-l grid `v` (the n of lv's axes; 3D), with the level tolerance tau0,
 // written to result[0..1] (device); `partial` holds 2 x kMinmaxBlocks
 // doubles of scratch.
+// Copy the nodes of a level out of an array in the finest layout (dims3)
+// into a compact grid of shape3, with per-axis node positions pos[a].
+template <typename T>
+cudaError_t launch_gather_level(const T* src, const int64_t* dims3, const int32_t* const* pos,
+                                const int64_t* shape3, T* dst, cudaStream_t s);
+// Iso-surface area of the 3D grid function v (dims3, axis coordinates
+// x[a] on the device) at `iso`, into result[0] (device); `partial` holds
+// kMinmaxBlocks doubles of scratch.
+template <typename T>
+cudaError_t launch_iso_area(const T* v, const int64_t* dims3, const double* const* x, double iso,
+                            double* partial, double* result, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_prediction_errors(const LevelK<T>& lv, const T* v, double tau0, double* partial,
                                      double* result, int level, cudaStream_t s);

@@ -297,6 +297,8 @@ int build_host_plan(int ndim, const int64_t* dims, const double* const* coords, 
   for (int64_t j0 = 0; j0 < p.dims3[0]; ++j0)
     for (int64_t j1 = 0; j1 < p.dims3[1]; ++j1)
       p.lev01[j0 * p.dims3[1] + j1] = std::max(p.lev[0][j0], p.lev[1][j1]);
+  for (int a = 0; a < 3; ++a) p.x[a] = a < pad ? std::vector<double>{0.0} : x[a];
+  p.idx = std::move(idx);
   return MGARD_OK;
 }
 

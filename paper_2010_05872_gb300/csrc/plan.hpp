@@ -49,6 +49,8 @@ struct HostPlan {
   std::vector<uint8_t> lev01;                 // per finest row (j0, j1): max(lev[0][j0], lev[1][j1])
   std::vector<double> knorm;                  // [L+1] bound on |K_l|_inf (entry 0 unused)
   std::vector<double> coords_key;             // coordinates as given (for the plan cache)
+  std::array<std::vector<double>, 3> x;       // finest coordinates per axis (padded: {0})
+  std::vector<std::array<std::vector<int64_t>, 3>> idx;  // [L+1] level-l node positions (finest indices)
   int64_t count() const { return dims3[0] * dims3[1] * dims3[2]; }
 };
 

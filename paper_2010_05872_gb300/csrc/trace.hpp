@@ -22,6 +22,8 @@ enum KernelKind : int {
   kKMinmax,
   kKSmallLevels,
   kKPredErr,
+  kKIsoArea,
+  kKGather,
   kKNumKinds
 };
 

@@ -97,3 +97,15 @@ def test_argument_errors(lib):
     assert B.mgard_decompose((2, 9), None, B.F32, 0, 0, 0, 0, 0) == -2
     assert B.mgard_recompose((9, 9), None, 5, 0, 0, 0, 0, 0) == -1
     assert lib.mgard_error_string(-5).decode().startswith("workspace")
+
+
+@pytest.mark.parametrize("dims,kind", [((33, 20, 17), "u"), ((10, 17, 9), "g"), ((1000,), "g"),
+                                       ((70, 45), "u")])
+def test_level_grid_matches_oracle(lib, dims, kind):
+    coords = None if kind == "u" else [F.geometric_coords(n, 1.03) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    for level in range(H.L + 1):
+        shape, axes = B.level_grid(dims, coords, level)
+        assert shape == H.levels[level]
+        for d in range(len(dims)):
+            np.testing.assert_array_equal(axes[d], H.coords[level][d])
