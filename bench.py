@@ -489,6 +489,36 @@ def run_gpu(args, rank, world, local_rank):
     })
     x.copy_(u)
 
+    # Progressive recomposition and analysis on reduced representations
+    # (the iso-surface use case): Q_k u for k = L .. L-3 from the decomposed
+    # field, and the iso-surface area at the field's mean on each.
+    B.decompose(x, None, 0, ws)
+    torch.cuda.synchronize()
+    iso = float(u.double().mean().item())
+    n_lv = B.mgard_num_levels(DIMS)
+    progressive = {"iso": "mean", "levels": {}}
+    area_full = None
+    for k in range(n_lv, n_lv - 4, -1):
+        _, axes = B.level_grid(DIMS, None, k)
+        tr, ti = [], []
+        for i in range(3):
+            ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            ea.record(stream)
+            qk = B.recompose_partial(x, k, None, 0, ws)
+            eb.record(stream)
+            area = B.iso_area(qk, iso, axes)
+            ec.record(stream)
+            torch.cuda.synchronize()
+            tr.append(ea.elapsed_time(eb))
+            ti.append(eb.elapsed_time(ec))
+            del qk
+        if area_full is None:
+            area_full = area
+        progressive["levels"][str(k)] = {
+            "recompose_ms": statistics.median(tr), "iso_area_ms": statistics.median(ti),
+            "area": area, "area_rel_diff_vs_full": area / area_full - 1.0}
+    x.copy_(u)
+
     # End to end through the host-buffer entry points.
     ws = B.workspace(DIMS, torch.float32, dev)
     labels = torch.empty(DIMS, dtype=torch.int64, device=dev)
@@ -549,6 +579,7 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks.summary(t0, t1),
         "fp64": fp64,
         "adaptive": adaptive,
+        "progressive": progressive,
         "linf_over_tau": linf,
         "top_kernels": kernels,
         "kinds_ms_per_step": {k: round(v, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1])},

@@ -531,17 +531,26 @@ int mgard_decompose_adaptive(int ndim, const int64_t* dims, const double* const*
 int mgard_level_grid(int ndim, const int64_t* dims, const double* const* coords, int level,
                      int64_t* shape_out, double* coords_out) {
   if (shape_out == nullptr) return MGARD_ERR_ARG;
-  HostPlan h;
-  const int rc = build_host_plan(ndim, dims, coords, h);
+  int L = 0;
+  const int rc = count_levels(ndim, dims, &L);
   if (rc != MGARD_OK) return rc;
-  if (level < 0 || level > h.L) return MGARD_ERR_LEVEL;
-  const int pad = 3 - ndim;
+  if (level < 0 || level > L) return MGARD_ERR_LEVEL;
   size_t o = 0;
   for (int d = 0; d < ndim; ++d) {
-    const auto& ix = h.idx[level][pad + d];
+    // Level-l positions from the finest: keep cpos(k, n) for k <= n / 2.
+    std::vector<int64_t> ix(static_cast<size_t>(dims[d]));
+    for (int64_t j = 0; j < dims[d]; ++j) ix[j] = j;
+    for (int l = L; l > level; --l) {
+      const int64_t n = static_cast<int64_t>(ix.size());
+      std::vector<int64_t> c;
+      for (int64_t k = 0; k < n / 2 + 1; ++k) c.push_back(ix[std::min(2 * k, n - 1)]);
+      ix.swap(c);
+    }
     shape_out[d] = static_cast<int64_t>(ix.size());
-    if (coords_out)
-      for (int64_t j : ix) coords_out[o++] = h.x[pad + d][j];
+    if (coords_out) {
+      const double* c = coords != nullptr ? coords[d] : nullptr;
+      for (int64_t j : ix) coords_out[o++] = c ? c[j] : static_cast<double>(j);
+    }
   }
   return MGARD_OK;
 }
