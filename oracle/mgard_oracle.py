@@ -40,6 +40,8 @@ explicit finite-element operators assembled from the grid coordinates:
 * Progressive recomposition (Section 1, data refactoring): ``Q_k u`` on the
   level-k grid from the decomposed array; and the iso-surface area of a 3D
   grid function (Section 6.2.2's analysis) by marching tetrahedra.
+* The labels' lossless stage (Algorithm 1 line 23; this build's coder is a
+  chunked zigzag bit packing, a reading) and PSNR (Section 6, "Quality").
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
 non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
@@ -52,7 +54,9 @@ interpolation stencils of Eq. (multilinear_interp), dense Kronecker brute
 force, invariants and bounds; the adaptive stopping level by hand-derived
 sums in tests/golden/prediction_errors.txt and exactness properties of the
 two predictors; partial recomposition by the projection chain; the iso
-area by planar surfaces, exact, and a sphere's convergence).
+area by planar surfaces, exact, and a sphere's convergence; the packed
+label stream by hand-derived bytes in tests/golden/packed_labels.txt and
+round trips; PSNR by a closed form).
 ``linf_constant`` is a reading (the paper
 gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
 worst-case error amplification, and its exact value is "parity unpinned" with
@@ -74,6 +78,7 @@ __all__ = [
     "quantize", "dequantize", "value_range",
     "LORENZO_PENALTY", "INTERP_PENALTY", "sampled_blocks", "prediction_errors",
     "adaptive_stop_level", "recompose_partial", "iso_area",
+    "PACK_CHUNK", "pack_labels", "unpack_labels", "psnr",
 ]
 
 
@@ -611,3 +616,72 @@ def iso_area(v: np.ndarray, coords, iso: float) -> float:
                 for t in TETS:
                     total += _tet_area([cp[c] for c in t], [cf[c] for c in t], iso)
     return total
+
+
+# --------------------------------------------------------------------------
+# Lossless stage for the labels (Section 4.1, Algorithm 1 line 23) and PSNR
+# (Section 6, "Quality")
+# --------------------------------------------------------------------------
+
+PACK_CHUNK = 1024
+
+
+def _zigzag(k: int) -> int:
+    """Signed to unsigned, small magnitudes to small codes: 0, -1, 1, -2, ..
+    map to 0, 1, 2, 3, .."""
+    return (k << 1) if k >= 0 else ((-k) << 1) - 1
+
+
+def pack_labels(labels) -> bytes:
+    """The labels' lossless stream.  The paper passes the labels to a
+    general-purpose lossless coder; this build's coder (a reading) packs
+    them in chunks of 1024: each label is zigzag-coded and stored in the
+    chunk's width w, the bit length of the chunk's largest code (0 when all
+    are 0), least significant bit first, in little-endian 64-bit words.
+    Layout: uint64 N | one width byte per chunk | zero padding to 8 bytes |
+    for each chunk, ceil(n_c w / 64) words."""
+    k = [int(v) for v in np.asarray(labels, dtype=np.int64).ravel()]
+    n = len(k)
+    chunks = [k[i:i + PACK_CHUNK] for i in range(0, n, PACK_CHUNK)]
+    widths = [max((_zigzag(v) for v in c), default=0).bit_length() for c in chunks]
+    out = bytearray(n.to_bytes(8, "little"))
+    out += bytes(widths)
+    out += bytes((-len(out)) % 8)
+    for c, w in zip(chunks, widths):
+        bits = 0
+        for i, v in enumerate(c):
+            bits |= _zigzag(v) << (i * w)
+        nwords = (len(c) * w + 63) // 64
+        out += bits.to_bytes(8 * nwords, "little")
+    return bytes(out)
+
+
+def unpack_labels(buf: bytes) -> np.ndarray:
+    """Inverse of :func:`pack_labels`."""
+    buf = bytes(buf)
+    n = int.from_bytes(buf[:8], "little")
+    nchunks = (n + PACK_CHUNK - 1) // PACK_CHUNK
+    widths = list(buf[8:8 + nchunks])
+    off = 8 + nchunks
+    off += (-off) % 8
+    out = []
+    for c, w in enumerate(widths):
+        nc = min(PACK_CHUNK, n - c * PACK_CHUNK)
+        nwords = (nc * w + 63) // 64
+        bits = int.from_bytes(buf[off:off + 8 * nwords], "little")
+        off += 8 * nwords
+        mask = (1 << w) - 1
+        for i in range(nc):
+            z = (bits >> (i * w)) & mask
+            out.append((z >> 1) if z % 2 == 0 else -((z + 1) >> 1))
+    return np.asarray(out, dtype=np.int64)
+
+
+def psnr(u: np.ndarray, v: np.ndarray) -> float:
+    """PSNR of a reconstruction ``v`` of ``u`` (Section 6, "Quality"): the
+    printed formula's range term is garbled (max u - min v); the value range
+    of the original, max u - min u, is used, in FP64."""
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    mse = float(np.mean((u - v) ** 2))
+    return 20.0 * math.log10(float(u.max() - u.min())) - 10.0 * math.log10(mse)

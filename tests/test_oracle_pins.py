@@ -624,3 +624,51 @@ def test_iso_area_sphere_converges():
         r2 = (i - c) ** 2 + (j - c) ** 2 + (k - c) ** 2
         errs.append(abs(O.iso_area(r2, None, R * R) / (4 * np.pi * R * R) - 1))
     assert errs[0] < 0.02 and errs[1] < errs[0]
+
+
+# ------------------------------------------------ lossless stage, PSNR ---
+
+def _packed_cases():
+    out = []
+    with open(os.path.join(GOLDEN, "packed_labels.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            labels_s, hex_s = [p.strip() for p in line.split("|")]
+            out.append(([int(v) for v in labels_s.split(",")], bytes.fromhex(hex_s.replace(" ", ""))))
+    return out
+
+
+@pytest.mark.parametrize("case", _packed_cases())
+def test_pack_labels_hand_streams(case):
+    labels, stream = case
+    assert O.pack_labels(labels) == stream
+    assert list(O.unpack_labels(stream)) == labels
+
+
+def test_pack_labels_round_trip_and_size():
+    rng = _rng(9)
+    for n in (0, 1, 1023, 1024, 1025, 5000):
+        x = rng.integers(-40, 40, n)
+        if n > 10:
+            x[3] = 2 ** 62
+            x[n - 1] = -2 ** 63
+            x[n // 2] = 2 ** 63 - 1
+        buf = O.pack_labels(x)
+        assert np.array_equal(O.unpack_labels(buf), x)
+        # Size: header, widths padded to 8 bytes, then ceil(n_c w / 64) words.
+        nch = (n + 1023) // 1024
+        size = 8 + nch + (-(8 + nch)) % 8
+        for c in range(nch):
+            z = [(2 * int(v)) if v >= 0 else (-2 * int(v) - 1) for v in x[c * 1024:(c + 1) * 1024]]
+            w = max(z).bit_length()
+            size += 8 * ((len(z) * w + 63) // 64)
+        assert len(buf) == size
+
+
+def test_psnr_closed_form():
+    u = np.array([0.0, 1.0])
+    v = np.array([0.0, 1.1])
+    # range 1, mean squared error 0.005
+    assert O.psnr(u, v) == pytest.approx(-10 * np.log10(0.005), rel=1e-14)
