@@ -217,6 +217,46 @@ int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* co
                           void* host_field, void* dev_data, int64_t* dev_labels, void* workspace,
                           size_t ws_bytes, void* stream);
 
+/* The labels' lossless stage (Section 4.1: labels go to a lossless coder;
+ * Algorithm 1 line 23).  This library's coder packs the labels in chunks
+ * of 1024: zigzag codes (0, -1, 1, -2, .. -> 0, 1, 2, 3, ..) in the chunk's
+ * width w (bit length of its largest code), least significant bit first.
+ * Stream (little-endian): uint64 count | one width byte per chunk | zero
+ * padding to 8 bytes | per chunk ceil(n_c w / 64) 64-bit words.
+ * mgard_pack_bound: the largest stream of `count` labels (host only).
+ * mgard_pack_labels: encode `count` device labels into the device buffer
+ * `out` (8-byte aligned, capacity >= mgard_pack_bound, else
+ * MGARD_ERR_WORKSPACE); *bytes_out receives the stream size; waits for
+ * `stream`.  mgard_unpack_labels: decode a device stream of `bytes` bytes
+ * into `count` device labels; the header is read back and checked (count,
+ * widths <= 64, size), MGARD_ERR_ARG if it does not match; waits for the
+ * header only. */
+int mgard_pack_bound(int64_t count, size_t* bytes);
+int mgard_pack_labels(int64_t count, const int64_t* labels, void* out, size_t capacity,
+                      size_t* bytes_out, void* stream);
+int mgard_unpack_labels(const void* in, size_t bytes, int64_t count, int64_t* labels, void* stream);
+
+/* mgard_compress_host / mgard_decompress_host with the packed label stream
+ * crossing between host and device instead of int64 labels: compress
+ * quantizes into dev_labels, packs into dev_stream (8-byte aligned, at
+ * least mgard_pack_bound(count) bytes) and copies the stream (its size in
+ * *stream_bytes, at most host_capacity, else MGARD_ERR_WORKSPACE) to
+ * host_stream; decompress checks the host stream's header, copies it to
+ * dev_stream, unpacks into dev_labels, dequantizes, recomposes and copies
+ * the field to host_field.  Both synchronise the stream before returning. */
+int mgard_compress_host_packed(int ndim, const int64_t* dims, const double* const* coords,
+                               int dtype, int stop_level, double rel_bound, const void* host_field,
+                               void* host_stream, size_t host_capacity, size_t* stream_bytes,
+                               double* tau_out, void* dev_data, int64_t* dev_labels,
+                               void* dev_stream, size_t dev_capacity, void* workspace,
+                               size_t ws_bytes, void* stream);
+int mgard_decompress_host_packed(int ndim, const int64_t* dims, const double* const* coords,
+                                 int dtype, int stop_level, double tau_linf,
+                                 const void* host_stream, size_t stream_bytes, void* host_field,
+                                 void* dev_data, int64_t* dev_labels, void* dev_stream,
+                                 size_t dev_capacity, void* workspace, size_t ws_bytes,
+                                 void* stream);
+
 /* Free every cached plan (device tables included) of the current device. */
 int mgard_release_plans(void);
 

@@ -39,6 +39,19 @@ _SIGNATURES = {
                                        _VP, _VP, ctypes.c_size_t, _VP]),
     "mgard_recompose": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                        _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_pack_bound": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "mgard_pack_labels": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_size_t,
+                                         ctypes.POINTER(ctypes.c_size_t), _VP]),
+    "mgard_unpack_labels": (ctypes.c_int, [_VP, ctypes.c_size_t, ctypes.c_int64, _VP, _VP]),
+    "mgard_compress_host_packed": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_double, _VP, _VP, ctypes.c_size_t,
+                                                  ctypes.POINTER(ctypes.c_size_t),
+                                                  ctypes.POINTER(ctypes.c_double), _VP, _VP, _VP,
+                                                  ctypes.c_size_t, _VP, ctypes.c_size_t, _VP]),
+    "mgard_decompress_host_packed": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_double, _VP,
+                                                    ctypes.c_size_t, _VP, _VP, _VP, _VP,
+                                                    ctypes.c_size_t, _VP, ctypes.c_size_t, _VP]),
     "mgard_level_grid": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, _I64P,
                                         ctypes.POINTER(ctypes.c_double)]),
     "mgard_recompose_partial": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
@@ -390,6 +403,32 @@ def mgard_decompress_host(dims, coords, dtype, stop_level, tau, host_labels_ptr,
                                        dev_labels_ptr, ws_ptr, ws_bytes, stream)
 
 
+def mgard_compress_host_packed(dims, coords, dtype, stop_level, rel_bound, host_field_ptr,
+                               host_stream_ptr, host_capacity, dev_data_ptr, dev_labels_ptr,
+                               dev_stream_ptr, dev_capacity, ws_ptr, ws_bytes, stream):
+    """Returns (rc, stream_bytes, tau)."""
+    s = _Shape(dims, coords)
+    tau = ctypes.c_double()
+    nb = ctypes.c_size_t()
+    rc = lib().mgard_compress_host_packed(s.ndim, s.dims, s.coords, dtype, stop_level,
+                                          float(rel_bound), host_field_ptr, host_stream_ptr,
+                                          host_capacity, ctypes.byref(nb), ctypes.byref(tau),
+                                          dev_data_ptr, dev_labels_ptr, dev_stream_ptr,
+                                          dev_capacity, ws_ptr, ws_bytes, stream)
+    return rc, nb.value, tau.value
+
+
+def mgard_decompress_host_packed(dims, coords, dtype, stop_level, tau, host_stream_ptr,
+                                 stream_bytes, host_field_ptr, dev_data_ptr, dev_labels_ptr,
+                                 dev_stream_ptr, dev_capacity, ws_ptr, ws_bytes, stream) -> int:
+    s = _Shape(dims, coords)
+    return lib().mgard_decompress_host_packed(s.ndim, s.dims, s.coords, dtype, stop_level,
+                                              float(tau), host_stream_ptr, stream_bytes,
+                                              host_field_ptr, dev_data_ptr, dev_labels_ptr,
+                                              dev_stream_ptr, dev_capacity, ws_ptr, ws_bytes,
+                                              stream)
+
+
 def mgard_release_plans() -> int:
     return lib().mgard_release_plans()
 
@@ -479,6 +518,38 @@ def decompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
                          ws.numel(), _stream(stream))
     _check(rc, "mgard_decompose")
     return x
+
+
+def pack_bound(count: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().mgard_pack_bound(int(count), ctypes.byref(b)), "mgard_pack_bound")
+    return b.value
+
+
+def pack_labels(labels, stream=None):
+    """The packed stream (a CUDA uint8 tensor of its exact size) of the int64
+    CUDA tensor `labels`."""
+    _cuda_tensor(labels, "labels")
+    torch = _torch()
+    n = labels.numel()
+    out = torch.empty(pack_bound(n), dtype=torch.uint8, device=labels.device)
+    nb = ctypes.c_size_t()
+    rc = lib().mgard_pack_labels(n, labels.data_ptr(), out.data_ptr(), out.numel(), ctypes.byref(nb),
+                                 _stream(stream))
+    _check(rc, "mgard_pack_labels")
+    return out[:nb.value]
+
+
+def unpack_labels(stream_bytes, count: int, out=None, stream=None):
+    """int64 CUDA labels from a packed CUDA uint8 stream."""
+    _cuda_tensor(stream_bytes, "stream")
+    torch = _torch()
+    if out is None:
+        out = torch.empty(int(count), dtype=torch.int64, device=stream_bytes.device)
+    rc = lib().mgard_unpack_labels(stream_bytes.data_ptr(), stream_bytes.numel(), int(count),
+                                   out.data_ptr(), _stream(stream))
+    _check(rc, "mgard_unpack_labels")
+    return out
 
 
 def level_grid(dims, coords, level: int):

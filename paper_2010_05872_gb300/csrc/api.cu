@@ -624,6 +624,175 @@ int mgard_iso_area(int ndim, const int64_t* dims, const double* const* coords, i
   return MGARD_OK;
 }
 
+int mgard_pack_bound(int64_t count, size_t* bytes) {
+  if (count < 0 || bytes == nullptr) return MGARD_ERR_ARG;
+  *bytes = pack_header_bytes(count) + 8 * static_cast<size_t>(count);
+  return MGARD_OK;
+}
+
+namespace {
+
+// Host-side check of a packed stream of `count` labels held in host memory:
+// the count, the widths and the total size.
+int check_stream(const uint8_t* h, size_t bytes, int64_t count) {
+  const size_t hdr = pack_header_bytes(count);
+  if (bytes < hdr) return MGARD_ERR_ARG;
+  uint64_t n = 0;
+  std::memcpy(&n, h, 8);
+  if (n != static_cast<uint64_t>(count)) return MGARD_ERR_ARG;
+  const int64_t nchunks = (count + kPackChunk - 1) / kPackChunk;
+  uint64_t words = 0;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int w = h[8 + c];
+    if (w > 64) return MGARD_ERR_ARG;
+    const uint64_t nc = static_cast<uint64_t>(std::min<int64_t>(kPackChunk, count - c * kPackChunk));
+    words += (nc * w + 63) / 64;
+  }
+  return hdr + 8 * words <= bytes ? MGARD_OK : MGARD_ERR_ARG;
+}
+
+// Pack on the device; *bytes_out receives the stream size (waits).
+int pack_device(int64_t count, const int64_t* labels, void* out, size_t capacity,
+                size_t* bytes_out, DevCtx* c, cudaStream_t s) {
+  size_t bound = 0;
+  mgard_pack_bound(count, &bound);
+  if (capacity < bound) return MGARD_ERR_WORKSPACE;
+  const int64_t nchunks = (count + kPackChunk - 1) / kPackChunk;
+  uint64_t* scratch = nullptr;
+  MGB_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(uint64_t) * (nchunks + 1), s));
+  cudaError_t e = launch_pack_labels(labels, count, static_cast<uint8_t*>(out), scratch + 1, scratch, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_result, scratch, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return MGARD_ERR_CUDA;
+  uint64_t words = 0;
+  std::memcpy(&words, c->h_result, sizeof words);
+  *bytes_out = pack_header_bytes(count) + 8 * static_cast<size_t>(words);
+  return MGARD_OK;
+}
+
+int unpack_device(const void* in, int64_t count, int64_t* labels, cudaStream_t s) {
+  const int64_t nchunks = (count + kPackChunk - 1) / kPackChunk;
+  if (nchunks == 0) return MGARD_OK;
+  uint64_t* scratch = nullptr;
+  MGB_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(uint64_t) * (nchunks + 1), s));
+  const cudaError_t e =
+      launch_unpack_labels(static_cast<const uint8_t*>(in), count, scratch + 1, scratch, labels, s);
+  cudaFreeAsync(scratch, s);
+  return e == cudaSuccess ? MGARD_OK : MGARD_ERR_CUDA;
+}
+
+}  // namespace
+
+int mgard_pack_labels(int64_t count, const int64_t* labels, void* out, size_t capacity,
+                      size_t* bytes_out, void* stream) {
+  if (count < 0 || bytes_out == nullptr || out == nullptr || reinterpret_cast<uintptr_t>(out) % 8)
+    return MGARD_ERR_ARG;
+  if (count > 0 && (labels == nullptr || reinterpret_cast<uintptr_t>(labels) % 8)) return MGARD_ERR_ARG;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  return pack_device(count, labels, out, capacity, bytes_out, c, static_cast<cudaStream_t>(stream));
+}
+
+int mgard_unpack_labels(const void* in, size_t bytes, int64_t count, int64_t* labels, void* stream) {
+  if (count < 0 || in == nullptr || reinterpret_cast<uintptr_t>(in) % 8) return MGARD_ERR_ARG;
+  if (count > 0 && (labels == nullptr || reinterpret_cast<uintptr_t>(labels) % 8)) return MGARD_ERR_ARG;
+  const size_t hdr = pack_header_bytes(count);
+  if (bytes < hdr) return MGARD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<uint8_t> h(hdr);
+  MGB_TRY(cudaMemcpyAsync(h.data(), in, hdr, cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  // The payload size follows from the header alone.
+  std::vector<uint8_t> probe(h);
+  const int rc = check_stream(probe.data(), bytes, count);
+  if (rc != MGARD_OK) return rc;
+  return unpack_device(in, count, labels, s);
+}
+
+int mgard_compress_host_packed(int ndim, const int64_t* dims, const double* const* coords,
+                               int dtype, int stop_level, double rel_bound, const void* host_field,
+                               void* host_stream, size_t host_capacity, size_t* stream_bytes,
+                               double* tau_out, void* dev_data, int64_t* dev_labels,
+                               void* dev_stream, size_t dev_capacity, void* workspace,
+                               size_t ws_bytes, void* stream) {
+  if (host_field == nullptr || host_stream == nullptr || stream_bytes == nullptr ||
+      tau_out == nullptr || dev_stream == nullptr || reinterpret_cast<uintptr_t>(dev_stream) % 8)
+    return MGARD_ERR_ARG;
+  if (!(rel_bound > 0.0) || !std::isfinite(rel_bound)) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*p, stop_level, dev_data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  if (dev_labels == nullptr || reinterpret_cast<uintptr_t>(dev_labels) % 8) return MGARD_ERR_ARG;
+  const int64_t count = p->h.count();
+  size_t bound = 0;
+  mgard_pack_bound(count, &bound);
+  if (dev_capacity < bound) return MGARD_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = static_cast<size_t>(count) * elem_size(dtype);
+  MGB_TRY(cudaMemcpyAsync(dev_data, host_field, bytes, cudaMemcpyHostToDevice, s));
+  double mm[2];
+  rc = mgard_value_range(count, dtype, dev_data, mm, stream);
+  if (rc != MGARD_OK) return rc;
+  double tau = rel_bound * (mm[1] - mm[0]);
+  if (!(tau > 0.0)) tau = rel_bound * (std::fabs(mm[0]) > 0.0 ? std::fabs(mm[0]) : 1.0);
+  rc = transform(true, ndim, dims, coords, dtype, stop_level, dev_data, workspace, ws_bytes, stream);
+  if (rc != MGARD_OK) return rc;
+  rc = mgard_quantize(ndim, dims, coords, dtype, stop_level, tau, dev_data, dev_labels, nullptr,
+                      stream);
+  if (rc != MGARD_OK) return rc;
+  size_t sb = 0;
+  {
+    DevCtx* c = get_ctx();
+    if (c == nullptr) return MGARD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(c->mu);
+    rc = pack_device(count, dev_labels, dev_stream, dev_capacity, &sb, c, s);
+  }
+  if (rc != MGARD_OK) return rc;
+  if (sb > host_capacity) return MGARD_ERR_WORKSPACE;
+  MGB_TRY(cudaMemcpyAsync(host_stream, dev_stream, sb, cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  *stream_bytes = sb;
+  *tau_out = tau;
+  return MGARD_OK;
+}
+
+int mgard_decompress_host_packed(int ndim, const int64_t* dims, const double* const* coords,
+                                 int dtype, int stop_level, double tau_linf,
+                                 const void* host_stream, size_t stream_bytes, void* host_field,
+                                 void* dev_data, int64_t* dev_labels, void* dev_stream,
+                                 size_t dev_capacity, void* workspace, size_t ws_bytes,
+                                 void* stream) {
+  if (host_field == nullptr || host_stream == nullptr || dev_stream == nullptr ||
+      reinterpret_cast<uintptr_t>(dev_stream) % 8 || stream_bytes > dev_capacity)
+    return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_transform_args(*p, stop_level, dev_data, workspace, ws_bytes);
+  if (rc != MGARD_OK) return rc;
+  if (dev_labels == nullptr || reinterpret_cast<uintptr_t>(dev_labels) % 8) return MGARD_ERR_ARG;
+  const int64_t count = p->h.count();
+  rc = check_stream(static_cast<const uint8_t*>(host_stream), stream_bytes, count);
+  if (rc != MGARD_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MGB_TRY(cudaMemcpyAsync(dev_stream, host_stream, stream_bytes, cudaMemcpyHostToDevice, s));
+  rc = unpack_device(dev_stream, count, dev_labels, s);
+  if (rc != MGARD_OK) return rc;
+  rc = mgard_dequantize(ndim, dims, coords, dtype, stop_level, tau_linf, dev_labels, dev_data, stream);
+  if (rc != MGARD_OK) return rc;
+  rc = transform(false, ndim, dims, coords, dtype, stop_level, dev_data, workspace, ws_bytes, stream);
+  if (rc != MGARD_OK) return rc;
+  MGB_TRY(cudaMemcpyAsync(host_field, dev_data, static_cast<size_t>(count) * elem_size(dtype),
+                          cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  return MGARD_OK;
+}
+
 int mgard_decompose_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,
                          int stop_level, const void* host_in, void* host_out, void* dev_data,
                          void* workspace, size_t ws_bytes, void* stream) {

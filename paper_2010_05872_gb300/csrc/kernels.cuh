@@ -114,6 +114,19 @@ constexpr int kMinmaxBlocks = 1216;  // 8 x 152 SMs
 // level-l grid `v` (the n of lv's axes; 3D), with the level tolerance tau0,
 // written to result[0..1] (device); `partial` holds 2 x kMinmaxBlocks
 // doubles of scratch.
+// The labels' packed stream (pack.cu): chunks of kPackChunk labels.
+constexpr int kPackChunk = 1024;
+// Bytes before the payload: the count, one width byte per chunk, padding.
+size_t pack_header_bytes(int64_t n);
+// Encode n device labels into `out` (8-byte aligned, at least
+// pack_header_bytes(n) + 8 n bytes); `words` (ceil(n / kPackChunk)
+// uint64) is scratch; *total_words (device) receives the payload words.
+cudaError_t launch_pack_labels(const int64_t* labels, int64_t n, uint8_t* out, uint64_t* words,
+                               uint64_t* total_words, cudaStream_t s);
+// Decode a validated stream of n labels.
+cudaError_t launch_unpack_labels(const uint8_t* in, int64_t n, uint64_t* words, uint64_t* total_words,
+                                 int64_t* labels, cudaStream_t s);
+
 // Copy the nodes of a level out of an array in the finest layout (dims3)
 // into a compact grid of shape3, with per-axis node positions pos[a].
 template <typename T>

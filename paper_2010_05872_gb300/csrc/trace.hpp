@@ -24,6 +24,8 @@ enum KernelKind : int {
   kKPredErr,
   kKIsoArea,
   kKGather,
+  kKPack,
+  kKUnpack,
   kKNumKinds
 };
 

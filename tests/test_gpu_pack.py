@@ -1,0 +1,93 @@
+"""GPU parity of the labels' lossless stage with the oracle's stream (bit for
+bit), round trips, argument checks, and the packed host-buffer compression
+path against the unpacked one."""
+import numpy as np
+import pytest
+
+from oracle import mgard_oracle as O
+from paper_2010_05872_gb300 import binding as B
+from paper_2010_05872_gb300 import fields as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2010_05872_gb300 import build as build_mod
+    build_mod.build()
+    B.lib()
+    return torch
+
+
+def _labels(n, seed, spread):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(-spread, spread + 1, n).astype(np.int64)
+    if n > 3000:
+        x[100:1124] = 0                      # an all-zero chunk
+        x[2000] = 2 ** 62
+        x[2500] = -2 ** 63                   # a 64-bit chunk
+        x[n - 1] = 2 ** 63 - 1
+    return x
+
+
+@pytest.mark.parametrize("n,spread", [(0, 1), (1, 5), (1023, 3), (1024, 0), (1025, 100),
+                                      (5000, 7), (70001, 1000)])
+def test_pack_matches_oracle_stream(cuda, n, spread):
+    torch = cuda
+    x = _labels(n, n, spread)
+    got = B.pack_labels(torch.from_numpy(x).cuda()).cpu().numpy().tobytes()
+    assert got == O.pack_labels(x)
+    y = B.unpack_labels(torch.from_numpy(np.frombuffer(got, dtype=np.uint8).copy()).cuda(), n)
+    assert np.array_equal(y.cpu().numpy(), x)
+
+
+def test_unpack_rejects_bad_streams(cuda):
+    torch = cuda
+    x = _labels(5000, 1, 9)
+    s = B.pack_labels(torch.from_numpy(x).cuda())
+    with pytest.raises(B.MgardError):
+        B.unpack_labels(s, 4999)                      # wrong count
+    with pytest.raises(B.MgardError):
+        B.unpack_labels(s[:-8].clone(), 5000)         # truncated payload
+    bad = s.clone()
+    bad[8] = 65                                       # width above 64
+    with pytest.raises(B.MgardError):
+        B.unpack_labels(bad, 5000)
+
+
+def test_packed_host_path_matches_unpacked(cuda):
+    """513 x 257 x 129 FP32: the packed host path returns the same field as
+    the int64 host path, its stream unpacks to the same labels, and the
+    stream is far smaller than the labels."""
+    torch = cuda
+    dims = (129, 257, 65)
+    u = F.grf_field(dims, seed=3)
+    n = u.size
+    ws = B.workspace(dims, torch.float32)
+    dev = torch.empty(dims, dtype=torch.float32, device="cuda")
+    lab = torch.empty(n, dtype=torch.int64, device="cuda")
+    cap = B.pack_bound(n)
+    dstream = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    hf = torch.from_numpy(u).pin_memory()
+    hs = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    rc, nbytes, tau = B.mgard_compress_host_packed(dims, None, B.F32, 0, 1e-3, hf.data_ptr(),
+                                                   hs.data_ptr(), cap, dev.data_ptr(),
+                                                   lab.data_ptr(), dstream.data_ptr(), cap,
+                                                   ws.data_ptr(), ws.numel(), 0)
+    assert rc == 0 and nbytes < n  # under one byte per label at this bound
+    hl = torch.empty(n, dtype=torch.int64).pin_memory()
+    rc, tau2 = B.mgard_compress_host(dims, None, B.F32, 0, 1e-3, hf.data_ptr(), hl.data_ptr(),
+                                     dev.data_ptr(), lab.data_ptr(), ws.data_ptr(), ws.numel(), 0)
+    assert rc == 0 and tau2 == tau
+    assert np.array_equal(O.unpack_labels(hs.numpy()[:nbytes].tobytes()), hl.numpy())
+    out_p = torch.empty(dims, dtype=torch.float32).pin_memory()
+    out_u = torch.empty(dims, dtype=torch.float32).pin_memory()
+    assert B.mgard_decompress_host_packed(dims, None, B.F32, 0, tau, hs.data_ptr(), nbytes,
+                                          out_p.data_ptr(), dev.data_ptr(), lab.data_ptr(),
+                                          dstream.data_ptr(), cap, ws.data_ptr(), ws.numel(), 0) == 0
+    assert B.mgard_decompress_host(dims, None, B.F32, 0, tau, hl.data_ptr(), out_u.data_ptr(),
+                                   dev.data_ptr(), lab.data_ptr(), ws.data_ptr(), ws.numel(), 0) == 0
+    assert np.array_equal(out_p.numpy(), out_u.numpy())
+    assert np.abs(out_p.numpy().astype(np.float64) - u).max() <= tau
