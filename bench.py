@@ -8,8 +8,10 @@ level-wise quantization -> dequantization -> recomposition, at an L-inf bound
 cycling through {1e-2, 1e-3, 1e-4, 1e-5} x range.  `value` is field bytes per
 step time (GB/s) with the field resident in HBM; `dec_rec_gbs` is field
 bytes / (decompose + recompose time) alone; `e2e` is the same step through the
-host-buffer C entry points (mgard_compress_host / mgard_decompress_host) with
-the copies inside the timed region.  Inside the timed region only the
+host-buffer C entry points (mgard_compress_host_packed /
+mgard_decompress_host_packed: the labels cross the link as their packed
+lossless stream) with the copies inside the timed region; `quality` gives the
+compression ratio, bits per value and PSNR of that stream per bound.  Inside the timed region only the
 dominant kernel's launches carry timing events (its `roofline` figures come
 from them); the per-kernel and per-phase split comes from passes outside it.
 
@@ -519,15 +521,35 @@ def run_gpu(args, rank, world, local_rank):
             "area": area, "area_rel_diff_vs_full": area / area_full - 1.0}
     x.copy_(u)
 
-    # End to end through the host-buffer entry points.
+    # End to end through the host-buffer entry points: the packed path (the
+    # labels' lossless stream crosses the link) is the headline, the int64
+    # label path beside it.
     ws = B.workspace(DIMS, torch.float32, dev)
     labels = torch.empty(DIMS, dtype=torch.int64, device=dev)
+    cnt = int(np.prod(DIMS))
+    cap = B.pack_bound(cnt)
+    d_stream = torch.empty(cap, dtype=torch.uint8, device=dev)
     h_field = torch.from_numpy(u_host).pin_memory()
     h_labels = torch.empty(DIMS, dtype=torch.int64).pin_memory()
+    h_stream = torch.empty(cap, dtype=torch.uint8).pin_memory()
     h_out = torch.empty(DIMS, dtype=torch.float32).pin_memory()
     ke = max(3, args.steps // 40)
+    sizes = {}
 
-    def e2e_step(rel):
+    def e2e_step(rel, packed=True):
+        if packed:
+            rc, nb, tau = B.mgard_compress_host_packed(
+                DIMS, None, B.F32, 0, rel, h_field.data_ptr(), h_stream.data_ptr(), cap,
+                x.data_ptr(), labels.data_ptr(), d_stream.data_ptr(), cap, ws.data_ptr(),
+                ws.numel(), stream.cuda_stream)
+            assert rc == 0, rc
+            sizes[rel] = nb
+            rc = B.mgard_decompress_host_packed(
+                DIMS, None, B.F32, 0, tau, h_stream.data_ptr(), nb, h_out.data_ptr(),
+                x.data_ptr(), labels.data_ptr(), d_stream.data_ptr(), cap, ws.data_ptr(),
+                ws.numel(), stream.cuda_stream)
+            assert rc == 0, rc
+            return tau
         rc, tau = B.mgard_compress_host(DIMS, None, B.F32, 0, rel, h_field.data_ptr(),
                                         h_labels.data_ptr(), x.data_ptr(), labels.data_ptr(),
                                         ws.data_ptr(), ws.numel(), stream.cuda_stream)
@@ -538,26 +560,50 @@ def run_gpu(args, rank, world, local_rank):
         assert rc == 0, rc
         return tau
 
-    e2e_step(1e-3)
-    torch.cuda.synchronize()
-    barrier()
-    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    es.record(stream)
-    for i in range(ke):
-        e2e_step(BOUNDS[i % 4])
-    ee.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = es.elapsed_time(ee)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = t.item()
-    tau = e2e_step(1e-3)
-    e2e_err = float(np.abs(h_out.numpy().astype(np.float64) - u_host).max()) / tau
-    cnt = int(np.prod(DIMS))
+    def timed_e2e(packed):
+        e2e_step(1e-3, packed)
+        torch.cuda.synchronize()
+        barrier()
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record(stream)
+        for i in range(ke):
+            e2e_step(BOUNDS[i % 4], packed)
+        ee.record(stream)
+        torch.cuda.synchronize()
+        ms = es.elapsed_time(ee)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = t.item()
+        return ms
+
+    e2e_ms = timed_e2e(True)
+    stream_bytes = sum(sizes[BOUNDS[i % 4]] for i in range(ke)) / ke
+    # Rate and distortion per bound (Section 6, "Quality"): compression
+    # ratio and bits per value of the packed stream, PSNR and L-inf / tau of
+    # the reconstruction.
+    quality = {}
+    u64 = u.double()
+    rng_u = float((u64.max() - u64.min()).item())
+    for rel in BOUNDS:
+        tau = e2e_step(rel, True)
+        rec = torch.from_numpy(h_out.numpy()).to(dev).double()
+        mse = float(((rec - u64) ** 2).mean().item())
+        quality[f"{rel:g}"] = {
+            "compression_ratio": nbytes / sizes[rel], "bits_per_value": 8.0 * sizes[rel] / cnt,
+            "psnr_db": 20 * np.log10(rng_u) - 10 * np.log10(mse),
+            "linf_over_tau": float((rec - u64).abs().max().item()) / tau}
+        del rec
     e2e = {"value": world * nbytes * ke / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": nbytes + 8 * cnt, "d2h_bytes_per_step": 8 * cnt + nbytes,
-           "ms_per_step": e2e_ms / ke, "steps": ke, "linf_over_tau_1e-3": e2e_err}
+           "h2d_bytes_per_step": nbytes + stream_bytes, "d2h_bytes_per_step": stream_bytes + nbytes,
+           "ms_per_step": e2e_ms / ke, "steps": ke,
+           "path": "mgard_compress_host_packed + mgard_decompress_host_packed",
+           "linf_over_tau_1e-3": quality["0.001"]["linf_over_tau"]}
+    e2e_u_ms = timed_e2e(False)
+    e2e_unpacked = {"value": world * nbytes * ke / (e2e_u_ms * 1e-3) / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": nbytes + 8 * cnt, "d2h_bytes_per_step": 8 * cnt + nbytes,
+                    "ms_per_step": e2e_u_ms / ke,
+                    "path": "mgard_compress_host + mgard_decompress_host (int64 labels)"}
 
     if rank != 0:
         return
@@ -575,6 +621,8 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "e2e_int64_labels": e2e_unpacked,
+        "quality": quality,
         "gpu_launches": launches,
         "clocks": clocks.summary(t0, t1),
         "fp64": fp64,
