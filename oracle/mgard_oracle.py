@@ -42,6 +42,8 @@ explicit finite-element operators assembled from the grid coordinates:
   grid function (Section 6.2.2's analysis) by marching tetrahedra.
 * The labels' lossless stage (Algorithm 1 line 23; this build's coder is a
   chunked zigzag bit packing, a reading) and PSNR (Section 6, "Quality").
+* The other bin-width rules of Section 4.1: L-infinity-optimal widths and
+  L2 error control.
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
 non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
@@ -56,7 +58,10 @@ sums in tests/golden/prediction_errors.txt and exactness properties of the
 two predictors; partial recomposition by the projection chain; the iso
 area by planar surfaces, exact, and a sphere's convergence; the packed
 label stream by hand-derived bytes in tests/golden/packed_labels.txt and
-round trips; PSNR by a closed form).
+round trips; PSNR by a closed form; the L2 and L-inf-optimal rules by a
+closed form, their sums, and worst-case coefficient errors staying within
+the bound after recomposition).  The L2 rule's constant C_L2 = 1 is a
+reading (the paper gives no value), derived and pinned as a valid bound.
 ``linf_constant`` is a reading (the paper
 gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
 worst-case error amplification, and its exact value is "parity unpinned" with
@@ -79,6 +84,7 @@ __all__ = [
     "LORENZO_PENALTY", "INTERP_PENALTY", "sampled_blocks", "prediction_errors",
     "adaptive_stop_level", "recompose_partial", "iso_area",
     "PACK_CHUNK", "pack_labels", "unpack_labels", "psnr",
+    "level_tolerances_mode", "l2_error",
 ]
 
 
@@ -685,3 +691,80 @@ def psnr(u: np.ndarray, v: np.ndarray) -> float:
     v = np.asarray(v, dtype=np.float64)
     mse = float(np.mean((u - v) ** 2))
     return 20.0 * math.log10(float(u.max() - u.min())) - 10.0 * math.log10(mse)
+
+
+# --------------------------------------------------------------------------
+# Other bin-width rules (Section 4.1): L-inf-optimal widths and L2 control
+# --------------------------------------------------------------------------
+
+def _level_counts(H: Hierarchy, stop_level: int) -> np.ndarray:
+    """#N*_l for l = 0..L: the nodes new at level l, with the whole coarse
+    block N_{l~} counted at the stopping level (it is quantized with
+    tau_{l~}); 0 below the stopping level."""
+    n = [int(np.prod(H.levels[l])) for l in range(H.L + 1)]
+    out = np.zeros(H.L + 1)
+    out[stop_level] = n[stop_level]
+    for l in range(stop_level + 1, H.L + 1):
+        out[l] = n[l] - n[l - 1]
+    return out
+
+
+def _cell_measure(H: Hierarchy, l: int) -> float:
+    """``h_l^d``: the product over the axes of the largest row sum of the
+    level-l 1D mass matrix (the integral of a hat function), which equals
+    h^d on a uniform grid of spacing h and bounds the mass matrix's largest
+    eigenvalue on any grid."""
+    out = 1.0
+    for d in range(H.ndim):
+        M = mass_matrix(H.coords[l][d])
+        out *= float(np.max(np.asarray(M.sum(axis=1)).ravel()))
+    return out
+
+
+def level_tolerances_mode(H: Hierarchy, stop_level: int, tau: float, mode: str) -> np.ndarray:
+    """Per-level tolerances ``tau_l`` (l = 0..L; below the stopping level
+    they repeat tau_{l~}) for the three rules of Section 4.1:
+
+    * ``"geometric"``: Eq. (LinfTau), ``tau_l = kappa^(l-l~) tau_{l~}`` with
+      ``sum tau_l = tau / C_Linf`` (the rule used throughout);
+    * ``"linf_optimal"``: the widths that minimise the estimated label cost
+      under the same L-infinity condition, ``tau_l = tau / C_Linf * #N*_l /
+      #N_L`` (noted in Section 4.1 for completeness);
+    * ``"l2"``: ``tau`` bounds the L2 norm of the reconstruction error:
+      ``tau_l = tau / (C_L2 h_l^d #N_L)^(1/2)``, which meets
+      ``sum_l h_l^d #N*_l tau_l^2 = tau^2 / C_L2``.  Reading: C_L2 = 1 with
+      h_l^d the largest mass-matrix row-sum product of level l; the
+      multilevel error components (I - Q_{l-1}) e_l are L2-orthogonal and
+      each is at most its nodal P1 function's norm, at most h_l^d sum e^2,
+      so the bound holds with that constant."""
+    if mode == "geometric":
+        return level_tolerances(H, stop_level, tau)
+    _check_stop(H, stop_level)
+    cnt = _level_counts(H, stop_level)
+    nL = float(np.prod(H.levels[H.L]))
+    taus = np.empty(H.L + 1)
+    if mode == "linf_optimal":
+        C = linf_constant(H, stop_level)
+        for l in range(stop_level, H.L + 1):
+            taus[l] = tau / C * cnt[l] / nL
+    elif mode == "l2":
+        for l in range(stop_level, H.L + 1):
+            taus[l] = tau / math.sqrt(_cell_measure(H, l) * nL)
+    else:
+        raise ValueError(f"unknown mode {mode}")
+    taus[:stop_level] = taus[stop_level]
+    return taus
+
+
+def l2_error(e: np.ndarray, H: Hierarchy) -> float:
+    """L2 norm of the P1 function with nodal values ``e`` on the finest
+    grid: sqrt(e^T M e), M the tensor-product mass matrix."""
+    e = np.asarray(e, dtype=np.float64)
+    Me = e
+    for d in range(H.ndim):
+        M = mass_matrix(H.coords[H.L][d])
+        vm = np.moveaxis(Me, d, 0)
+        shape = vm.shape
+        X = np.ascontiguousarray(vm).reshape(shape[0], -1)
+        Me = np.moveaxis((M @ X).reshape(shape), 0, d)
+    return math.sqrt(float(np.sum(e * Me)))

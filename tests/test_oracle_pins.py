@@ -672,3 +672,53 @@ def test_psnr_closed_form():
     v = np.array([0.0, 1.1])
     # range 1, mean squared error 0.005
     assert O.psnr(u, v) == pytest.approx(-10 * np.log10(0.005), rel=1e-14)
+
+
+# --------------------------------------- L-inf-optimal and L2 bin widths ---
+
+def test_l2_tolerances_uniform_closed_form():
+    # 5^3 with index coordinates: h_1 = 1, h_0 = 2, #N_L = 125.
+    H = O.Hierarchy((5, 5, 5))
+    t = O.level_tolerances_mode(H, 0, 1.0, "l2")
+    assert t[1] == pytest.approx(1.0 / np.sqrt(125.0), rel=1e-14)
+    assert t[0] == pytest.approx(1.0 / np.sqrt(8.0 * 125.0), rel=1e-14)
+    # Geometric growth kappa = 2^(d/2) on dyadic grids (Section 4.1).
+    H = O.Hierarchy((33, 17, 9))
+    t = O.level_tolerances_mode(H, 1, 2.0, "l2")
+    np.testing.assert_allclose(t[2:] / t[1:-1], np.sqrt(8.0), rtol=1e-13)
+
+
+def _worst_errors(H, stop, taus, seed):
+    # Coefficient errors of magnitude tau_l with random signs at every node.
+    rng = _rng(seed)
+    lev = O.node_levels(H, stop)
+    return np.asarray(taus)[lev] * rng.choice([-1.0, 1.0], size=lev.shape)
+
+
+@pytest.mark.parametrize("dims,kind,stop", [((17, 17, 9), "u", 0), ((12, 10, 9), "g", 1),
+                                            ((33, 17), "g", 0)])
+def test_l2_bound_holds_for_worst_errors(dims, kind, stop):
+    coords = None if kind == "u" else [F.geometric_coords(n, 1.08) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    tau = 0.3
+    taus = O.level_tolerances_mode(H, stop, tau, "l2")
+    for seed in range(3):
+        err = O.recompose(_worst_errors(H, stop, taus, seed), H, stop)
+        assert O.l2_error(err, H) <= tau * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("dims,kind,stop", [((17, 17, 9), "u", 0), ((12, 10, 9), "g", 1)])
+def test_linf_optimal_widths(dims, kind, stop):
+    coords = None if kind == "u" else [F.geometric_coords(n, 1.08) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    tau = 0.3
+    taus = O.level_tolerances_mode(H, stop, tau, "linf_optimal")
+    # Proportional to the level's node count, summing to tau / C_Linf.
+    counts = [np.prod(H.levels[stop])] + [np.prod(H.levels[l]) - np.prod(H.levels[l - 1])
+                                          for l in range(stop + 1, H.L + 1)]
+    np.testing.assert_allclose(taus[stop:] / np.asarray(counts, dtype=float),
+                               taus[stop] / counts[0], rtol=1e-13)
+    assert taus[stop:].sum() == pytest.approx(tau / O.linf_constant(H, stop), rel=1e-13)
+    for seed in range(3):
+        err = O.recompose(_worst_errors(H, stop, taus, seed), H, stop)
+        assert np.abs(err).max() <= tau * (1 + 1e-12)
