@@ -95,6 +95,29 @@ int mgard_decompose(int ndim, const int64_t* dims, const double* const* coords, 
                     int stop_level, void* data, void* workspace, size_t ws_bytes,
                     void* stream);
 
+/* The other bin-width rules of Section 4.1.  mgard_level_tolerances_mode
+ * writes L + 1 level tolerances (entries below stop_level repeat
+ * tau_{l~}) for mode 0: the geometric rule of mgard_level_tolerances (Eq.
+ * LinfTau, tau an L-inf bound); 1: the L-inf-optimal widths, tau_l =
+ * tau / C_Linf * #N*_l / #N_L (#N*_l the nodes new at level l, the whole
+ * coarse block at the stopping level), the same L-inf guarantee; 2: tau an
+ * L2 bound on the reconstruction error, tau_l = tau / (C_L2 h_l^d
+ * #N_L)^(1/2) with C_L2 = 1 and h_l^d the product over the axes of the
+ * largest integral of a level-l hat function (the reconstruction's error
+ * components are L2-orthogonal across levels, so the bound holds with
+ * that constant).  Host only.  mgard_quantize_levels and
+ * mgard_dequantize_levels are mgard_quantize / mgard_dequantize with the
+ * level tolerances given (tau_levels, host, L + 1 values, those from
+ * stop_level on positive and finite, else MGARD_ERR_ARG). */
+int mgard_level_tolerances_mode(int ndim, const int64_t* dims, const double* const* coords,
+                                int stop_level, double tau, int mode, double* tau_out);
+int mgard_quantize_levels(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                          int stop_level, const double* tau_levels, const void* coeffs,
+                          int64_t* labels, void* stream);
+int mgard_dequantize_levels(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                            int stop_level, const double* tau_levels, const int64_t* labels,
+                            void* coeffs, void* stream);
+
 /* Adaptive decomposition, in place (Section 4.2, Algorithm 1 lines 1-16):
  * for l = L, L-1, .., 1 the level-l grid is sampled (the cells of the
  * level-(l-1) grid with every index a multiple of 4, i.e. one 3^3 block in

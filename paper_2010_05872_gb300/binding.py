@@ -39,6 +39,14 @@ _SIGNATURES = {
                                        _VP, _VP, ctypes.c_size_t, _VP]),
     "mgard_recompose": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                        _VP, _VP, ctypes.c_size_t, _VP]),
+    "mgard_level_tolerances_mode": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_double)]),
+    "mgard_quantize_levels": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_double), _VP, _VP, _VP]),
+    "mgard_dequantize_levels": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP,
+                                               _VP, _VP]),
     "mgard_pack_bound": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "mgard_pack_labels": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_size_t,
                                          ctypes.POINTER(ctypes.c_size_t), _VP]),
@@ -518,6 +526,48 @@ def decompose(x, coords=None, stop_level: int = 0, ws=None, stream=None):
                          ws.numel(), _stream(stream))
     _check(rc, "mgard_decompose")
     return x
+
+
+TOL_MODES = {"geometric": 0, "linf_optimal": 1, "l2": 2}
+
+
+def mgard_level_tolerances_mode(dims, coords, stop_level: int, tau: float, mode: str) -> np.ndarray:
+    """Level tolerances for one of the Section 4.1 rules (see TOL_MODES)."""
+    s = _Shape(dims, coords)
+    L = mgard_num_levels(dims)
+    out = (ctypes.c_double * (L + 1))()
+    rc = lib().mgard_level_tolerances_mode(s.ndim, s.dims, s.coords, int(stop_level), float(tau),
+                                           TOL_MODES[mode], out)
+    _check(rc, "mgard_level_tolerances_mode")
+    return np.array(out[:], dtype=np.float64)
+
+
+def quantize_levels(x, taus, coords=None, stop_level: int = 0, labels=None, stream=None):
+    """int64 labels of the CUDA tensor x with the given level tolerances."""
+    _cuda_tensor(x, "x")
+    torch = _torch()
+    if labels is None:
+        labels = torch.empty(x.shape, dtype=torch.int64, device=x.device)
+    t = (ctypes.c_double * len(taus))(*[float(v) for v in taus])
+    s = _Shape(x.shape, coords)
+    rc = lib().mgard_quantize_levels(s.ndim, s.dims, s.coords, dtype_code(x), int(stop_level), t,
+                                     x.data_ptr(), labels.data_ptr(), _stream(stream))
+    _check(rc, "mgard_quantize_levels")
+    return labels
+
+
+def dequantize_levels(labels, taus, dtype, coords=None, stop_level: int = 0, out=None, stream=None):
+    """Coefficients from int64 CUDA labels with the given level tolerances."""
+    _cuda_tensor(labels, "labels")
+    torch = _torch()
+    if out is None:
+        out = torch.empty(labels.shape, dtype=dtype, device=labels.device)
+    t = (ctypes.c_double * len(taus))(*[float(v) for v in taus])
+    s = _Shape(labels.shape, coords)
+    rc = lib().mgard_dequantize_levels(s.ndim, s.dims, s.coords, dtype_code(out), int(stop_level), t,
+                                       labels.data_ptr(), out.data_ptr(), _stream(stream))
+    _check(rc, "mgard_dequantize_levels")
+    return out
 
 
 def pack_bound(count: int) -> int:

@@ -424,6 +424,14 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
   if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
   double t[kMaxLevels];
   level_tolerances(p.h, stop_level, tau, t);
+  return make_table_levels(p, stop_level, t, tab, tau_out);
+}
+
+int make_table_levels(const DevPlan& p, int stop_level, const double* t, LevelTable& tab,
+                      double* tau_out) {
+  if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
+  for (int l = stop_level; l <= p.h.L; ++l)
+    if (!(t[l] > 0.0) || !std::isfinite(t[l])) return MGARD_ERR_ARG;
   for (int l = 0; l < 48; ++l) {
     tab.q[l] = 1.0;
     tab.rq[l] = std::nanf("");
@@ -431,7 +439,8 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
     tab.dqf[l] = 0.0f;
   }
   for (int l = 0; l <= p.h.L; ++l) {
-    tab.q[l] = 2.0 * t[l];
+    // Levels below the stopping level are quantized with tau_{l~}.
+    tab.q[l] = 2.0 * t[std::max(l, stop_level)];
     // The FP32 reciprocal drives the exact fast path of the quantizer; it is
     // only usable when it is a normal float.
     const double r = 1.0 / tab.q[l];
@@ -445,7 +454,7 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
     tab.dqf[l] = qok ? static_cast<float>(tab.q[l] - static_cast<double>(qf)) : 0.0f;
   }
   if (tau_out)
-    for (int l = 0; l <= p.h.L; ++l) tau_out[l] = t[l];
+    for (int l = 0; l <= p.h.L; ++l) tau_out[l] = t[std::max(l, stop_level)];
   return MGARD_OK;
 }
 
@@ -490,6 +499,18 @@ int mgard_level_tolerances(int ndim, const int64_t* dims, const double* const* c
   if (rc != MGARD_OK) return rc;
   if (stop_level < 0 || stop_level > h.L) return MGARD_ERR_LEVEL;
   level_tolerances(h, stop_level, tau_linf, tau_out);
+  return MGARD_OK;
+}
+
+int mgard_level_tolerances_mode(int ndim, const int64_t* dims, const double* const* coords,
+                                int stop_level, double tau, int mode, double* tau_out) {
+  if (tau_out == nullptr || mode < 0 || mode > 2) return MGARD_ERR_ARG;
+  if (!(tau > 0.0) || !std::isfinite(tau)) return MGARD_ERR_ARG;
+  HostPlan h;
+  int rc = build_host_plan(ndim, dims, coords, h);
+  if (rc != MGARD_OK) return rc;
+  if (stop_level < 0 || stop_level > h.L) return MGARD_ERR_LEVEL;
+  level_tolerances_mode(h, stop_level, tau, mode, tau_out);
   return MGARD_OK;
 }
 
@@ -807,29 +828,21 @@ int mgard_recompose_host(int ndim, const int64_t* dims, const double* const* coo
                         workspace, ws_bytes, stream);
 }
 
-int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
-                   int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
-                   double* tau_levels_out, void* stream) {
-  DevPlan* p = nullptr;
-  int rc = get_plan(ndim, dims, coords, dtype, &p);
-  if (rc != MGARD_OK) return rc;
-  if (coeffs == nullptr || labels == nullptr) return MGARD_ERR_ARG;
-  if (reinterpret_cast<uintptr_t>(coeffs) % elem_size(dtype) || reinterpret_cast<uintptr_t>(labels) % 8)
-    return MGARD_ERR_ARG;
-  LevelTable tab;
-  rc = make_table(*p, stop_level, tau_linf, tab, tau_levels_out);
-  if (rc != MGARD_OK) return rc;
+namespace {
+
+int quantize_table(const DevPlan& p, int dtype, int stop_level, const LevelTable& tab,
+                   const void* coeffs, int64_t* labels, void* stream) {
   DevCtx* c = get_ctx();
   if (c == nullptr) return MGARD_ERR_CUDA;
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MGB_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s));
-  const auto& d = p->h.dims3;
+  const auto& d = p.h.dims3;
   if (dtype == MGARD_F64)
-    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p->lev01, p->lev[2],
+    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p.lev01, p.lev[2],
                                     d[0] * d[1], d[2], stop_level, tab, c->flags, s));
   else
-    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p->lev01, p->lev[2],
+    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p.lev01, p.lev[2],
                                    d[0] * d[1], d[2], stop_level, tab, c->flags, s));
   MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
@@ -841,6 +854,70 @@ int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, i
   if (f & 1u) return MGARD_ERR_NONFINITE;
   if (f & 2u) return MGARD_ERR_OVERFLOW;
   return MGARD_OK;
+}
+
+int dequantize_table(const DevPlan& p, int dtype, int stop_level, const LevelTable& tab,
+                     const int64_t* labels, void* coeffs, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto& d = p.h.dims3;
+  if (dtype == MGARD_F64)
+    return cuda_rc(launch_dequantize<double>(labels, static_cast<double*>(coeffs), p.lev01,
+                                             p.lev[2], d[0] * d[1], d[2], stop_level, tab, s));
+  return cuda_rc(launch_dequantize<float>(labels, static_cast<float*>(coeffs), p.lev01, p.lev[2],
+                                          d[0] * d[1], d[2], stop_level, tab, s));
+}
+
+int check_q_args(int dtype, const void* coeffs, const int64_t* labels) {
+  if (coeffs == nullptr || labels == nullptr) return MGARD_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(coeffs) % elem_size(dtype) || reinterpret_cast<uintptr_t>(labels) % 8)
+    return MGARD_ERR_ARG;
+  return MGARD_OK;
+}
+
+}  // namespace
+
+int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                   int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
+                   double* tau_levels_out, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_q_args(dtype, coeffs, labels);
+  if (rc != MGARD_OK) return rc;
+  LevelTable tab;
+  rc = make_table(*p, stop_level, tau_linf, tab, tau_levels_out);
+  if (rc != MGARD_OK) return rc;
+  return quantize_table(*p, dtype, stop_level, tab, coeffs, labels, stream);
+}
+
+int mgard_quantize_levels(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                          int stop_level, const double* tau_levels, const void* coeffs,
+                          int64_t* labels, void* stream) {
+  if (tau_levels == nullptr) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_q_args(dtype, coeffs, labels);
+  if (rc != MGARD_OK) return rc;
+  LevelTable tab;
+  rc = make_table_levels(*p, stop_level, tau_levels, tab, nullptr);
+  if (rc != MGARD_OK) return rc;
+  return quantize_table(*p, dtype, stop_level, tab, coeffs, labels, stream);
+}
+
+int mgard_dequantize_levels(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                            int stop_level, const double* tau_levels, const int64_t* labels,
+                            void* coeffs, void* stream) {
+  if (tau_levels == nullptr) return MGARD_ERR_ARG;
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_q_args(dtype, coeffs, labels);
+  if (rc != MGARD_OK) return rc;
+  LevelTable tab;
+  rc = make_table_levels(*p, stop_level, tau_levels, tab, nullptr);
+  if (rc != MGARD_OK) return rc;
+  return dequantize_table(*p, dtype, stop_level, tab, labels, coeffs, stream);
 }
 
 int mgard_dequantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,

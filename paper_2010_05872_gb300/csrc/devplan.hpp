@@ -72,5 +72,9 @@ int run_transform(bool dec, const DevPlan& p, int stop_level, void* data, char* 
 // LinfTau), with the FP32 helpers of the quantizer's fast paths; tau_out
 // (L + 1 values, may be NULL) receives the level tolerances.
 int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, double* tau_out);
+// The same from given level tolerances t[0..L] (entries from stop_level on
+// must be positive and finite).
+int make_table_levels(const DevPlan& p, int stop_level, const double* t, LevelTable& tab,
+                      double* tau_out);
 
 }  // namespace mgb

@@ -308,6 +308,47 @@ double linf_constant(const HostPlan& p, int stop_level) {
   return C;
 }
 
+void level_tolerances_mode(const HostPlan& p, int stop_level, double tau, int mode,
+                           double* out) {
+  if (mode == 0) {
+    level_tolerances(p, stop_level, tau, out);
+    return;
+  }
+  const int pad = 3 - p.ndim;
+  auto nodes = [&](int l) { return double(p.shape[l][0]) * p.shape[l][1] * p.shape[l][2]; };
+  const double nL = nodes(p.L);
+  if (mode == 1) {
+    // L-inf-optimal widths: tau_l proportional to #N*_l (the coarse block
+    // counted whole at the stopping level), summing to tau / C_Linf.
+    const double C = linf_constant(p, stop_level);
+    for (int l = stop_level; l <= p.L; ++l) {
+      const double cnt = l == stop_level ? nodes(l) : nodes(l) - nodes(l - 1);
+      out[l] = tau / C * cnt / nL;
+    }
+  } else {
+    // L2 control: tau_l = tau / sqrt(h_l^d #N_L), h_l^d the product of the
+    // largest 1D mass-matrix row sums (integrals of the hat functions) of
+    // level l.
+    for (int l = stop_level; l <= p.L; ++l) {
+      double hd = 1.0;
+      for (int d = 0; d < p.ndim; ++d) {
+        const auto& ix = p.idx[l][pad + d];
+        const auto& x = p.x[pad + d];
+        const size_t n = ix.size();
+        double m = 0.0;
+        for (size_t j = 0; j < n; ++j) {
+          const double left = j > 0 ? x[ix[j]] - x[ix[j - 1]] : 0.0;
+          const double right = j + 1 < n ? x[ix[j + 1]] - x[ix[j]] : 0.0;
+          m = std::max(m, 0.5 * (left + right));
+        }
+        hd *= m;
+      }
+      out[l] = tau / std::sqrt(hd * nL);
+    }
+  }
+  for (int l = 0; l < stop_level; ++l) out[l] = out[stop_level];
+}
+
 void level_tolerances(const HostPlan& p, int stop_level, double tau, double* out) {
   const double C = linf_constant(p, stop_level);
   const double kappa = std::sqrt(std::pow(2.0, p.ndim));

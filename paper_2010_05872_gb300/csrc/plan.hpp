@@ -62,5 +62,9 @@ int build_host_plan(int ndim, const int64_t* dims, const double* const* coords, 
 double linf_constant(const HostPlan& p, int stop_level);
 // tau_out receives L+1 values (entries below stop_level repeat tau_{stop}).
 void level_tolerances(const HostPlan& p, int stop_level, double tau, double* tau_out);
+// mode 0: the geometric rule above; 1: L-inf-optimal widths (tau_l
+// proportional to the level's new nodes, sum tau / C_Linf); 2: tau is an L2
+// bound, tau_l = tau / sqrt(h_l^d #N_L) (Section 4.1).
+void level_tolerances_mode(const HostPlan& p, int stop_level, double tau, int mode, double* tau_out);
 
 }  // namespace mgb

@@ -109,3 +109,15 @@ def test_level_grid_matches_oracle(lib, dims, kind):
         assert shape == H.levels[level]
         for d in range(len(dims)):
             np.testing.assert_array_equal(axes[d], H.coords[level][d])
+
+
+@pytest.mark.parametrize("dims,kind,stop", [((33, 20, 17), "u", 0), ((10, 17, 9), "g", 1),
+                                            ((1000,), "g", 2), ((70, 45), "u", 0)])
+@pytest.mark.parametrize("mode", ["geometric", "linf_optimal", "l2"])
+def test_level_tolerance_modes_match_oracle(lib, dims, kind, stop, mode):
+    coords = None if kind == "u" else [F.geometric_coords(n, 1.03) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    stop = min(stop, H.L)
+    got = B.mgard_level_tolerances_mode(dims, coords, stop, 0.7, mode)
+    exp = O.level_tolerances_mode(H, stop, 0.7, mode)
+    np.testing.assert_allclose(got, exp, rtol=1e-12)
