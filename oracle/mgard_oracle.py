@@ -44,6 +44,8 @@ explicit finite-element operators assembled from the grid coordinates:
   chunked zigzag bit packing, a reading) and PSNR (Section 6, "Quality").
 * The other bin-width rules of Section 4.1: L-infinity-optimal widths and
   L2 error control.
+* The coarse part's Lorenzo coder (Algorithm 1 line 18): Lorenzo residuals
+  of the coarse block's labels and their inverse.
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
 non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
@@ -60,7 +62,8 @@ area by planar surfaces, exact, and a sphere's convergence; the packed
 label stream by hand-derived bytes in tests/golden/packed_labels.txt and
 round trips; PSNR by a closed form; the L2 and L-inf-optimal rules by a
 closed form, their sums, and worst-case coefficient errors staying within
-the bound after recomposition).  The L2 rule's constant C_L2 = 1 is a
+the bound after recomposition; the Lorenzo coder by hand residuals and
+round trips).  The L2 rule's constant C_L2 = 1 is a
 reading (the paper gives no value), derived and pinned as a valid bound.
 ``linf_constant`` is a reading (the paper
 gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
@@ -84,7 +87,7 @@ __all__ = [
     "LORENZO_PENALTY", "INTERP_PENALTY", "sampled_blocks", "prediction_errors",
     "adaptive_stop_level", "recompose_partial", "iso_area",
     "PACK_CHUNK", "pack_labels", "unpack_labels", "psnr",
-    "level_tolerances_mode", "l2_error",
+    "level_tolerances_mode", "l2_error", "lorenzo_encode", "lorenzo_decode",
 ]
 
 
@@ -768,3 +771,52 @@ def l2_error(e: np.ndarray, H: Hierarchy) -> float:
         X = np.ascontiguousarray(vm).reshape(shape[0], -1)
         Me = np.moveaxis((M @ X).reshape(shape), 0, d)
     return math.sqrt(float(np.sum(e * Me)))
+
+
+# --------------------------------------------------------------------------
+# Coarse-part predictor (Algorithm 1 line 18; Section 4.2, Eq. (lorenzo))
+# --------------------------------------------------------------------------
+
+def _coarse_block(labels, H: Hierarchy, stop_level: int):
+    return np.ix_(*H.index[stop_level])
+
+
+def lorenzo_encode(labels: np.ndarray, H: Hierarchy, stop_level: int) -> np.ndarray:
+    """Labels with the coarse block N_{l~} replaced by its Lorenzo residuals:
+    r = q - pred(q), pred the signed sum of the 2^d - 1 lower neighbours in
+    the coarse grid (0 outside it), in 64-bit wrap-around integer arithmetic
+    (an exact bijection).  The coarse labels are the linear quantization of
+    Q_{l~}u with bin 2 tau_{l~}, so predicting from them is predicting from
+    the reconstructed values, as the Lorenzo coder of Section 4.2 does; the
+    residuals of a smooth coarse part are small and pack tightly."""
+    out = np.array(labels, dtype=np.int64, copy=True)
+    ix = _coarse_block(out, H, stop_level)
+    q = out[ix].astype(np.uint64)
+    r = q.copy()
+    d = q.ndim
+    for mask in range(1, 1 << d):
+        shifted = q
+        for a in range(d):
+            if mask >> a & 1:
+                pad = [(0, 0)] * d
+                pad[a] = (1, 0)
+                shifted = np.pad(shifted, pad)[tuple(slice(0, n) for n in q.shape)]
+        if bin(mask).count("1") % 2 == 1:
+            r = r - shifted
+        else:
+            r = r + shifted
+    out[ix] = r.astype(np.int64)
+    return out
+
+
+def lorenzo_decode(labels: np.ndarray, H: Hierarchy, stop_level: int) -> np.ndarray:
+    """Inverse of :func:`lorenzo_encode`: the residual operator is the product
+    of the backward differences along every axis, so cumulative sums along
+    every axis (64-bit wrap-around) restore the labels."""
+    out = np.array(labels, dtype=np.int64, copy=True)
+    ix = _coarse_block(out, H, stop_level)
+    q = out[ix].astype(np.uint64)
+    for a in range(q.ndim):
+        q = np.cumsum(q, axis=a, dtype=np.uint64)
+    out[ix] = q.astype(np.int64)
+    return out

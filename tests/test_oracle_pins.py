@@ -722,3 +722,33 @@ def test_linf_optimal_widths(dims, kind, stop):
     for seed in range(3):
         err = O.recompose(_worst_errors(H, stop, taus, seed), H, stop)
         assert np.abs(err).max() <= tau * (1 + 1e-12)
+
+
+# -------------------------------------------- coarse-part Lorenzo coder ---
+
+def test_lorenzo_residuals_by_hand():
+    # On a 3^3 coarse block: a constant leaves one residual, at the origin
+    # (no lower neighbours); q = i (the axis-0 index) leaves 1 on the line
+    # j = k = 0 for i >= 1 (every other node's mixed difference vanishes).
+    H = O.Hierarchy((3, 3, 3))
+    r = O.lorenzo_encode(np.full((3, 3, 3), 5, dtype=np.int64), H, 0)
+    exp = np.zeros((3, 3, 3), dtype=np.int64)
+    exp[0, 0, 0] = 5
+    assert np.array_equal(r, exp)
+    q = np.broadcast_to(np.arange(3)[:, None, None], (3, 3, 3)).astype(np.int64)
+    exp = np.zeros((3, 3, 3), dtype=np.int64)
+    exp[1, 0, 0] = exp[2, 0, 0] = 1
+    assert np.array_equal(O.lorenzo_encode(q, H, 0), exp)
+
+
+@pytest.mark.parametrize("dims,stop", [((17, 9, 12), 0), ((17, 9, 12), 2), ((33, 20), 1),
+                                       ((100,), 3)])
+def test_lorenzo_round_trip_and_scope(dims, stop):
+    H = O.Hierarchy(dims)
+    x = _rng(2).integers(-2 ** 62, 2 ** 62, dims)
+    e = O.lorenzo_encode(x, H, stop)
+    assert np.array_equal(O.lorenzo_decode(e, H, stop), x)
+    # Only the coarse block changes.
+    mask = np.zeros(dims, dtype=bool)
+    mask[np.ix_(*H.index[stop])] = True
+    assert np.array_equal(e[~mask], x[~mask])
