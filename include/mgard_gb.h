@@ -240,6 +240,21 @@ int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* co
                           void* host_field, void* dev_data, int64_t* dev_labels, void* workspace,
                           size_t ws_bytes, void* stream);
 
+/* The coarse part's Lorenzo coder (Algorithm 1 line 18, Section 4.2 Eq.
+ * lorenzo) as an exact transform of the labels: mgard_lorenzo_encode
+ * replaces the labels q of the coarse block N_{stop_level} (in the finest
+ * layout, device, in place) by q - pred(q), pred the signed sum of the
+ * lower neighbours in the coarse grid (0 outside it), in 64-bit
+ * wrap-around arithmetic; mgard_lorenzo_decode is its inverse (cumulative
+ * sums along every axis).  The coarse labels are the linear quantization of
+ * Q_{l~}u, so the prediction uses the reconstructed values; a smooth coarse
+ * part leaves small residuals for the lossless stage.  Other labels are
+ * untouched.  Asynchronous on `stream`. */
+int mgard_lorenzo_encode(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, int64_t* labels, void* stream);
+int mgard_lorenzo_decode(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, int64_t* labels, void* stream);
+
 /* The labels' lossless stage (Section 4.1: labels go to a lossless coder;
  * Algorithm 1 line 23).  This library's coder packs the labels in chunks
  * of 1024: zigzag codes (0, -1, 1, -2, .. -> 0, 1, 2, 3, ..) in the chunk's
@@ -261,12 +276,14 @@ int mgard_unpack_labels(const void* in, size_t bytes, int64_t count, int64_t* la
 
 /* mgard_compress_host / mgard_decompress_host with the packed label stream
  * crossing between host and device instead of int64 labels: compress
- * quantizes into dev_labels, packs into dev_stream (8-byte aligned, at
- * least mgard_pack_bound(count) bytes) and copies the stream (its size in
- * *stream_bytes, at most host_capacity, else MGARD_ERR_WORKSPACE) to
- * host_stream; decompress checks the host stream's header, copies it to
- * dev_stream, unpacks into dev_labels, dequantizes, recomposes and copies
- * the field to host_field.  Both synchronise the stream before returning. */
+ * quantizes into dev_labels, replaces the coarse block's labels by their
+ * Lorenzo residuals (mgard_lorenzo_encode), packs into dev_stream (8-byte
+ * aligned, at least mgard_pack_bound(count) bytes) and copies the stream
+ * (its size in *stream_bytes, at most host_capacity, else
+ * MGARD_ERR_WORKSPACE) to host_stream; decompress checks the host stream's
+ * header, copies it to dev_stream, unpacks into dev_labels, undoes the
+ * Lorenzo residuals, dequantizes, recomposes and copies the field to
+ * host_field.  Both synchronise the stream before returning. */
 int mgard_compress_host_packed(int ndim, const int64_t* dims, const double* const* coords,
                                int dtype, int stop_level, double rel_bound, const void* host_field,
                                void* host_stream, size_t host_capacity, size_t* stream_bytes,

@@ -47,6 +47,10 @@ _SIGNATURES = {
     "mgard_dequantize_levels": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int,
                                                ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP,
                                                _VP, _VP]),
+    "mgard_lorenzo_encode": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                            _VP, _VP]),
+    "mgard_lorenzo_decode": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                            _VP, _VP]),
     "mgard_pack_bound": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "mgard_pack_labels": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_size_t,
                                          ctypes.POINTER(ctypes.c_size_t), _VP]),
@@ -568,6 +572,19 @@ def dequantize_levels(labels, taus, dtype, coords=None, stop_level: int = 0, out
                                        labels.data_ptr(), out.data_ptr(), _stream(stream))
     _check(rc, "mgard_dequantize_levels")
     return out
+
+
+def lorenzo(labels, dtype, encode: bool, coords=None, stop_level: int = 0, stream=None):
+    """In-place Lorenzo residuals (encode) or their inverse on the coarse block
+    of int64 CUDA labels (finest layout); dtype is the field's torch dtype."""
+    _cuda_tensor(labels, "labels")
+    torch = _torch()
+    s = _Shape(labels.shape, coords)
+    code = dtype_code(torch.empty(0, dtype=dtype))
+    fn = lib().mgard_lorenzo_encode if encode else lib().mgard_lorenzo_decode
+    rc = fn(s.ndim, s.dims, s.coords, code, int(stop_level), labels.data_ptr(), _stream(stream))
+    _check(rc, "mgard_lorenzo_encode" if encode else "mgard_lorenzo_decode")
+    return labels
 
 
 def pack_bound(count: int) -> int:

@@ -706,6 +706,42 @@ int unpack_device(const void* in, int64_t count, int64_t* labels, cudaStream_t s
 
 }  // namespace
 
+namespace {
+
+// Lorenzo transform of the coarse block N_stop of `labels` (finest layout).
+int lorenzo_device(bool encode, const DevPlan& p, int stop_level, int64_t* labels, cudaStream_t s) {
+  const auto& sh = p.h.shape[stop_level];
+  const int64_t total = sh[0] * sh[1] * sh[2];
+  uint64_t* tmp = nullptr;
+  MGB_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(uint64_t) * total, s));
+  const int32_t* pos[3] = {p.pos[stop_level][0], p.pos[stop_level][1], p.pos[stop_level][2]};
+  const cudaError_t e = launch_lorenzo(encode, labels, p.h.dims3.data(), pos, sh.data(), tmp, s);
+  cudaFreeAsync(tmp, s);
+  return e == cudaSuccess ? MGARD_OK : MGARD_ERR_CUDA;
+}
+
+int lorenzo_entry(bool encode, int ndim, const int64_t* dims, const double* const* coords,
+                  int dtype, int stop_level, int64_t* labels, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  if (stop_level < 0 || stop_level > p->h.L) return MGARD_ERR_LEVEL;
+  if (labels == nullptr || reinterpret_cast<uintptr_t>(labels) % 8) return MGARD_ERR_ARG;
+  return lorenzo_device(encode, *p, stop_level, labels, static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace
+
+int mgard_lorenzo_encode(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, int64_t* labels, void* stream) {
+  return lorenzo_entry(true, ndim, dims, coords, dtype, stop_level, labels, stream);
+}
+
+int mgard_lorenzo_decode(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, int64_t* labels, void* stream) {
+  return lorenzo_entry(false, ndim, dims, coords, dtype, stop_level, labels, stream);
+}
+
 int mgard_pack_labels(int64_t count, const int64_t* labels, void* out, size_t capacity,
                       size_t* bytes_out, void* stream) {
   if (count < 0 || bytes_out == nullptr || out == nullptr || reinterpret_cast<uintptr_t>(out) % 8)
@@ -766,6 +802,8 @@ int mgard_compress_host_packed(int ndim, const int64_t* dims, const double* cons
   rc = mgard_quantize(ndim, dims, coords, dtype, stop_level, tau, dev_data, dev_labels, nullptr,
                       stream);
   if (rc != MGARD_OK) return rc;
+  rc = lorenzo_device(true, *p, stop_level, dev_labels, s);
+  if (rc != MGARD_OK) return rc;
   size_t sb = 0;
   {
     DevCtx* c = get_ctx();
@@ -803,6 +841,8 @@ int mgard_decompress_host_packed(int ndim, const int64_t* dims, const double* co
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MGB_TRY(cudaMemcpyAsync(dev_stream, host_stream, stream_bytes, cudaMemcpyHostToDevice, s));
   rc = unpack_device(dev_stream, count, dev_labels, s);
+  if (rc != MGARD_OK) return rc;
+  rc = lorenzo_device(false, *p, stop_level, dev_labels, s);
   if (rc != MGARD_OK) return rc;
   rc = mgard_dequantize(ndim, dims, coords, dtype, stop_level, tau_linf, dev_labels, dev_data, stream);
   if (rc != MGARD_OK) return rc;

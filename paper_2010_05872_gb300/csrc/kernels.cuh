@@ -127,6 +127,14 @@ cudaError_t launch_pack_labels(const int64_t* labels, int64_t n, uint8_t* out, u
 cudaError_t launch_unpack_labels(const uint8_t* in, int64_t n, uint64_t* words, uint64_t* total_words,
                                  int64_t* labels, cudaStream_t s);
 
+// Lorenzo residuals (encode) of the labels of a level's nodes (positions
+// pos[a], block shape shape3) in an array of the finest layout (dims3), in
+// place, or their inverse (decode); `tmp` holds the block's element count
+// of uint64 scratch.
+cudaError_t launch_lorenzo(bool encode, int64_t* labels, const int64_t* dims3,
+                           const int32_t* const* pos, const int64_t* shape3, uint64_t* tmp,
+                           cudaStream_t s);
+
 // Copy the nodes of a level out of an array in the finest layout (dims3)
 // into a compact grid of shape3, with per-axis node positions pos[a].
 template <typename T>

@@ -55,7 +55,8 @@ const char* kernel_kind_name(int kind) {
       "solve_strided_kernel",    "finish_kernel<dec>",      "finish_kernel<rec>",
       "quantize_kernel",         "dequantize_kernel",       "minmax_partial_kernel",
       "small_levels_kernel",     "prediction_errors_kernel", "iso_area_kernel",
-      "gather_level_kernel",     "pack_labels_kernel",      "unpack_labels_kernel"};
+      "gather_level_kernel",     "pack_labels_kernel",      "unpack_labels_kernel",
+      "lorenzo_kernel"};
   return (kind >= 0 && kind < kKNumKinds) ? names[kind] : "unknown";
 }
 

@@ -26,6 +26,7 @@ enum KernelKind : int {
   kKGather,
   kKPack,
   kKUnpack,
+  kKLorenzo,
   kKNumKinds
 };
 

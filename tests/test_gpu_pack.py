@@ -81,7 +81,10 @@ def test_packed_host_path_matches_unpacked(cuda):
     rc, tau2 = B.mgard_compress_host(dims, None, B.F32, 0, 1e-3, hf.data_ptr(), hl.data_ptr(),
                                      dev.data_ptr(), lab.data_ptr(), ws.data_ptr(), ws.numel(), 0)
     assert rc == 0 and tau2 == tau
-    assert np.array_equal(O.unpack_labels(hs.numpy()[:nbytes].tobytes()), hl.numpy())
+    H = O.Hierarchy(dims)
+    # The stream carries the labels with the coarse block's Lorenzo residuals.
+    assert np.array_equal(O.unpack_labels(hs.numpy()[:nbytes].tobytes()),
+                          O.lorenzo_encode(hl.numpy().reshape(dims), H, 0).ravel())
     out_p = torch.empty(dims, dtype=torch.float32).pin_memory()
     out_u = torch.empty(dims, dtype=torch.float32).pin_memory()
     assert B.mgard_decompress_host_packed(dims, None, B.F32, 0, tau, hs.data_ptr(), nbytes,
@@ -91,3 +94,35 @@ def test_packed_host_path_matches_unpacked(cuda):
                                    dev.data_ptr(), lab.data_ptr(), ws.data_ptr(), ws.numel(), 0) == 0
     assert np.array_equal(out_p.numpy(), out_u.numpy())
     assert np.abs(out_p.numpy().astype(np.float64) - u).max() <= tau
+
+
+@pytest.mark.parametrize("dims,stop", [((17, 9, 12), 0), ((17, 9, 12), 2), ((33, 20), 1),
+                                       ((100,), 3), ((65, 65, 65), 5)])
+def test_lorenzo_matches_oracle(cuda, dims, stop):
+    torch = cuda
+    H = O.Hierarchy(dims)
+    stop = min(stop, H.L)
+    x = np.random.default_rng(7).integers(-2 ** 62, 2 ** 62, dims).astype(np.int64)
+    x.flat[0] = 2 ** 62 - 1
+    t = torch.from_numpy(x).cuda()
+    B.lorenzo(t, torch.float32, True, None, stop)
+    enc = t.cpu().numpy()
+    assert np.array_equal(enc, O.lorenzo_encode(x, H, stop))
+    B.lorenzo(t, torch.float32, False, None, stop)
+    assert np.array_equal(t.cpu().numpy(), x)
+
+
+def test_lorenzo_shrinks_a_smooth_coarse_part(cuda):
+    """A smooth 65^3 field kept whole (stop level = L, the coarse block is the
+    grid): the Lorenzo residuals of its labels pack several times smaller
+    than the labels themselves."""
+    torch = cuda
+    dims = (65, 65, 65)
+    H = O.Hierarchy(dims)
+    u = torch.from_numpy(F.sinusoid_field(dims, seed=2, kmax=2.0, noise=0.0).astype(np.float32)).cuda()
+    lo, hi = B.value_range(u)
+    labels, _ = B.quantize(u, 1e-4 * (hi - lo), None, H.L)
+    plain = B.pack_labels(labels.view(-1)).numel()
+    B.lorenzo(labels, torch.float32, True, None, H.L)
+    coded = B.pack_labels(labels.view(-1)).numel()
+    assert coded * 3 < plain
