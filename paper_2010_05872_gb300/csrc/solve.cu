@@ -90,15 +90,6 @@ solve_contig_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t n
   solve_contig_tile<T>(ax, F, B, nlines, rows, mode, blockIdx.x, smem_raw);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128)
-solve_contig_tma_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines,
-                        int rows, int mode, unsigned int* __restrict__ status) {
-  grid_dep_enter();
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  solve_contig_tma_tile<T>(ax, F, B, nlines, rows, mode, status, blockIdx.x, smem_raw);
-}
-
 // The per-level form keeps its own body (one 32-line group per CTA of
 // exactly nseg warps); solve_seg_tile is the same method for the persistent
 // batched kernel, with several groups side by side.
