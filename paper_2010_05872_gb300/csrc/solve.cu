@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128)
 solve_contig_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines, int rows,
                     int mode) {
   grid_dep_enter();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   solve_contig_tile<T>(ax, F, B, nlines, rows, mode, blockIdx.x, smem_raw);
 }
 
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(32 * kSegWarps, 2)
 solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines, int64_t S,
                  int64_t block_stride, int mode) {
   grid_dep_enter();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int nc = ax.nc, L = ax.seg_len;
   const int nseg = blockDim.x >> 5;
   T* s_tm = reinterpret_cast<T*>(smem_raw);
