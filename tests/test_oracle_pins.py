@@ -215,7 +215,8 @@ def _kron_all(mats):
 
 
 @pytest.mark.parametrize("dims,nonuni", [((9, 9), False), ((8, 6), True), ((5, 6, 7), True),
-                                         ((9, 5, 9), False), ((4, 4, 4), True)])
+                                         ((9, 5, 9), False), ((4, 4, 4), True),
+                                         ((5, 4, 5, 6), True), ((5, 5, 5, 5), False)])
 def test_dense_kronecker_projection(dims, nonuni):
     """Q_{l-1} w equals the dense Galerkin projection with the full
     tensor-product matrices: (P^T M P)^{-1} P^T M w (numpy.linalg.solve)."""
@@ -752,3 +753,25 @@ def test_lorenzo_round_trip_and_scope(dims, stop):
     mask = np.zeros(dims, dtype=bool)
     mask[np.ix_(*H.index[stop])] = True
     assert np.array_equal(e[~mask], x[~mask])
+
+
+
+# ----------------------------------------------------------- 4D grids ---
+
+@pytest.mark.parametrize("dims", [(9, 5, 7, 6), (17, 9, 9, 5)])
+def test_4d_multilinear_zero_coefficients_and_identity(dims):
+    # The 4D hierarchy (QMCPACK's shape class, Section 6): multilinear input
+    # has zero coefficients at every level; decompose-then-recompose is the
+    # identity to 1e-12.
+    coords = [F.geometric_coords(n, 1.05) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    u = F.multilinear_field(dims, coords)
+    umc = O.decompose(u, H, 0)
+    lev = O.node_levels(H)
+    assert np.abs(umc[lev > 0]).max() < 1e-12
+    x = _rng(4).standard_normal(dims)
+    r = O.recompose(O.decompose(x, H, 0), H, 0)
+    assert np.abs(r - x).max() <= 1e-12 * np.abs(x).max()
+    # kappa = sqrt(2^4) = 4 between consecutive level tolerances.
+    t = O.level_tolerances(H, 0, 1.0)
+    np.testing.assert_allclose(t[1:] / t[:-1], 4.0, rtol=1e-13)
