@@ -297,6 +297,42 @@ int mgard_decompress_host_packed(int ndim, const int64_t* dims, const double* co
                                  size_t dev_capacity, void* workspace, size_t ws_bytes,
                                  void* stream);
 
+/* Four-dimensional grids (the tensor-product hierarchy of Section 2 with
+ * d = 4; QMCPACK's data in Section 6 has this shape class).  dims[4] gives
+ * the axes, slowest first (C order), each in 3..2^20 nodes; coords is NULL
+ * (uniform) or four arrays of strictly increasing coordinates.  The
+ * hierarchy halves every axis together, n -> n / 2 + 1, while the smallest
+ * axis has more than 3 nodes; mgard_num_levels_4d gives its L.
+ * mgard_decompose_4d / mgard_recompose_4d overwrite `data` (device, dtype
+ * elements) in place with u_mc (the same layout as the 1-3D calls: the
+ * coefficients at their nodes, Q_{l~}u at the nodes of N_{l~}) and back; the
+ * workspace (device, 256-byte aligned, mgard_workspace_size_4d bytes) holds
+ * the compact grids of the levels below L and four arrays of #N_L elements.
+ * They run a plain axis-by-axis form of the method (a gather, four
+ * interpolation passes, four restriction passes and four Thomas passes per
+ * level), not the fused 1-3D kernels.  mgard_level_tolerances_4d writes the
+ * L+1 tolerances of Eq. (LinfTau) with kappa = sqrt(2^4) = 4 and the C_Linf
+ * bound of the four axes (entries below stop_level repeat tau_{l~}).
+ * mgard_quantize_4d / mgard_dequantize_4d are the level-wise quantizer and
+ * its inverse on a 4D u_mc (labels int64, device; bin width 2 tau_l in FP64);
+ * both wait for the stream; quantize returns MGARD_ERR_NONFINITE /
+ * MGARD_ERR_OVERFLOW as mgard_quantize does.  Errors: MGARD_ERR_SHAPE for
+ * an axis outside 3..2^20 or more than 2^40 nodes, MGARD_ERR_COORDS,
+ * MGARD_ERR_LEVEL, MGARD_ERR_WORKSPACE, MGARD_ERR_ARG as for the 1-3D calls. */
+int mgard_num_levels_4d(const int64_t* dims, int* L_out);
+int mgard_workspace_size_4d(const int64_t* dims, int dtype, size_t* bytes);
+int mgard_level_tolerances_4d(const int64_t* dims, const double* const* coords, int stop_level,
+                              double tau_linf, double* tau_out);
+int mgard_decompose_4d(const int64_t* dims, const double* const* coords, int dtype, int stop_level,
+                       void* data, void* workspace, size_t ws_bytes, void* stream);
+int mgard_recompose_4d(const int64_t* dims, const double* const* coords, int dtype, int stop_level,
+                       void* data, void* workspace, size_t ws_bytes, void* stream);
+int mgard_quantize_4d(const int64_t* dims, const double* const* coords, int dtype, int stop_level,
+                      double tau_linf, const void* coeffs, int64_t* labels, double* tau_levels_out,
+                      void* stream);
+int mgard_dequantize_4d(const int64_t* dims, const double* const* coords, int dtype, int stop_level,
+                        double tau_linf, const int64_t* labels, void* coeffs, void* stream);
+
 /* Free every cached plan (device tables included) of the current device. */
 int mgard_release_plans(void);
 

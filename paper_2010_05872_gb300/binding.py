@@ -89,6 +89,17 @@ _SIGNATURES = {
     "mgard_decompress_host": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_double, _VP, _VP, _VP, _VP, _VP,
                                              ctypes.c_size_t, _VP]),
+    "mgard_num_levels_4d": (ctypes.c_int, [_I64P, ctypes.POINTER(ctypes.c_int)]),
+    "mgard_workspace_size_4d": (ctypes.c_int, [_I64P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "mgard_level_tolerances_4d": (ctypes.c_int, [_I64P, _DPP, ctypes.c_int, ctypes.c_double, _DP]),
+    "mgard_decompose_4d": (ctypes.c_int, [_I64P, _DPP, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                                          ctypes.c_size_t, _VP]),
+    "mgard_recompose_4d": (ctypes.c_int, [_I64P, _DPP, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                                          ctypes.c_size_t, _VP]),
+    "mgard_quantize_4d": (ctypes.c_int, [_I64P, _DPP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         _VP, _VP, _DP, _VP]),
+    "mgard_dequantize_4d": (ctypes.c_int, [_I64P, _DPP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           _VP, _VP, _VP]),
     "mgard_release_plans": (ctypes.c_int, []),
     "mgard_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mgard_decompose_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
@@ -441,6 +452,60 @@ def mgard_decompress_host_packed(dims, coords, dtype, stop_level, tau, host_stre
                                               stream)
 
 
+def _shape4(dims, coords):
+    if len(dims) != 4:
+        raise ValueError("a 4D grid needs four axes")
+    return _Shape(dims, coords)
+
+
+def mgard_num_levels_4d(dims) -> int:
+    s = _shape4(dims, None)
+    L = ctypes.c_int()
+    _check(lib().mgard_num_levels_4d(s.dims, ctypes.byref(L)), "mgard_num_levels_4d")
+    return L.value
+
+
+def mgard_workspace_size_4d(dims, dtype: int) -> int:
+    s = _shape4(dims, None)
+    b = ctypes.c_size_t()
+    _check(lib().mgard_workspace_size_4d(s.dims, dtype, ctypes.byref(b)), "mgard_workspace_size_4d")
+    return b.value
+
+
+def mgard_level_tolerances_4d(dims, coords, stop_level: int, tau: float) -> np.ndarray:
+    s = _shape4(dims, coords)
+    out = np.zeros(mgard_num_levels_4d(dims) + 1)
+    _check(lib().mgard_level_tolerances_4d(s.dims, s.coords, stop_level, float(tau),
+                                           out.ctypes.data_as(_DP)), "mgard_level_tolerances_4d")
+    return out
+
+
+def mgard_decompose_4d(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:
+    s = _shape4(dims, coords)
+    return lib().mgard_decompose_4d(s.dims, s.coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes,
+                                    stream)
+
+
+def mgard_recompose_4d(dims, coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes, stream) -> int:
+    s = _shape4(dims, coords)
+    return lib().mgard_recompose_4d(s.dims, s.coords, dtype, stop_level, data_ptr, ws_ptr, ws_bytes,
+                                    stream)
+
+
+def mgard_quantize_4d(dims, coords, dtype, stop_level, tau, coeffs_ptr, labels_ptr, stream):
+    s = _shape4(dims, coords)
+    taus = np.zeros(mgard_num_levels_4d(dims) + 1)
+    rc = lib().mgard_quantize_4d(s.dims, s.coords, dtype, stop_level, float(tau), coeffs_ptr,
+                                 labels_ptr, taus.ctypes.data_as(_DP), stream)
+    return rc, taus
+
+
+def mgard_dequantize_4d(dims, coords, dtype, stop_level, tau, labels_ptr, coeffs_ptr, stream) -> int:
+    s = _shape4(dims, coords)
+    return lib().mgard_dequantize_4d(s.dims, s.coords, dtype, stop_level, float(tau), labels_ptr,
+                                     coeffs_ptr, stream)
+
+
 def mgard_release_plans() -> int:
     return lib().mgard_release_plans()
 
@@ -770,3 +835,57 @@ def value_range(x, stream=None):
     rc, out = mgard_value_range(x.numel(), dtype_code(x), x.data_ptr(), _stream(stream))
     _check(rc, "mgard_value_range")
     return float(out[0]), float(out[1])
+
+
+# ---------------------------------------------------------------- 4D grids ---
+
+def workspace_4d(shape, dtype, device=None):
+    """A device workspace tensor of the size the 4D transform needs."""
+    torch = _torch()
+    code = dtype if isinstance(dtype, int) else dtype_code(torch.empty(0, dtype=dtype))
+    nbytes = mgard_workspace_size_4d(shape, code)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def decompose_4d(x, coords=None, stop_level: int = 0, ws=None, stream=None):
+    """In-place multilevel decomposition of a 4D CUDA tensor (returns it)."""
+    _cuda_tensor(x, "x")
+    if ws is None:
+        ws = workspace_4d(x.shape, x.dtype, x.device)
+    _check(mgard_decompose_4d(x.shape, coords, dtype_code(x), stop_level, x.data_ptr(),
+                              ws.data_ptr(), ws.numel(), _stream(stream)), "mgard_decompose_4d")
+    return x
+
+
+def recompose_4d(x, coords=None, stop_level: int = 0, ws=None, stream=None):
+    """In-place multilevel recomposition of a 4D CUDA tensor (returns it)."""
+    _cuda_tensor(x, "x")
+    if ws is None:
+        ws = workspace_4d(x.shape, x.dtype, x.device)
+    _check(mgard_recompose_4d(x.shape, coords, dtype_code(x), stop_level, x.data_ptr(),
+                              ws.data_ptr(), ws.numel(), _stream(stream)), "mgard_recompose_4d")
+    return x
+
+
+def quantize_4d(coeffs, tau: float, coords=None, stop_level: int = 0, labels=None, stream=None):
+    """Level-wise labels of a 4D u_mc and the tolerances tau_0..tau_L."""
+    torch = _torch()
+    _cuda_tensor(coeffs, "coeffs")
+    if labels is None:
+        labels = torch.empty(coeffs.shape, dtype=torch.int64, device=coeffs.device)
+    rc, taus = mgard_quantize_4d(coeffs.shape, coords, dtype_code(coeffs), stop_level, tau,
+                                 coeffs.data_ptr(), labels.data_ptr(), _stream(stream))
+    _check(rc, "mgard_quantize_4d")
+    return labels, taus
+
+
+def dequantize_4d(labels, tau: float, dtype, coords=None, stop_level: int = 0, out=None,
+                  stream=None):
+    torch = _torch()
+    _cuda_tensor(labels, "labels")
+    if out is None:
+        out = torch.empty(labels.shape, dtype=dtype, device=labels.device)
+    _check(mgard_dequantize_4d(labels.shape, coords, dtype_code(out), stop_level, tau,
+                               labels.data_ptr(), out.data_ptr(), _stream(stream)),
+           "mgard_dequantize_4d")
+    return out

@@ -1073,6 +1073,7 @@ int mgard_release_plans(void) {
     if (it->second->device == device) it = g_plans.erase(it);
     else ++it;
   }
+  release_plans4(device);
   return MGARD_OK;
 }
 

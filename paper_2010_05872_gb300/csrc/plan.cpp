@@ -302,6 +302,8 @@ int build_host_plan(int ndim, const int64_t* dims, const double* const* coords, 
   return MGARD_OK;
 }
 
+void build_axis_tables(const std::vector<double>& x, AxisTables& t) { build_axis(x, t); }
+
 double linf_constant(const HostPlan& p, int stop_level) {
   double C = 1.0;
   for (int l = stop_level + 1; l <= p.L; ++l) C = std::max(C, 1.0 + p.knorm[l]);

@@ -60,6 +60,13 @@ int count_levels(int ndim, const int64_t* dims, int* L);
 int build_host_plan(int ndim, const int64_t* dims, const double* const* coords, HostPlan& out);
 
 double linf_constant(const HostPlan& p, int stop_level);
+// The tables of one axis of a level transition from the level's coordinates
+// (used directly by the 4D path).
+void build_axis_tables(const std::vector<double>& x, AxisTables& t);
+
+// Free the cached 4D plans of one device (the 4D grids keep their own cache).
+void release_plans4(int device);
+
 // tau_out receives L+1 values (entries below stop_level repeat tau_{stop}).
 void level_tolerances(const HostPlan& p, int stop_level, double tau, double* tau_out);
 // mode 0: the geometric rule above; 1: L-inf-optimal widths (tau_l

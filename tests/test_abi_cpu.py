@@ -121,3 +121,42 @@ def test_level_tolerance_modes_match_oracle(lib, dims, kind, stop, mode):
     got = B.mgard_level_tolerances_mode(dims, coords, stop, 0.7, mode)
     exp = O.level_tolerances_mode(H, stop, 0.7, mode)
     np.testing.assert_allclose(got, exp, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3, 3), (9, 5, 7, 6), (17, 17, 17, 17), (33, 9, 100, 12),
+                                  (115, 69, 69, 288)])
+def test_levels_4d_match_oracle(lib, dims):
+    assert B.mgard_num_levels_4d(dims) == O.Hierarchy(dims).L
+
+
+def test_workspace_size_4d(lib):
+    for dims in [(9, 5, 7, 6), (17, 17, 17, 17), (33, 9, 10, 12)]:
+        H = O.Hierarchy(dims)
+        for dtype, es in ((B.F32, 4), (B.F64, 8)):
+            need = es * (4 * int(np.prod(dims)) + sum(int(np.prod(H.levels[l])) for l in range(H.L)))
+            got = B.mgard_workspace_size_4d(dims, dtype)
+            assert need <= got <= need + 256 * (H.L + 4)
+            assert got % 256 == 0
+
+
+@pytest.mark.parametrize("dims,kind,stop", [((9, 9, 9, 9), "u", 0), ((17, 9, 10, 9), "g", 1),
+                                            ((12, 17, 9, 33), "g", 0), ((9, 5, 7, 6), "u", 1)])
+def test_level_tolerances_4d_match_oracle(lib, dims, kind, stop):
+    coords = None if kind == "u" else [F.geometric_coords(n, 1.04 + 0.01 * d) for d, n in enumerate(dims)]
+    got = B.mgard_level_tolerances_4d(dims, coords, stop, 1e-3)
+    exp = O.level_tolerances(O.Hierarchy(dims, coords), stop, 1e-3)
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=0)
+
+
+def test_argument_errors_4d(lib):
+    assert _rc(B.mgard_num_levels_4d, (2, 5, 5, 5)) == -2
+    assert _rc(B.mgard_level_tolerances_4d, (9, 9, 9, 9), None, 3, 1.0) == -4
+    assert _rc(B.mgard_level_tolerances_4d, (9, 9, 9, 9), None, 0, -1.0) == -1
+    bad = [None, np.array([0, 1, 2, 2, 3, 4, 5, 6, 7.0]), None, None]
+    assert _rc(B.mgard_level_tolerances_4d, (9, 9, 9, 9), bad, 0, 1.0) == -3
+    assert _rc(B.mgard_workspace_size_4d, (9, 9, 9, 9), 3) == -1
+    with pytest.raises(ValueError):
+        B.mgard_num_levels_4d((9, 9, 9))
+    # Shape and dtype errors are reported before any CUDA call.
+    assert B.mgard_decompose_4d((9, 2, 9, 9), None, B.F32, 0, 0, 0, 0, 0) == -2
+    assert B.mgard_recompose_4d((9, 9, 9, 9), None, 5, 0, 0, 0, 0, 0) == -1
