@@ -307,17 +307,18 @@ int mgard_decompress_host_packed(int ndim, const int64_t* dims, const double* co
  * elements) in place with u_mc (the same layout as the 1-3D calls: the
  * coefficients at their nodes, Q_{l~}u at the nodes of N_{l~}) and back; the
  * workspace (device, 256-byte aligned, mgard_workspace_size_4d bytes) holds
- * the compact grids of the levels below L and four arrays of #N_L elements.
- * They run a plain axis-by-axis form of the method (a gather, four
- * interpolation passes, four restriction passes and four Thomas passes per
- * level), not the fused 1-3D kernels.  mgard_level_tolerances_4d writes the
+ * the compact grids of the levels below L, two arrays of #N_L elements and
+ * one of #N_{L-1}.  Per level they run one pass that forms the coefficients
+ * in place (the interpolant from up to 16 coarse nodes) or adds the
+ * interpolant back, four restriction passes and four Thomas passes (the
+ * operators applied axis by axis), not the fused 1-3D kernels.  mgard_level_tolerances_4d writes the
  * L+1 tolerances of Eq. (LinfTau) with kappa = sqrt(2^4) = 4 and the C_Linf
  * bound of the four axes (entries below stop_level repeat tau_{l~}).
  * mgard_quantize_4d / mgard_dequantize_4d are the level-wise quantizer and
  * its inverse on a 4D u_mc (labels int64, device; bin width 2 tau_l in FP64);
  * both wait for the stream; quantize returns MGARD_ERR_NONFINITE /
  * MGARD_ERR_OVERFLOW as mgard_quantize does.  Errors: MGARD_ERR_SHAPE for
- * an axis outside 3..2^20 or more than 2^40 nodes, MGARD_ERR_COORDS,
+ * an axis outside 3..2^20 or 2^31 nodes or more (32-bit index arithmetic), MGARD_ERR_COORDS,
  * MGARD_ERR_LEVEL, MGARD_ERR_WORKSPACE, MGARD_ERR_ARG as for the 1-3D calls. */
 int mgard_num_levels_4d(const int64_t* dims, int* L_out);
 int mgard_workspace_size_4d(const int64_t* dims, int dtype, size_t* bytes);

@@ -133,7 +133,8 @@ def test_workspace_size_4d(lib):
     for dims in [(9, 5, 7, 6), (17, 17, 17, 17), (33, 9, 10, 12)]:
         H = O.Hierarchy(dims)
         for dtype, es in ((B.F32, 4), (B.F64, 8)):
-            need = es * (4 * int(np.prod(dims)) + sum(int(np.prod(H.levels[l])) for l in range(H.L)))
+            need = es * (2 * int(np.prod(dims)) + int(np.prod(H.levels[max(H.L - 1, 0)]))
+                         + sum(int(np.prod(H.levels[l])) for l in range(H.L)))
             got = B.mgard_workspace_size_4d(dims, dtype)
             assert need <= got <= need + 256 * (H.L + 4)
             assert got % 256 == 0
@@ -160,3 +161,10 @@ def test_argument_errors_4d(lib):
     # Shape and dtype errors are reported before any CUDA call.
     assert B.mgard_decompose_4d((9, 2, 9, 9), None, B.F32, 0, 0, 0, 0, 0) == -2
     assert B.mgard_recompose_4d((9, 9, 9, 9), None, 5, 0, 0, 0, 0, 0) == -1
+
+
+def test_node_limit_4d(lib):
+    # 4D grids index in 32 bits: 2^31 nodes or more is a shape error.
+    assert _rc(B.mgard_num_levels_4d, (2048, 1024, 1024, 3)) == -2
+    assert B.mgard_num_levels_4d((1024, 1024, 682, 3)) == O.Hierarchy((1024, 1024, 682, 3)).L
+    assert _rc(B.mgard_workspace_size_4d, (1024, 1024, 1024, 3), B.F32) == -2
