@@ -60,7 +60,8 @@ def parse_args():
     ap.add_argument("--case-dims", default="513x513x513", help=argparse.SUPPRESS)
     ap.add_argument("--batch-count", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", action="store_true",
-                    help="only decompose+recompose of the 513^3 FP32 field (for ncu captures)")
+                    help="only one compression round trip of a --case-dims FP32 field, 3D or "
+                         "4D (for ncu captures)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-reps", type=int, default=3, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -521,6 +522,56 @@ def run_gpu(args, rank, world, local_rank):
             "area": area, "area_rel_diff_vs_full": area / area_full - 1.0}
     x.copy_(u)
 
+    # 4D grids (QMCPACK's shape, 288 x 115 x 69 x 69 FP32): the time of
+    # the decomposition and recomposition, and one compressed round trip at
+    # 1e-3 x range (labels packed for the rate).
+    dims4 = (288, 115, 69, 69)
+    u4 = F.grf_field_device(dims4, seed=F.SEED_LARGE + 4 + rank, device=dev)
+    x4 = u4.clone()
+    ws4 = B.workspace_4d(dims4, torch.float32, dev)
+    nb4 = u4.numel() * 4
+    B.decompose_4d(x4, None, 0, ws4)
+    B.recompose_4d(x4, None, 0, ws4)
+    t_d4, t_r4 = [], []
+    for i in range(5):
+        x4.copy_(u4)
+        ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        ea.record(stream)
+        B.decompose_4d(x4, None, 0, ws4)
+        eb.record(stream)
+        B.recompose_4d(x4, None, 0, ws4)
+        ec.record(stream)
+        torch.cuda.synchronize()
+        t_d4.append(ea.elapsed_time(eb))
+        t_r4.append(eb.elapsed_time(ec))
+    md4, mr4 = statistics.median(t_d4), statistics.median(t_r4)
+    lo4, hi4 = B.value_range(u4)
+    tau4 = 1e-3 * (hi4 - lo4)
+    x4.copy_(u4)
+    B.decompose_4d(x4, None, 0, ws4)
+    lab4, _ = B.quantize_4d(x4, tau4)
+    pk4 = B.pack_labels(lab4)
+    B.dequantize_4d(lab4, tau4, torch.float32, out=x4)
+    B.recompose_4d(x4, None, 0, ws4)
+    err4 = float((x4.double() - u4.double()).abs().max().item())
+    peak4, _ = measured_peak()
+    sizes4, n4 = [], list(dims4)
+    while min(n4) > 3:
+        sizes4.append(int(np.prod(n4)))
+        n4 = [v // 2 + 1 for v in n4]
+    b_alg4 = 2 * 2 * 4 * sum(sizes4)
+    nd4 = {"dims": list(dims4), "levels": B.mgard_num_levels_4d(dims4),
+           "decompose_ms": md4, "recompose_ms": mr4,
+           "dec_rec_gbs": nb4 / ((md4 + mr4) * 1e-3) / 1e9,
+           "path_roofline_frac_dec_rec": b_alg4 / ((md4 + mr4) * 1e-3) / 1e9 / peak4,
+           "bits_per_value_1e-3": 8.0 * len(pk4) / u4.numel(),
+           "linf_over_tau_1e-3": err4 / tau4,
+           "note": ("median of 5 runs; dec_rec_gbs = field bytes / (decompose + recompose) as "
+                    "for 1-3D; path fraction = one read and one write of every decomposed level "
+                    "per transform over the time, of measured HBM; synthetic k^-5/3 Gaussian "
+                    "random field")}
+    del u4, x4, ws4, lab4, pk4
+
     # End to end through the host-buffer entry points: the packed path (the
     # labels' lossless stream crosses the link) is the headline, the int64
     # label path beside it.
@@ -628,6 +679,7 @@ def run_gpu(args, rank, world, local_rank):
         "fp64": fp64,
         "adaptive": adaptive,
         "progressive": progressive,
+        "nd4": nd4,
         "linf_over_tau": linf,
         "top_kernels": kernels,
         "kinds_ms_per_step": {k: round(v, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1])},
@@ -647,12 +699,22 @@ def run_kernel_case(args):
     from paper_2010_05872_gb300 import fields as F
     build_mod.build()
     dims = tuple(int(v) for v in args.case_dims.split("x"))
-    u = torch.from_numpy(F.grf_field(dims, seed=F.SEED_LARGE)).cuda()
-    ws = B.workspace(dims, torch.float32)
+    if len(dims) == 4:
+        u = F.grf_field_device(dims, seed=F.SEED_LARGE + 4)
+        ws = B.workspace_4d(dims, torch.float32)
+    else:
+        u = torch.from_numpy(F.grf_field(dims, seed=F.SEED_LARGE)).cuda()
+        ws = B.workspace(dims, torch.float32)
     x = u.clone()
 
     def step():
         lo, hi = B.value_range(x)
+        if len(dims) == 4:
+            B.decompose_4d(x, None, 0, ws)
+            labels, _ = B.quantize_4d(x, 1e-3 * (hi - lo))
+            B.dequantize_4d(labels, 1e-3 * (hi - lo), torch.float32, out=x)
+            B.recompose_4d(x, None, 0, ws)
+            return
         B.decompose(x, None, 0, ws)
         labels, _ = B.quantize(x, 1e-3 * (hi - lo))
         B.dequantize(labels, 1e-3 * (hi - lo), torch.float32, out=x)
