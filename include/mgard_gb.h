@@ -315,9 +315,10 @@ int mgard_decompress_host_packed(int ndim, const int64_t* dims, const double* co
  * L+1 tolerances of Eq. (LinfTau) with kappa = sqrt(2^4) = 4 and the C_Linf
  * bound of the four axes (entries below stop_level repeat tau_{l~}).
  * mgard_quantize_4d / mgard_dequantize_4d are the level-wise quantizer and
- * its inverse on a 4D u_mc (labels int64, device; bin width 2 tau_l in FP64);
- * both wait for the stream; quantize returns MGARD_ERR_NONFINITE /
- * MGARD_ERR_OVERFLOW as mgard_quantize does.  Errors: MGARD_ERR_SHAPE for
+ * its inverse on a 4D u_mc (labels int64, device; bin width 2 tau_l, labels
+ * and values exactly those of the FP64 definition, as for 1-3D); quantize
+ * waits for the stream and returns MGARD_ERR_NONFINITE / MGARD_ERR_OVERFLOW
+ * as mgard_quantize does; dequantize is enqueued on the stream.  Errors: MGARD_ERR_SHAPE for
  * an axis outside 3..2^20 or 2^31 nodes or more (32-bit index arithmetic), MGARD_ERR_COORDS,
  * MGARD_ERR_LEVEL, MGARD_ERR_WORKSPACE, MGARD_ERR_ARG as for the 1-3D calls. */
 int mgard_num_levels_4d(const int64_t* dims, int* L_out);

@@ -429,8 +429,12 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
 
 int make_table_levels(const DevPlan& p, int stop_level, const double* t, LevelTable& tab,
                       double* tau_out) {
-  if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
-  for (int l = stop_level; l <= p.h.L; ++l)
+  return make_level_table(p.h.L, stop_level, t, tab, tau_out);
+}
+
+int make_level_table(int L, int stop_level, const double* t, LevelTable& tab, double* tau_out) {
+  if (stop_level < 0 || stop_level > L) return MGARD_ERR_LEVEL;
+  for (int l = stop_level; l <= L; ++l)
     if (!(t[l] > 0.0) || !std::isfinite(t[l])) return MGARD_ERR_ARG;
   for (int l = 0; l < 48; ++l) {
     tab.q[l] = 1.0;
@@ -438,7 +442,7 @@ int make_table_levels(const DevPlan& p, int stop_level, const double* t, LevelTa
     tab.qf[l] = 1.0f;
     tab.dqf[l] = 0.0f;
   }
-  for (int l = 0; l <= p.h.L; ++l) {
+  for (int l = 0; l <= L; ++l) {
     // Levels below the stopping level are quantized with tau_{l~}.
     tab.q[l] = 2.0 * t[std::max(l, stop_level)];
     // The FP32 reciprocal drives the exact fast path of the quantizer; it is
@@ -454,7 +458,7 @@ int make_table_levels(const DevPlan& p, int stop_level, const double* t, LevelTa
     tab.dqf[l] = qok ? static_cast<float>(tab.q[l] - static_cast<double>(qf)) : 0.0f;
   }
   if (tau_out)
-    for (int l = 0; l <= p.h.L; ++l) tau_out[l] = t[std::max(l, stop_level)];
+    for (int l = 0; l <= L; ++l) tau_out[l] = t[std::max(l, stop_level)];
   return MGARD_OK;
 }
 

@@ -76,5 +76,7 @@ int make_table(const DevPlan& p, int stop_level, double tau, LevelTable& tab, do
 // must be positive and finite).
 int make_table_levels(const DevPlan& p, int stop_level, const double* t, LevelTable& tab,
                       double* tau_out);
+// The same for any hierarchy of L + 1 levels.
+int make_level_table(int L, int stop_level, const double* t, LevelTable& tab, double* tau_out);
 
 }  // namespace mgb

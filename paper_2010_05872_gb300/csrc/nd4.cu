@@ -29,6 +29,7 @@
 
 #include <cuda_runtime.h>
 
+#include "devplan.hpp"
 #include "mgard_gb.h"
 #include "pdl.cuh"
 #include "plan.hpp"
@@ -441,54 +442,6 @@ axpy4_kernel(T* __restrict__ out, const T* __restrict__ a, const T* __restrict__
   GRID_LOOP(t, n) out[t] = a[t] + s * b[t];
 }
 
-// Level-wise quantization / dequantization of a 4D array: the level of a
-// node is the largest of its axes' levels, raised to the stopping level;
-// label = round(x / q_l) ties away from zero in FP64, value = label q_l.
-template <typename T>
-__global__ void __launch_bounds__(kT)
-quantize4_kernel(const T* __restrict__ x, int64_t* __restrict__ labels, Shape4 s,
-                 const uint8_t* __restrict__ l0, const uint8_t* __restrict__ l1,
-                 const uint8_t* __restrict__ l2, const uint8_t* __restrict__ l3, int stop,
-                 const double* __restrict__ q, unsigned int* __restrict__ flags) {
-  grid_dep_enter();
-  const uint32_t total = static_cast<uint32_t>(s.count());
-  GRID_LOOP(t, total) {
-    int j[4];
-    unflat(t, s, j);
-    const int lev = max(max(max(int(l0[j[0]]), int(l1[j[1]])), max(int(l2[j[2]]), int(l3[j[3]]))), stop);
-    const double v = static_cast<double>(x[t]);
-    if (!isfinite(v)) {
-      atomicOr(flags, 1u);
-      labels[t] = 0;
-      continue;
-    }
-    const double y = v / q[lev];
-    if (!(fabs(y) < 4611686018427387904.0)) {  // 2^62
-      atomicOr(flags, 2u);
-      labels[t] = 0;
-      continue;
-    }
-    const double tr = trunc(y);
-    labels[t] = static_cast<int64_t>(tr) + (fabs(y - tr) >= 0.5 ? (y < 0 ? -1 : 1) : 0);
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kT)
-dequantize4_kernel(const int64_t* __restrict__ labels, T* __restrict__ x, Shape4 s,
-                   const uint8_t* __restrict__ l0, const uint8_t* __restrict__ l1,
-                   const uint8_t* __restrict__ l2, const uint8_t* __restrict__ l3, int stop,
-                   const double* __restrict__ q) {
-  grid_dep_enter();
-  const uint32_t total = static_cast<uint32_t>(s.count());
-  GRID_LOOP(t, total) {
-    int j[4];
-    unflat(t, s, j);
-    const int lev = max(max(max(int(l0[j[0]]), int(l1[j[1]])), max(int(l2[j[2]]), int(l3[j[3]]))), stop);
-    x[t] = static_cast<T>(static_cast<double>(labels[t]) * q[lev]);
-  }
-}
-
 #undef GRID_LOOP
 
 // ------------------------------------------------------------------ plan
@@ -504,9 +457,9 @@ struct Plan4 {
   std::vector<std::array<Ax4, 4>> ax;   // [L+1], entry l = transition l -> l-1
   std::vector<double> knorm;            // [L+1]
   std::vector<double> hd;               // [L+1] largest hat-integral products (unused here)
-  std::array<std::vector<uint8_t>, 4> lev;
-  size_t lev_off[4] = {0, 0, 0, 0};
-  size_t q_off = 0;                     // kMaxLevels doubles of bin widths (per call)
+  std::array<std::vector<uint8_t>, 4> lev;  // per finest index of an axis: least level holding it
+  size_t lev012_off = 0;  // per row (j0, j1, j2): the largest of its three axes' levels
+  size_t lev3_off = 0;    // per index of axis 3
   void* dmem = nullptr;
   std::vector<size_t> offB;             // compact level grids l < L
   size_t off_buf[3] = {0, 0, 0};        // scratch: two of #N_L elements, one of #N_{L-1}
@@ -611,10 +564,16 @@ int build_plan4(const int64_t* dims, const double* const* coords, Plan4& p, bool
     p.lev[a].assign(dims[a], static_cast<uint8_t>(L));
     for (int l = L - 1; l >= 0; --l)
       for (int64_t j : idx[l][a]) p.lev[a][j] = static_cast<uint8_t>(l);
-    p.lev_off[a] = reserve(p.lev[a].size());
   }
-  p.q_off = reserve(sizeof(double) * kMaxLevels);
   if (!upload) return MGARD_OK;
+  // The quantizer sees the array as rows (j0, j1, j2) of n3 elements.
+  std::vector<uint8_t> lev012(static_cast<size_t>(dims[0] * dims[1] * dims[2]));
+  for (int64_t j0 = 0, r = 0; j0 < dims[0]; ++j0)
+    for (int64_t j1 = 0; j1 < dims[1]; ++j1)
+      for (int64_t j2 = 0; j2 < dims[2]; ++j2, ++r)
+        lev012[r] = std::max(std::max(p.lev[0][j0], p.lev[1][j1]), p.lev[2][j2]);
+  p.lev012_off = reserve(lev012.size());
+  p.lev3_off = reserve(p.lev[3].size());
   std::vector<char> stage(total, 0);
   auto put = [&](size_t off, const std::vector<double>& v) {
     T* dst = reinterpret_cast<T*>(stage.data() + off);
@@ -627,7 +586,8 @@ int build_plan4(const int64_t* dims, const double* const* coords, Plan4& p, bool
       put(g.off[0], t.iwl); put(g.off[1], t.iwr); put(g.off[2], t.rw);
       put(g.off[3], t.ta); put(g.off[4], t.tm); put(g.off[5], t.tc);
     }
-  for (int a = 0; a < 4; ++a) std::memcpy(stage.data() + p.lev_off[a], p.lev[a].data(), p.lev[a].size());
+  std::memcpy(stage.data() + p.lev012_off, lev012.data(), lev012.size());
+  std::memcpy(stage.data() + p.lev3_off, p.lev[3].data(), p.lev[3].size());
   if (cudaMalloc(&p.dmem, total) != cudaSuccess) return MGARD_ERR_CUDA;
   if (cudaMemcpy(p.dmem, stage.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) return MGARD_ERR_CUDA;
   // Workspace: compact grids of the levels below L, then four scratch arrays.
@@ -845,47 +805,41 @@ int quant4(bool quantize, const int64_t* dims, const double* const* coords, int 
   if (coeffs == nullptr || labels == nullptr || reinterpret_cast<uintptr_t>(coeffs) % es ||
       reinterpret_cast<uintptr_t>(labels) % 8)
     return MGARD_ERR_ARG;
-  double t[kMaxLevels], q[kMaxLevels];
+  double t[kMaxLevels];
   level_tolerances4(*p, stop, tau, t);
-  for (int l = 0; l < kMaxLevels; ++l) q[l] = l <= p->L ? 2.0 * t[l] : 1.0;
-  if (tau_out)
-    for (int l = 0; l <= p->L; ++l) tau_out[l] = t[l];
+  LevelTable tab;
+  rc = make_level_table(p->L, stop, t, tab, tau_out);
+  if (rc != MGARD_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  std::lock_guard<std::mutex> lk(g_mu4);  // the bin-width slot of the plan
-  char* base = static_cast<char*>(p->dmem);
-  double* dq = reinterpret_cast<double*>(base + p->q_off);
-  if (cudaMemcpyAsync(dq, q, sizeof q, cudaMemcpyHostToDevice, s) != cudaSuccess) return MGARD_ERR_CUDA;
-  const uint8_t* lv[4];
-  for (int a = 0; a < 4; ++a) lv[a] = reinterpret_cast<const uint8_t*>(base + p->lev_off[a]);
-  const Shape4 sh = p->shape[p->L];
+  const char* base = static_cast<const char*>(p->dmem);
+  const uint8_t* lev012 = reinterpret_cast<const uint8_t*>(base + p->lev012_off);
+  const uint8_t* lev3 = reinterpret_cast<const uint8_t*>(base + p->lev3_off);
+  const int64_t rows = dims[0] * dims[1] * dims[2], n3 = dims[3];
+  // The quantizer kernels of the 1-3D path on the (rows, n3) view: the same
+  // exact fast paths and FP64 fallbacks.
   if (!quantize) {
-    if (dtype == MGARD_F64)
-      launch_pdl(dequantize4_kernel<double>, dim3(grid_of(sh.count())), dim3(kT), 0, s,
-                 static_cast<const int64_t*>(labels), static_cast<double*>(coeffs), sh, lv[0], lv[1],
-                 lv[2], lv[3], stop, static_cast<const double*>(dq));
-    else
-      launch_pdl(dequantize4_kernel<float>, dim3(grid_of(sh.count())), dim3(kT), 0, s,
-                 static_cast<const int64_t*>(labels), static_cast<float*>(coeffs), sh, lv[0], lv[1],
-                 lv[2], lv[3], stop, static_cast<const double*>(dq));
-    // The bin widths must outlive the launch: wait before the slot is reused.
-    return cudaStreamSynchronize(s) == cudaSuccess ? MGARD_OK : MGARD_ERR_CUDA;
+    const cudaError_t e =
+        dtype == MGARD_F64
+            ? launch_dequantize<double>(labels, static_cast<double*>(coeffs), lev012, lev3, rows, n3,
+                                        stop, tab, s)
+            : launch_dequantize<float>(labels, static_cast<float*>(coeffs), lev012, lev3, rows, n3,
+                                       stop, tab, s);
+    return e == cudaSuccess ? MGARD_OK : MGARD_ERR_CUDA;
   }
   unsigned int* flags = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&flags), sizeof(unsigned), s) != cudaSuccess)
     return MGARD_ERR_CUDA;
   cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
-  if (dtype == MGARD_F64)
-    launch_pdl(quantize4_kernel<double>, dim3(grid_of(sh.count())), dim3(kT), 0, s,
-               static_cast<const double*>(coeffs), labels, sh, lv[0], lv[1], lv[2], lv[3], stop,
-               static_cast<const double*>(dq), flags);
-  else
-    launch_pdl(quantize4_kernel<float>, dim3(grid_of(sh.count())), dim3(kT), 0, s,
-               static_cast<const float*>(coeffs), labels, sh, lv[0], lv[1], lv[2], lv[3], stop,
-               static_cast<const double*>(dq), flags);
+  const cudaError_t e =
+      dtype == MGARD_F64
+          ? launch_quantize<double>(static_cast<const double*>(coeffs), labels, lev012, lev3, rows, n3,
+                                    stop, tab, flags, s)
+          : launch_quantize<float>(static_cast<const float*>(coeffs), labels, lev012, lev3, rows, n3,
+                                   stop, tab, flags, s);
   unsigned h = 0;
   cudaMemcpyAsync(&h, flags, sizeof h, cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(flags, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return MGARD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess || e != cudaSuccess) return MGARD_ERR_CUDA;
   if (h & 1u) return MGARD_ERR_NONFINITE;
   if (h & 2u) return MGARD_ERR_OVERFLOW;
   return MGARD_OK;
