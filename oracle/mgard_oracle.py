@@ -46,6 +46,9 @@ explicit finite-element operators assembled from the grid coordinates:
   L2 error control.
 * The coarse part's Lorenzo coder (Algorithm 1 line 18): Lorenzo residuals
   of the coarse block's labels and their inverse.
+* The labels' order-0 entropy and the cost model of Section 4.1, and a
+  canonical Huffman coder of the labels (a reading of Algorithm 1 line 23's
+  lossless encoder, which the paper does not name).
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
 non-cubic shapes, the constant ``C_Linf``) are documented beside the functions
@@ -63,7 +66,10 @@ label stream by hand-derived bytes in tests/golden/packed_labels.txt and
 round trips; PSNR by a closed form; the L2 and L-inf-optimal rules by a
 closed form, their sums, and worst-case coefficient errors staying within
 the bound after recomposition; the Lorenzo coder by hand residuals and
-round trips).  The L2 rule's constant C_L2 = 1 is a
+round trips; the entropy and cost model by closed forms and a hand count;
+the Huffman coder by the textbook six-symbol example, brute-force optimal
+lengths on small alphabets, Kraft's equality, the entropy bound, hand
+streams in tests/golden/huffman_streams.txt and round trips).  The L2 rule's constant C_L2 = 1 is a
 reading (the paper gives no value), derived and pinned as a valid bound.
 ``linf_constant`` is a reading (the paper
 gives no value for ``C_Linf``); it is pinned only as a valid upper bound on the
@@ -820,3 +826,194 @@ def lorenzo_decode(labels: np.ndarray, H: Hierarchy, stop_level: int) -> np.ndar
         q = np.cumsum(q, axis=a, dtype=np.uint64)
     out[ix] = q.astype(np.int64)
     return out
+
+
+# --------------------------------------------------------------------------
+# Entropy of the labels and the cost model (Section 4.1), and a canonical
+# Huffman coder of the labels (a reading of Algorithm 1 line 23's lossless
+# encoder)
+# --------------------------------------------------------------------------
+
+def label_entropy(labels) -> float:
+    """Order-0 Shannon entropy of the labels in bits per label (Section 4.1
+    estimates the encoding cost with it): ``-sum_v p_v log2 p_v`` over the
+    distinct values, ``p_v`` their relative counts; 0 for no labels."""
+    k = np.asarray(labels, dtype=np.int64).ravel()
+    if k.size == 0:
+        return 0.0
+    _, cnt = np.unique(k, return_counts=True)
+    p = cnt.astype(np.float64) / k.size
+    return float(-(p * np.log2(p)).sum())
+
+
+def cost_model(H: Hierarchy, stop_level: int, taus, R: float) -> float:
+    """Estimated cost in bits of the level-wise labels, Section 4.1:
+    ``sum_l #N*_l log2(R / q_l)`` with ``q_l = 2 tau_l`` and R the range of
+    the multilevel coefficients (the coarse block N_{l~} counted at the
+    stopping level, as it is quantized with tau_{l~})."""
+    cnt = _level_counts(H, stop_level)
+    taus = np.asarray(taus, dtype=np.float64)
+    return float(sum(cnt[l] * math.log2(R / (2.0 * taus[l]))
+                     for l in range(stop_level, H.L + 1)))
+
+
+HUFF_CHUNK = 1024
+HUFF_K = 65536          # alphabet: zigzag codes 0 .. K-2, and K-1 = escape
+HUFF_MAXLEN = 31
+
+
+def huffman_lengths(counts) -> list:
+    """Code lengths of a Huffman code for symbol counts (0 = unused symbol).
+
+    Huffman's construction with a fixed order, so that the lengths are a
+    function of the counts alone: leaves sorted by (count, symbol), merged
+    nodes queued in the order they are made; each step takes the lighter of
+    the two queue heads, a leaf on a tie.  One used symbol gets length 1.  If
+    the longest code exceeds 31 bits, every used count c becomes
+    max(1, c // 2) and the code is rebuilt (a reading: the paper's coder has
+    no length limit; this keeps every code in 32 bits)."""
+    counts = [int(c) for c in counts]
+    while True:
+        used = sorted((c, s) for s, c in enumerate(counts) if c > 0)
+        lengths = [0] * len(counts)
+        if not used:
+            return lengths
+        if len(used) == 1:
+            lengths[used[0][1]] = 1
+            return lengths
+        parent = {}
+        leaves = [(c, ("leaf", s)) for c, s in used]
+        merged = []
+        li = mi = 0
+        nid = 0
+
+        def take():
+            nonlocal li, mi
+            if mi >= len(merged) or (li < len(leaves) and leaves[li][0] <= merged[mi][0]):
+                li += 1
+                return leaves[li - 1]
+            mi += 1
+            return merged[mi - 1]
+
+        while (len(leaves) - li) + (len(merged) - mi) > 1:
+            a = take()
+            b = take()
+            node = ("node", nid)
+            nid += 1
+            parent[a[1]] = node
+            parent[b[1]] = node
+            merged.append((a[0] + b[0], node))
+        for _, s in used:
+            d, x = 0, ("leaf", s)
+            while x in parent:
+                x = parent[x]
+                d += 1
+            lengths[s] = d
+        if max(lengths) <= HUFF_MAXLEN:
+            return lengths
+        counts = [max(1, c // 2) if c > 0 else 0 for c in counts]
+
+
+def huffman_codes(lengths) -> dict:
+    """Canonical codes: symbols ordered by (length, symbol) take consecutive
+    code values, the first of each length being (first of the previous
+    length + its count) shifted left by the length difference."""
+    order = sorted((L, s) for s, L in enumerate(lengths) if L > 0)
+    codes, code, prev = {}, 0, None
+    for L, s in order:
+        if prev is not None:
+            code = (code + 1) << (L - prev)
+        codes[s] = code
+        prev = L
+    return codes
+
+
+def _huff_symbol(z: int) -> int:
+    return z if z < HUFF_K - 1 else HUFF_K - 1
+
+
+def huffman_encode(labels) -> bytes:
+    """The labels' Huffman stream.  Each label is zigzag-coded; codes below
+    K - 1 are symbols, larger ones the escape symbol K - 1 with the code
+    itself stored in the escape list.  Layout (little-endian): uint64 N |
+    uint32 K | uint32 longest code length | uint64 number of escapes | K
+    bytes of code lengths | per chunk of 1024 labels a uint16 word count and
+    a uint16 escape count | zero padding to 8 bytes | per chunk its words:
+    each symbol's canonical code, most significant bit first, at increasing
+    bit positions from the least significant bit of the first word | the
+    escaped codes as uint64, in label order."""
+    z = [_zigzag(int(v)) for v in np.asarray(labels, dtype=np.int64).ravel()]
+    n = len(z)
+    sym = [_huff_symbol(v) for v in z]
+    counts = [0] * HUFF_K
+    for s in sym:
+        counts[s] += 1
+    lengths = huffman_lengths(counts)
+    codes = huffman_codes(lengths)
+    esc = [v for v in z if v >= HUFF_K - 1]
+    out = bytearray(n.to_bytes(8, "little"))
+    out += HUFF_K.to_bytes(4, "little") + max(lengths).to_bytes(4, "little")
+    out += len(esc).to_bytes(8, "little")
+    out += bytes(lengths)
+    payload = []
+    for c0 in range(0, n, HUFF_CHUNK):
+        bits, pos, ne = 0, 0, 0
+        for s in sym[c0:c0 + HUFF_CHUNK]:
+            L, code = lengths[s], codes[s]
+            for i in range(L):
+                bits |= ((code >> (L - 1 - i)) & 1) << (pos + i)
+            pos += L
+            ne += s == HUFF_K - 1
+        nwords = (pos + 63) // 64
+        out += nwords.to_bytes(2, "little") + ne.to_bytes(2, "little")
+        payload.append(bits.to_bytes(8 * nwords, "little"))
+    out += bytes((-len(out)) % 8)
+    for p in payload:
+        out += p
+    for v in esc:
+        out += v.to_bytes(8, "little")
+    return bytes(out)
+
+
+def huffman_decode(buf: bytes) -> np.ndarray:
+    """Inverse of :func:`huffman_encode`: read code bits one at a time; a
+    code of length L is complete when it falls among the canonical codes of
+    that length."""
+    buf = bytes(buf)
+    n = int.from_bytes(buf[0:8], "little")
+    K = int.from_bytes(buf[8:12], "little")
+    nesc = int.from_bytes(buf[16:24], "little")
+    lengths = list(buf[24:24 + K])
+    codes = huffman_codes(lengths)
+    lookup = {(lengths[s], c): s for s, c in codes.items()}
+    nchunks = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
+    off = 24 + K
+    words = []
+    for c in range(nchunks):
+        words.append(int.from_bytes(buf[off:off + 2], "little"))
+        off += 4
+    off += (-off) % 8
+    chunk_bits = []
+    for w in words:
+        chunk_bits.append(int.from_bytes(buf[off:off + 8 * w], "little"))
+        off += 8 * w
+    esc = [int.from_bytes(buf[off + 8 * i:off + 8 * i + 8], "little") for i in range(nesc)]
+    out, ei = [], 0
+    for c in range(nchunks):
+        bits, pos = chunk_bits[c], 0
+        for _ in range(min(HUFF_CHUNK, n - c * HUFF_CHUNK)):
+            code, L = 0, 0
+            while True:
+                code = (code << 1) | ((bits >> pos) & 1)
+                pos += 1
+                L += 1
+                if (L, code) in lookup:
+                    s = lookup[(L, code)]
+                    break
+            if s == K - 1:
+                zv = esc[ei]
+                ei += 1
+            else:
+                zv = s
+            out.append((zv >> 1) if zv % 2 == 0 else -((zv + 1) >> 1))
+    return np.asarray(out, dtype=np.int64)

@@ -6,6 +6,8 @@ matrix of Section 5.4, the interpolation stencils of Section 4.2), numerical
 quadrature with an independent piecewise-linear evaluator, exact rational
 arithmetic, dense Kronecker brute force, and invariants of the transform.
 """
+import itertools
+import math
 import os
 from fractions import Fraction
 
@@ -775,3 +777,141 @@ def test_4d_multilinear_zero_coefficients_and_identity(dims):
     # kappa = sqrt(2^4) = 4 between consecutive level tolerances.
     t = O.level_tolerances(H, 0, 1.0)
     np.testing.assert_allclose(t[1:] / t[:-1], 4.0, rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Entropy, cost model and the Huffman coder of the labels
+# ---------------------------------------------------------------------------
+
+def test_label_entropy_closed_forms():
+    assert O.label_entropy([]) == 0.0
+    assert O.label_entropy([7] * 10) == 0.0
+    for k in (1, 3, 6):
+        x = np.repeat(np.arange(-(2 ** (k - 1)), 2 ** (k - 1)), 5)
+        assert O.label_entropy(x) == pytest.approx(k, abs=1e-12)
+    p = 0.2
+    x = [0] * 200 + [1] * 800
+    assert O.label_entropy(x) == pytest.approx(-p * math.log2(p) - (1 - p) * math.log2(1 - p), abs=1e-12)
+
+
+def test_cost_model_hand_count():
+    # 1D, 5 nodes: N_0 has 3 nodes, N*_1 the other 2.  Full depth:
+    # 3 log2(R / q_0) + 2 log2(R / q_1) with q_l = 2 tau_l.
+    H = O.Hierarchy((5,))
+    taus = [0.125, 0.25]
+    assert O.cost_model(H, 0, taus, 8.0) == pytest.approx(3 * math.log2(32) + 2 * math.log2(16))
+    # Stopping at level 1 counts the whole grid with tau_1.
+    assert O.cost_model(H, 1, taus, 8.0) == pytest.approx(5 * math.log2(16))
+
+
+def test_huffman_lengths_textbook_example():
+    # The classic six-symbol example (counts 45, 13, 12, 16, 9, 5): the
+    # optimal code lengths are 1, 3, 3, 3, 4, 4 (224 bits per 100 symbols).
+    L = O.huffman_lengths([45, 13, 12, 16, 9, 5])
+    assert L == [1, 3, 3, 3, 4, 4]
+
+
+def _optimal_cost_brute(counts):
+    """Least sum c_i L_i over length vectors meeting Kraft's equality (every
+    full binary tree), by enumeration for a handful of symbols."""
+    n = len(counts)
+    best = None
+    for Ls in itertools.product(range(1, n), repeat=n):
+        if sum(2.0 ** -L for L in Ls) == 1.0:
+            cost = sum(c * L for c, L in zip(counts, Ls))
+            best = cost if best is None else min(best, cost)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_huffman_lengths_optimal_and_kraft(seed):
+    rng = _rng(40 + seed)
+    n = int(rng.integers(2, 6))
+    counts = [int(v) for v in rng.integers(1, 50, n)]
+    L = O.huffman_lengths(counts)
+    assert sum(2.0 ** -l for l in L) == 1.0
+    assert sum(c * l for c, l in zip(counts, L)) == _optimal_cost_brute(counts)
+    # Average length within [H, H + 1) (the entropy bound of Section 4.1's
+    # cost estimate).
+    p = np.asarray(counts, dtype=np.float64) / sum(counts)
+    Hs = float(-(p * np.log2(p)).sum())
+    avg = sum(c * l for c, l in zip(counts, L)) / sum(counts)
+    assert Hs - 1e-12 <= avg < Hs + 1.0
+
+
+def test_huffman_length_limit():
+    # Fibonacci counts make the unlimited Huffman tree a chain of depth
+    # n - 1; with 40 symbols the limit (31 bits) must engage.
+    fib = [1, 1]
+    while len(fib) < 40:
+        fib.append(fib[-1] + fib[-2])
+    L = O.huffman_lengths(fib)
+    assert max(L) <= 31
+    assert sum(2.0 ** -l for l in L) == 1.0
+    # Below the limit the chain is kept: 20 Fibonacci counts, depth 19.
+    assert max(O.huffman_lengths(fib[:20])) == 19
+
+
+def _huffman_cases():
+    out = []
+    with open(os.path.join(GOLDEN, "huffman_streams.txt")) as fh:
+        for line in fh:
+            line = line.rstrip("\n")
+            if not line.strip() or line.startswith("#"):
+                continue
+            f = [p.strip() for p in line.split("|")]
+            labels = [int(v) for v in f[0].split(",")]
+            lengths = {int(a): int(b) for a, b in (t.split(":") for t in f[1].split(","))}
+            chunks = [tuple(int(v) for v in t.split(":")) for t in f[2].split(",")]
+            payload = bytes.fromhex(f[3].replace(" ", ""))
+            esc = bytes.fromhex(f[4].replace(" ", "")) if f[4] else b""
+            out.append((labels, lengths, chunks, payload, esc))
+    return out
+
+
+@pytest.mark.parametrize("case", _huffman_cases())
+def test_huffman_hand_streams(case):
+    labels, lengths, chunks, payload, esc = case
+    buf = O.huffman_encode(labels)
+    n = len(labels)
+    K = O.HUFF_K
+    assert int.from_bytes(buf[0:8], "little") == n
+    assert int.from_bytes(buf[8:12], "little") == K
+    assert int.from_bytes(buf[12:16], "little") == max(lengths.values())
+    assert int.from_bytes(buf[16:24], "little") == len(esc) // 8
+    table = buf[24:24 + K]
+    assert {s: table[s] for s in range(K) if table[s]} == lengths
+    off = 24 + K
+    got_chunks = [(int.from_bytes(buf[off + 4 * c:off + 4 * c + 2], "little"),
+                   int.from_bytes(buf[off + 4 * c + 2:off + 4 * c + 4], "little"))
+                  for c in range(len(chunks))]
+    assert got_chunks == chunks
+    off += 4 * len(chunks)
+    off += (-off) % 8
+    assert buf[off:] == payload + esc
+    assert list(O.huffman_decode(buf)) == labels
+
+
+def test_huffman_round_trip():
+    rng = _rng(77)
+    assert O.huffman_decode(O.huffman_encode([])).size == 0
+    for n in (1, 1023, 1024, 1025, 3000):
+        x = (rng.geometric(0.1, n) - 1) * rng.choice([-1, 1], n)
+        if n > 10:
+            x[2] = 2 ** 62
+            x[n - 1] = -2 ** 63
+            x[n // 2] = 2 ** 63 - 1
+            x[5] = 32767     # zigzag 65534: the last direct symbol
+            x[6] = -32768    # zigzag 65535: the first escaped code
+        buf = O.huffman_encode(x)
+        assert np.array_equal(O.huffman_decode(buf), x)
+        # The payload is within one bit per label of the entropy of the
+        # symbols (the escape list aside).
+        z = np.where(x >= 0, 2 * x.astype(object), -2 * x.astype(object) - 1)
+        sym = np.asarray([min(int(v), O.HUFF_K - 1) for v in z])
+        nchunks = (n + 1023) // 1024
+        off = 24 + O.HUFF_K + 4 * nchunks
+        off += (-off) % 8
+        nesc = int.from_bytes(buf[16:24], "little")
+        payload_bits = 8 * (len(buf) - off - 8 * nesc)
+        assert payload_bits <= n * (O.label_entropy(sym) + 1) + 64 * nchunks
