@@ -335,6 +335,44 @@ int mgard_quantize_4d(const int64_t* dims, const double* const* coords, int dtyp
 int mgard_dequantize_4d(const int64_t* dims, const double* const* coords, int dtype, int stop_level,
                         double tau_linf, const int64_t* labels, void* coeffs, void* stream);
 
+/* Canonical Huffman coding of the labels (a reading of the lossless encoder
+ * of Algorithm 1 line 23, which the paper does not name), the labels'
+ * order-0 entropy and the cost model of Section 4.1.
+ * Stream (little-endian): uint64 N | uint32 K = 32817 | uint32 longest code
+ * length (<= 31) | K bytes of code lengths per symbol (0 = unused) | zero
+ * padding to 8 bytes | per chunk of 1024 labels a uint32 payload word count
+ * | zero padding to 8 bytes | the chunks' 64-bit payload words.  Symbol of a label: its zigzag
+ * code z (0, -1, 1, -2, .. -> 0, 1, 2, 3, ..) when z < 2^15, else 32768 +
+ * b - 16 for z of bit length b, followed by the b - 1 low bits of z.  Code
+ * lengths: Huffman's construction with leaves ordered by (count, symbol),
+ * merged nodes queued in creation order, a leaf taken on a tie; a code
+ * longer than 31 bits halves every used count (at least 1) and rebuilds.
+ * Canonical codes, written most significant bit first from bit 0 of the
+ * chunk's first word, extra bits after the code, least significant first.
+ * mgard_huffman_bound: an upper bound on the stream size of `count` labels.
+ * mgard_huffman_encode: labels (device int64, `count`) -> stream at `out`
+ * (device, 8-byte aligned, `capacity` bytes, else MGARD_ERR_WORKSPACE);
+ * *bytes_out receives its size; waits for the stream (the histogram is
+ * read on the host to build the code).
+ * mgard_huffman_decode: the inverse; MGARD_ERR_ARG if the stream does not
+ * match `count` and `bytes` or is not a valid code (checked on the host
+ * from its header and in the kernel while reading); waits for the stream.
+ * mgard_label_entropy: -sum p log2 p over the distinct label values, in
+ * bits per label (0 for no labels); waits for the stream.
+ * mgard_huffman_lengths: host only, the code lengths of `nsym` (<= 65536)
+ * symbol counts by the rule above.
+ * mgard_cost_model: host only, sum_l #N*_l log2(range / q_l) with
+ * q_l = 2 tau_levels[l] for l = stop_level .. L (N_{l~} counted whole at the
+ * stopping level), `range` the range of the multilevel coefficients. */
+int mgard_huffman_bound(int64_t count, size_t* bytes);
+int mgard_huffman_encode(int64_t count, const int64_t* labels, void* out, size_t capacity,
+                         size_t* bytes_out, void* stream);
+int mgard_huffman_decode(const void* in, size_t bytes, int64_t count, int64_t* labels, void* stream);
+int mgard_label_entropy(int64_t count, const int64_t* labels, double* bits_per_label, void* stream);
+int mgard_huffman_lengths(int nsym, const uint64_t* counts, uint8_t* lengths);
+int mgard_cost_model(int ndim, const int64_t* dims, int stop_level, const double* tau_levels,
+                     double range, double* bits);
+
 /* Free every cached plan (device tables included) of the current device. */
 int mgard_release_plans(void);
 

@@ -858,7 +858,8 @@ def cost_model(H: Hierarchy, stop_level: int, taus, R: float) -> float:
 
 
 HUFF_CHUNK = 1024
-HUFF_K = 65536          # alphabet: zigzag codes 0 .. K-2, and K-1 = escape
+HUFF_DIRECT = 32768     # zigzag codes below this are symbols of their own
+HUFF_K = HUFF_DIRECT + 49   # then one symbol per bit length 16 .. 64
 HUFF_MAXLEN = 31
 
 
@@ -928,79 +929,80 @@ def huffman_codes(lengths) -> dict:
     return codes
 
 
-def _huff_symbol(z: int) -> int:
-    return z if z < HUFF_K - 1 else HUFF_K - 1
+def _huff_symbol(z: int):
+    """(symbol, extra bits, number of extra bits) of a zigzag code: codes
+    below 2^15 are their own symbol; a larger code of bit length b is the
+    symbol 32768 + b - 16 followed by its b - 1 low bits (its leading 1 is
+    implied), as DEFLATE codes lengths with extra bits."""
+    if z < HUFF_DIRECT:
+        return z, 0, 0
+    b = z.bit_length()
+    return HUFF_DIRECT + b - 16, z - (1 << (b - 1)), b - 1
 
 
 def huffman_encode(labels) -> bytes:
-    """The labels' Huffman stream.  Each label is zigzag-coded; codes below
-    K - 1 are symbols, larger ones the escape symbol K - 1 with the code
-    itself stored in the escape list.  Layout (little-endian): uint64 N |
-    uint32 K | uint32 longest code length | uint64 number of escapes | K
-    bytes of code lengths | per chunk of 1024 labels a uint16 word count and
-    a uint16 escape count | zero padding to 8 bytes | per chunk its words:
-    each symbol's canonical code, most significant bit first, at increasing
-    bit positions from the least significant bit of the first word | the
-    escaped codes as uint64, in label order."""
+    """The labels' Huffman stream.  Layout (little-endian): uint64 N |
+    uint32 K (32817) | uint32 longest code length | K bytes of code lengths
+    (0 = unused symbol) | zero padding to 8 bytes | per chunk of 1024 labels
+    a uint32 word count | zero padding to 8 bytes | per chunk its 64-bit
+    words.  Each label's
+    symbol code is written most significant bit first at increasing bit
+    positions from the least significant bit of the chunk's first word,
+    followed by its extra bits, least significant first."""
     z = [_zigzag(int(v)) for v in np.asarray(labels, dtype=np.int64).ravel()]
     n = len(z)
-    sym = [_huff_symbol(v) for v in z]
+    parts = [_huff_symbol(v) for v in z]
     counts = [0] * HUFF_K
-    for s in sym:
+    for s, _, _ in parts:
         counts[s] += 1
     lengths = huffman_lengths(counts)
     codes = huffman_codes(lengths)
-    esc = [v for v in z if v >= HUFF_K - 1]
     out = bytearray(n.to_bytes(8, "little"))
     out += HUFF_K.to_bytes(4, "little") + max(lengths).to_bytes(4, "little")
-    out += len(esc).to_bytes(8, "little")
     out += bytes(lengths)
+    out += bytes((-len(out)) % 8)
     payload = []
     for c0 in range(0, n, HUFF_CHUNK):
-        bits, pos, ne = 0, 0, 0
-        for s in sym[c0:c0 + HUFF_CHUNK]:
+        bits, pos = 0, 0
+        for s, extra, nx in parts[c0:c0 + HUFF_CHUNK]:
             L, code = lengths[s], codes[s]
             for i in range(L):
                 bits |= ((code >> (L - 1 - i)) & 1) << (pos + i)
             pos += L
-            ne += s == HUFF_K - 1
+            bits |= extra << pos
+            pos += nx
         nwords = (pos + 63) // 64
-        out += nwords.to_bytes(2, "little") + ne.to_bytes(2, "little")
+        out += nwords.to_bytes(4, "little")
         payload.append(bits.to_bytes(8 * nwords, "little"))
     out += bytes((-len(out)) % 8)
     for p in payload:
         out += p
-    for v in esc:
-        out += v.to_bytes(8, "little")
     return bytes(out)
 
 
 def huffman_decode(buf: bytes) -> np.ndarray:
     """Inverse of :func:`huffman_encode`: read code bits one at a time; a
     code of length L is complete when it falls among the canonical codes of
-    that length."""
+    that length; a bit-length symbol is followed by its extra bits."""
     buf = bytes(buf)
     n = int.from_bytes(buf[0:8], "little")
     K = int.from_bytes(buf[8:12], "little")
-    nesc = int.from_bytes(buf[16:24], "little")
-    lengths = list(buf[24:24 + K])
+    lengths = list(buf[16:16 + K])
     codes = huffman_codes(lengths)
     lookup = {(lengths[s], c): s for s, c in codes.items()}
     nchunks = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
-    off = 24 + K
+    off = 16 + K
+    off += (-off) % 8
     words = []
     for c in range(nchunks):
-        words.append(int.from_bytes(buf[off:off + 2], "little"))
+        words.append(int.from_bytes(buf[off:off + 4], "little"))
         off += 4
     off += (-off) % 8
-    chunk_bits = []
-    for w in words:
-        chunk_bits.append(int.from_bytes(buf[off:off + 8 * w], "little"))
-        off += 8 * w
-    esc = [int.from_bytes(buf[off + 8 * i:off + 8 * i + 8], "little") for i in range(nesc)]
-    out, ei = [], 0
+    out = []
     for c in range(nchunks):
-        bits, pos = chunk_bits[c], 0
+        bits = int.from_bytes(buf[off:off + 8 * words[c]], "little")
+        off += 8 * words[c]
+        pos = 0
         for _ in range(min(HUFF_CHUNK, n - c * HUFF_CHUNK)):
             code, L = 0, 0
             while True:
@@ -1010,10 +1012,11 @@ def huffman_decode(buf: bytes) -> np.ndarray:
                 if (L, code) in lookup:
                     s = lookup[(L, code)]
                     break
-            if s == K - 1:
-                zv = esc[ei]
-                ei += 1
-            else:
+            if s < HUFF_DIRECT:
                 zv = s
+            else:
+                b = s - HUFF_DIRECT + 16
+                zv = (1 << (b - 1)) | ((bits >> pos) & ((1 << (b - 1)) - 1))
+                pos += b - 1
             out.append((zv >> 1) if zv % 2 == 0 else -((zv + 1) >> 1))
     return np.asarray(out, dtype=np.int64)

@@ -100,6 +100,14 @@ _SIGNATURES = {
                                          _VP, _VP, _DP, _VP]),
     "mgard_dequantize_4d": (ctypes.c_int, [_I64P, _DPP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            _VP, _VP, _VP]),
+    "mgard_huffman_bound": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "mgard_huffman_encode": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_size_t), _VP]),
+    "mgard_huffman_decode": (ctypes.c_int, [_VP, ctypes.c_size_t, ctypes.c_int64, _VP, _VP]),
+    "mgard_label_entropy": (ctypes.c_int, [ctypes.c_int64, _VP, _DP, _VP]),
+    "mgard_huffman_lengths": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(ctypes.c_uint8)]),
+    "mgard_cost_model": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.c_int, _DP, ctypes.c_double, _DP]),
     "mgard_release_plans": (ctypes.c_int, []),
     "mgard_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mgard_decompose_noalloc": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
@@ -889,3 +897,66 @@ def dequantize_4d(labels, tau: float, dtype, coords=None, stop_level: int = 0, o
                                labels.data_ptr(), out.data_ptr(), _stream(stream)),
            "mgard_dequantize_4d")
     return out
+
+
+# ------------------------------------------------- entropy stage of labels ---
+
+def huffman_bound(count: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().mgard_huffman_bound(int(count), ctypes.byref(b)), "mgard_huffman_bound")
+    return b.value
+
+
+def huffman_encode(labels, stream=None):
+    """The Huffman stream (a CUDA uint8 tensor of its exact size) of the int64
+    CUDA tensor `labels`."""
+    _cuda_tensor(labels, "labels")
+    torch = _torch()
+    n = labels.numel()
+    out = torch.empty(huffman_bound(n), dtype=torch.uint8, device=labels.device)
+    nb = ctypes.c_size_t()
+    rc = lib().mgard_huffman_encode(n, labels.data_ptr(), out.data_ptr(), out.numel(),
+                                    ctypes.byref(nb), _stream(stream))
+    _check(rc, "mgard_huffman_encode")
+    return out[:nb.value]
+
+
+def huffman_decode(stream_bytes, count: int, out=None, stream=None):
+    """Labels (int64 CUDA tensor of `count`) from a device Huffman stream."""
+    torch = _torch()
+    _cuda_tensor(stream_bytes, "stream")
+    if out is None:
+        out = torch.empty(count, dtype=torch.int64, device=stream_bytes.device)
+    rc = lib().mgard_huffman_decode(stream_bytes.data_ptr(), stream_bytes.numel(), int(count),
+                                    out.data_ptr(), _stream(stream))
+    _check(rc, "mgard_huffman_decode")
+    return out
+
+
+def label_entropy(labels, stream=None) -> float:
+    """Order-0 entropy of the labels in bits per label."""
+    _cuda_tensor(labels, "labels")
+    h = ctypes.c_double()
+    _check(lib().mgard_label_entropy(labels.numel(), labels.data_ptr(), ctypes.byref(h),
+                                     _stream(stream)), "mgard_label_entropy")
+    return h.value
+
+
+def huffman_lengths(counts) -> np.ndarray:
+    """Code lengths for symbol counts (host only)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    out = np.zeros(c.size, dtype=np.uint8)
+    _check(lib().mgard_huffman_lengths(c.size, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+           "mgard_huffman_lengths")
+    return out
+
+
+def cost_model(dims, stop_level: int, taus, value_range: float) -> float:
+    """Section 4.1's estimated label cost in bits (host only)."""
+    s = _Shape(dims)
+    t = np.ascontiguousarray(taus, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(lib().mgard_cost_model(s.ndim, s.dims, stop_level, t.ctypes.data_as(_DP),
+                                  float(value_range), ctypes.byref(out)), "mgard_cost_model")
+    return out.value

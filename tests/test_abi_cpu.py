@@ -168,3 +168,42 @@ def test_node_limit_4d(lib):
     assert _rc(B.mgard_num_levels_4d, (2048, 1024, 1024, 3)) == -2
     assert B.mgard_num_levels_4d((1024, 1024, 682, 3)) == O.Hierarchy((1024, 1024, 682, 3)).L
     assert _rc(B.mgard_workspace_size_4d, (1024, 1024, 1024, 3), B.F32) == -2
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_huffman_lengths_match_oracle(lib, seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 3000))
+    counts = rng.integers(0, 1000, n) * (rng.random(n) < 0.6)
+    counts[rng.integers(0, n)] = 5   # at least one used symbol
+    got = B.huffman_lengths(counts)
+    assert list(got) == O.huffman_lengths(list(counts))
+
+
+def test_huffman_lengths_special_cases(lib):
+    assert list(B.huffman_lengths([45, 13, 12, 16, 9, 5])) == [1, 3, 3, 3, 4, 4]
+    assert list(B.huffman_lengths([0, 0, 7, 0])) == [0, 0, 1, 0]
+    assert list(B.huffman_lengths([0, 0])) == [0, 0]
+    fib = [1, 1]
+    while len(fib) < 45:
+        fib.append(fib[-1] + fib[-2])
+    got = B.huffman_lengths(fib)
+    assert list(got) == O.huffman_lengths(fib) and max(got) <= 31
+    assert _rc(B.huffman_lengths, np.zeros(65537)) == -1
+
+
+@pytest.mark.parametrize("dims,stop", [((5,), 0), ((33, 20, 17), 1), ((65, 65, 65), 0)])
+def test_cost_model_matches_oracle(lib, dims, stop):
+    H = O.Hierarchy(dims)
+    taus = O.level_tolerances(H, stop, 1e-3)
+    got = B.cost_model(dims, stop, taus, 3.5)
+    np.testing.assert_allclose(got, O.cost_model(H, stop, taus, 3.5), rtol=1e-12)
+    assert _rc(B.cost_model, dims, stop, taus, 0.0) == -1
+
+
+def test_huffman_bound(lib):
+    assert B.huffman_bound(0) >= 16 + 32817
+    for n in (1, 1024, 10 ** 6):
+        nch = (n + 1023) // 1024
+        # header, chunk table, and at most 31 code + 63 extra bits per label
+        assert B.huffman_bound(n) >= 16 + 32817 + 4 * nch + (n * 94 + 7) // 8

@@ -862,33 +862,30 @@ def _huffman_cases():
             f = [p.strip() for p in line.split("|")]
             labels = [int(v) for v in f[0].split(",")]
             lengths = {int(a): int(b) for a, b in (t.split(":") for t in f[1].split(","))}
-            chunks = [tuple(int(v) for v in t.split(":")) for t in f[2].split(",")]
+            chunks = [int(v) for v in f[2].split(",")]
             payload = bytes.fromhex(f[3].replace(" ", ""))
-            esc = bytes.fromhex(f[4].replace(" ", "")) if f[4] else b""
-            out.append((labels, lengths, chunks, payload, esc))
+            out.append((labels, lengths, chunks, payload))
     return out
 
 
 @pytest.mark.parametrize("case", _huffman_cases())
 def test_huffman_hand_streams(case):
-    labels, lengths, chunks, payload, esc = case
+    labels, lengths, chunks, payload = case
     buf = O.huffman_encode(labels)
-    n = len(labels)
     K = O.HUFF_K
-    assert int.from_bytes(buf[0:8], "little") == n
-    assert int.from_bytes(buf[8:12], "little") == K
+    assert int.from_bytes(buf[0:8], "little") == len(labels)
+    assert int.from_bytes(buf[8:12], "little") == K == 32817
     assert int.from_bytes(buf[12:16], "little") == max(lengths.values())
-    assert int.from_bytes(buf[16:24], "little") == len(esc) // 8
-    table = buf[24:24 + K]
+    table = buf[16:16 + K]
     assert {s: table[s] for s in range(K) if table[s]} == lengths
-    off = 24 + K
-    got_chunks = [(int.from_bytes(buf[off + 4 * c:off + 4 * c + 2], "little"),
-                   int.from_bytes(buf[off + 4 * c + 2:off + 4 * c + 4], "little"))
-                  for c in range(len(chunks))]
-    assert got_chunks == chunks
+    off = 16 + K
+    assert buf[off:off + (-off) % 8] == bytes((-off) % 8)
+    off += (-off) % 8
+    got = [int.from_bytes(buf[off + 4 * c:off + 4 * c + 4], "little") for c in range(len(chunks))]
+    assert got == chunks
     off += 4 * len(chunks)
     off += (-off) % 8
-    assert buf[off:] == payload + esc
+    assert buf[off:] == payload
     assert list(O.huffman_decode(buf)) == labels
 
 
@@ -899,19 +896,22 @@ def test_huffman_round_trip():
         x = (rng.geometric(0.1, n) - 1) * rng.choice([-1, 1], n)
         if n > 10:
             x[2] = 2 ** 62
-            x[n - 1] = -2 ** 63
+            x[n - 1] = -2 ** 63      # zigzag 2^64 - 1: bit length 64
             x[n // 2] = 2 ** 63 - 1
-            x[5] = 32767     # zigzag 65534: the last direct symbol
-            x[6] = -32768    # zigzag 65535: the first escaped code
+            x[5] = 16383             # zigzag 32766, the last direct symbols
+            x[6] = -16384            # zigzag 32767
+            x[7] = 16384             # zigzag 32768: bit length 16, 15 extra bits
         buf = O.huffman_encode(x)
         assert np.array_equal(O.huffman_decode(buf), x)
         # The payload is within one bit per label of the entropy of the
-        # symbols (the escape list aside).
-        z = np.where(x >= 0, 2 * x.astype(object), -2 * x.astype(object) - 1)
-        sym = np.asarray([min(int(v), O.HUFF_K - 1) for v in z])
+        # symbols plus the extra bits.
+        z = [O._zigzag(int(v)) for v in x]
+        parts = [O._huff_symbol(v) for v in z]
+        sym = np.asarray([p[0] for p in parts])
+        extra = sum(p[2] for p in parts)
         nchunks = (n + 1023) // 1024
-        off = 24 + O.HUFF_K + 4 * nchunks
+        off = 16 + O.HUFF_K
+        off += (-off) % 8 + 4 * nchunks
         off += (-off) % 8
-        nesc = int.from_bytes(buf[16:24], "little")
-        payload_bits = 8 * (len(buf) - off - 8 * nesc)
-        assert payload_bits <= n * (O.label_entropy(sym) + 1) + 64 * nchunks
+        payload_bits = 8 * (len(buf) - off)
+        assert payload_bits <= n * (O.label_entropy(sym) + 1) + extra + 64 * nchunks
