@@ -645,6 +645,42 @@ def run_gpu(args, rank, world, local_rank):
             "psnr_db": 20 * np.log10(rng_u) - 10 * np.log10(mse),
             "linf_over_tau": float((rec - u64).abs().max().item()) / tau}
         del rec
+        # The same labels through the Huffman stage, their order-0 entropy
+        # and Section 4.1's cost estimate (R = range of the coefficients).
+        flat = labels.reshape(-1)
+        hs = B.huffman_encode(flat)
+        x.copy_(u)
+        B.decompose(x, None, 0, ws)
+        clo, chi = B.value_range(x)
+        taus_q = B.mgard_level_tolerances(DIMS, None, 0, tau)
+        quality[f"{rel:g}"].update({
+            "huffman_bits_per_value": 8.0 * hs.numel() / cnt,
+            "huffman_compression_ratio": nbytes / hs.numel(),
+            "entropy_bits_per_value": B.label_entropy(flat),
+            "cost_model_bits_per_value": B.cost_model(DIMS, 0, taus_q, chi - clo) / cnt})
+        del hs
+    # Huffman stage throughput on the 1e-3 labels (median of 3).
+    e2e_step(1e-3, True)
+    flat = labels.reshape(-1)
+    t_he, t_hd = [], []
+    for i in range(3):
+        ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        ea.record(stream)
+        hs = B.huffman_encode(flat)
+        eb.record(stream)
+        back = B.huffman_decode(hs, cnt)
+        ec.record(stream)
+        torch.cuda.synchronize()
+        t_he.append(ea.elapsed_time(eb))
+        t_hd.append(eb.elapsed_time(ec))
+    assert torch.equal(back, flat)
+    huffman = {"encode_ms": statistics.median(t_he), "decode_ms": statistics.median(t_hd),
+               "labels_gbs_encode": 8 * cnt / (statistics.median(t_he) * 1e-3) / 1e9,
+               "labels_gbs_decode": 8 * cnt / (statistics.median(t_hd) * 1e-3) / 1e9,
+               "stream_bytes_1e-3": int(hs.numel()),
+               "note": "int64 labels of the 513^3 field at 1e-3 x range; the encoder waits once "
+                       "for the histogram (code built on the host)"}
+    del hs, back
     e2e = {"value": world * nbytes * ke / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": nbytes + stream_bytes, "d2h_bytes_per_step": stream_bytes + nbytes,
            "ms_per_step": e2e_ms / ke, "steps": ke,
@@ -680,6 +716,7 @@ def run_gpu(args, rank, world, local_rank):
         "adaptive": adaptive,
         "progressive": progressive,
         "nd4": nd4,
+        "huffman": huffman,
         "linf_over_tau": linf,
         "top_kernels": kernels,
         "kinds_ms_per_step": {k: round(v, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1])},
