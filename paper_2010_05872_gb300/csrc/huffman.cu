@@ -49,7 +49,7 @@ constexpr int kHuffMaxLen = 31;
 constexpr int kSmemBins = 8192;   // symbols counted in shared memory per CTA
 constexpr int kPeekBits = 11;     // decoder lookup table of the short codes
 constexpr int kHeaderFixed = 16;  // N, K, longest length
-constexpr int kEncWarps = 4;
+constexpr int kEncWarps = 8;
 constexpr int kChunkWords = (kHuffChunk * (kHuffMaxLen + 63) + 63) / 64;  // 1504
 
 __device__ __forceinline__ uint64_t zig(int64_t k) {
@@ -113,7 +113,7 @@ huff_escapes_kernel(const int64_t* __restrict__ labels, int64_t n, uint64_t* __r
 __global__ void __launch_bounds__(256)
 huff_sizes_kernel(const int64_t* __restrict__ labels, int64_t n, int64_t nchunks,
                   const uint64_t* __restrict__ enc, uint64_t* __restrict__ words,
-                  uint32_t* __restrict__ table) {
+                  uint32_t* __restrict__ table, unsigned long long* __restrict__ maxw) {
   grid_dep_enter();
   const int lane = threadIdx.x & 31;
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -132,6 +132,7 @@ huff_sizes_kernel(const int64_t* __restrict__ labels, int64_t n, int64_t nchunks
       const uint64_t w = (bits + 63) / 64;
       words[c] = w;
       table[c] = static_cast<uint32_t>(w);
+      atomicMax(maxw, static_cast<unsigned long long>(w));
     }
   }
 }
@@ -167,17 +168,19 @@ huff_scan_kernel(uint64_t* __restrict__ v, int64_t n, uint64_t* __restrict__ tot
 // A warp per chunk: bit positions by a warp scan of the labels' bit counts
 // (code + extra bits), the chunk's words assembled in shared memory, then
 // stored.
+// Each warp's words sit in dynamic shared memory at a pitch of the
+// largest chunk's word count.
 __global__ void __launch_bounds__(32 * kEncWarps)
 huff_encode_kernel(const int64_t* __restrict__ labels, int64_t n, int64_t nchunks,
                    const uint64_t* __restrict__ enc, const uint64_t* __restrict__ woff,
-                   uint64_t* __restrict__ payload) {
+                   uint64_t* __restrict__ payload, int pitch) {
   grid_dep_enter();
-  __shared__ unsigned long long sw[kEncWarps][kChunkWords];
+  extern __shared__ __align__(16) unsigned long long sw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long* w = sw[wid];
+  unsigned long long* w = sw + static_cast<size_t>(wid) * pitch;
   const int64_t nw = int64_t(gridDim.x) * kEncWarps;
   for (int64_t c = int64_t(blockIdx.x) * kEncWarps + wid; c < nchunks; c += nw) {
-    for (int i = lane; i < kChunkWords; i += 32) w[i] = 0ull;
+    for (int i = lane; i < pitch; i += 32) w[i] = 0ull;
     __syncwarp();
     const int64_t base = c * kHuffChunk;
     const int nc = static_cast<int>(min(int64_t(kHuffChunk), n - base));
@@ -380,14 +383,16 @@ bool huff_codes(const std::vector<uint8_t>& len, std::vector<uint64_t>& enc, Dec
   sorted.assign(off, 0);
   std::vector<uint32_t> fill(kHuffMaxLen + 2, 0);
   enc.assign(K, 0);
-  for (int L = 1; L <= maxlen; ++L)
-    for (int s = 0; s < K; ++s)
-      if (len[s] == L) {
-        const uint32_t c = dt.first[L] + fill[L];
-        sorted[dt.offset[L] + fill[L]] = static_cast<uint16_t>(s);
-        ++fill[L];
-        enc[s] = (uint64_t(L) << 32) | c;
-      }
+  // One pass in symbol order: within a length, codes go to the symbols in
+  // increasing order.
+  for (int s = 0; s < K; ++s) {
+    const int L = len[s];
+    if (L == 0) continue;
+    const uint32_t c = dt.first[L] + fill[L];
+    sorted[dt.offset[L] + fill[L]] = static_cast<uint16_t>(s);
+    ++fill[L];
+    enc[s] = (uint64_t(L) << 32) | c;
+  }
   peek.assign(1u << kPeekBits, 0);
   for (int s = 0; s < K; ++s) {
     const int L = len[s];
@@ -466,27 +471,35 @@ int encode(int64_t n, const int64_t* labels, uint8_t* out, size_t capacity, size
   std::memcpy(head.data() + kHeaderFixed, len.data(), kHuffK);
   uint64_t* d_enc = sc.get<uint64_t>(kHuffK);
   uint64_t* words = sc.get<uint64_t>(nchunks);
-  uint64_t* tot = sc.get<uint64_t>(1);
+  uint64_t* tot = sc.get<uint64_t>(2);  // total words, largest chunk
   if (!d_enc || !words || !tot) return MGARD_ERR_CUDA;
   HUFF_TRY(cudaMemcpyAsync(d_enc, enc.data(), sizeof(uint64_t) * kHuffK, cudaMemcpyHostToDevice, s));
   HUFF_TRY(cudaMemcpyAsync(out, head.data(), head.size(), cudaMemcpyHostToDevice, s));
   const size_t pad0 = kTableOff + 4 * static_cast<size_t>(nchunks);
   if (hdr > pad0) HUFF_TRY(cudaMemsetAsync(out + pad0, 0, hdr - pad0, s));
-  uint64_t total = 0;
+  uint64_t totals[2] = {0, 0};
   if (nchunks > 0) {
+    HUFF_TRY(cudaMemsetAsync(tot + 1, 0, sizeof(uint64_t), s));
     HUFF_TRY(launch_pdl(huff_sizes_kernel, dim3(grid_for(nchunks, 8)), dim3(256), 0, s, labels, n,
                         nchunks, static_cast<const uint64_t*>(d_enc), words,
-                        reinterpret_cast<uint32_t*>(out + kTableOff)));
+                        reinterpret_cast<uint32_t*>(out + kTableOff),
+                        reinterpret_cast<unsigned long long*>(tot + 1)));
     HUFF_TRY(launch_pdl(huff_scan_kernel, dim3(1), dim3(kScanT), 0, s, words, nchunks, tot));
-    HUFF_TRY(cudaMemcpyAsync(&total, tot, sizeof total, cudaMemcpyDeviceToHost, s));
+    HUFF_TRY(cudaMemcpyAsync(totals, tot, sizeof totals, cudaMemcpyDeviceToHost, s));
     HUFF_TRY(cudaStreamSynchronize(s));
   }
-  const size_t bytes = hdr + 8 * total;
+  const size_t bytes = hdr + 8 * totals[0];
   if (bytes > capacity) return MGARD_ERR_WORKSPACE;
-  if (nchunks > 0)
-    HUFF_TRY(launch_pdl(huff_encode_kernel, dim3(grid_for(nchunks, kEncWarps)), dim3(32 * kEncWarps), 0,
-                        s, labels, n, nchunks, static_cast<const uint64_t*>(d_enc),
-                        static_cast<const uint64_t*>(words), reinterpret_cast<uint64_t*>(out + hdr)));
+  if (nchunks > 0) {
+    const int pitch = static_cast<int>(std::max<uint64_t>(1, totals[1]));  // <= kChunkWords
+    const size_t smem = sizeof(uint64_t) * kEncWarps * static_cast<size_t>(pitch);
+    HUFF_TRY(cudaFuncSetAttribute(huff_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+    HUFF_TRY(launch_pdl(huff_encode_kernel, dim3(grid_for(nchunks, kEncWarps)), dim3(32 * kEncWarps),
+                        smem, s, labels, n, nchunks, static_cast<const uint64_t*>(d_enc),
+                        static_cast<const uint64_t*>(words), reinterpret_cast<uint64_t*>(out + hdr),
+                        pitch));
+  }
   HUFF_TRY(cudaGetLastError());
   *bytes_out = bytes;
   return MGARD_OK;
