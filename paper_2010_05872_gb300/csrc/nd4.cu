@@ -1,22 +1,21 @@
 // Four-dimensional grids (QMCPACK's shape class, Section 6): the same
 // multilevel decomposition, recomposition and level-wise quantization on a
-// 4D tensor-product grid, built from one-axis passes over the array seen as
-// (outer, n, inner) for each axis in turn.  This is the plain form of the
-// method (every operator applied axis by axis, the way it factors), not the
-// fused 1-3D kernels.
+// 4D tensor-product grid.  The operators are applied the way they factor,
+// axis by axis, in separate passes (not the fused 1-3D kernels).
 //
-// Decomposition of level l (v the level-l grid, n its shape, c the coarse
-// shape):
-//   v_c   = v at the coarse nodes (gather),
-//   Pi    = multilinear interpolant of v_c, expanded one axis at a time,
-//   w     = v - Pi (zero at the coarse nodes: the coefficients, Section 2),
-//   F     = (R_0 x R_1 x R_2 x R_3) w, one restriction pass per axis (R the
-//           rows of P^T M_f, Section 5.2),
-//   z     = M_c^{-1} F, a Thomas solve along every axis (Section 5.4),
-//   Q_{l-1}u = v_c + z, and v keeps w at its coefficient nodes.
+// Decomposition of level l (v the level-l grid, c the compact coarse grid):
+//   one pass: c = v at the coarse nodes, and at every other node
+//             v <- w = v - Pi(v at the coarse nodes) (the coefficients,
+//             Section 2; Pi the multilinear interpolant),
+//   F = (R_0 x R_1 x R_2 x R_3) w, one restriction pass per axis (R the
+//       rows of P^T M_f, Section 5.2; the first pass reads v with its
+//       coarse nodes taken as 0),
+//   z = M_c^{-1} F, a Thomas solve along every axis (Section 5.4),
+//   Q_{l-1}u = c + z.
 // The coarse values go back into the nodal positions, coarsest first.
-// Recomposition inverts it: w from the coefficient nodes, z = M_c^{-1} R w,
-// c' = Q_{l-1}u - z, v = Pi(c') + w.
+// Recomposition inverts it: the level grids are gathered from u_mc, then
+// per level z = M_c^{-1} R w (w the coefficients at their nodes),
+// c' = Q_{l-1}u - z and, in one pass, v = Pi(c') + w.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -456,7 +455,6 @@ struct Plan4 {
   std::vector<Shape4> shape;            // [L+1]
   std::vector<std::array<Ax4, 4>> ax;   // [L+1], entry l = transition l -> l-1
   std::vector<double> knorm;            // [L+1]
-  std::vector<double> hd;               // [L+1] largest hat-integral products (unused here)
   std::array<std::vector<uint8_t>, 4> lev;  // per finest index of an axis: least level holding it
   size_t lev012_off = 0;  // per row (j0, j1, j2): the largest of its three axes' levels
   size_t lev3_off = 0;    // per index of axis 3
