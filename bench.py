@@ -428,6 +428,8 @@ def run_gpu(args, rank, world, local_rank):
         n = [v // 2 + 1 for v in n]
     b_alg = 2 * 2 * 4 * sum(sizes)
     path_frac = b_alg / ((phase["decompose"] + phase["recompose"]) * 1e-3) / 1e9 / peak
+    # The same against the nominal HBM3e bandwidth (7.9 TB/s), as a second column.
+    path_frac_nominal = b_alg / ((phase["decompose"] + phase["recompose"]) * 1e-3) / 1e9 / 7900.0
 
     kinds = {}
     for r in trace:
@@ -733,6 +735,7 @@ def run_gpu(args, rank, world, local_rank):
         "dec_rec_gbs": dec_rec_gbs,
         "phases_ms_per_step": phase,
         "path_roofline_frac_dec_rec": path_frac,
+        "path_roofline_frac_dec_rec_nominal_7900": path_frac_nominal,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
