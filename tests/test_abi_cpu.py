@@ -207,3 +207,14 @@ def test_huffman_bound(lib):
         nch = (n + 1023) // 1024
         # header, chunk table, and at most 31 code + 63 extra bits per label
         assert B.huffman_bound(n) >= 16 + 32817 + 4 * nch + (n * 94 + 7) // 8
+
+
+def test_device_helpers_refuse_cpu_tensors(lib):
+    # There is no CPU path: the tensor helpers raise before any call.
+    import torch
+    x = torch.zeros(1000, dtype=torch.int64)
+    for fn in (B.huffman_encode, B.label_entropy, B.pack_labels):
+        with pytest.raises(ValueError):
+            fn(x)
+    with pytest.raises(ValueError):
+        B.decompose_4d(torch.zeros((3, 3, 3, 3)))
