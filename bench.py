@@ -707,8 +707,8 @@ def run_gpu(args, rank, world, local_rank):
                "labels_gbs_encode": 8 * cnt / (statistics.median(t_he) * 1e-3) / 1e9,
                "labels_gbs_decode": 8 * cnt / (statistics.median(t_hd) * 1e-3) / 1e9,
                "stream_bytes_1e-3": int(hs.numel()),
-               "note": "int64 labels of the 513^3 field at 1e-3 x range; the encoder waits once "
-                       "for the histogram (code built on the host)"}
+               "note": "int64 labels of the 513^3 field at 1e-3 x range; the encoder waits twice "
+                       "(for the histogram, from which the host builds the code, and for the chunk sizes)"}
     del hs, back
     e2e = {"value": world * nbytes * ke / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": nbytes + stream_bytes, "d2h_bytes_per_step": stream_bytes + nbytes,
