@@ -418,7 +418,7 @@ def run_gpu(args, rank, world, local_rank):
         "launches_timed": tt["launches"],
         "share_of_kernel_time": top["total_ms"] / total_kernel_ms,
     }
-    # Whole-path roofline on the survey's algorithmic byte count
+    # Whole-path roofline on the path's algorithmic byte count
     # B_alg = 2 (decompose + recompose) x 2 s sum_{l<=L} #N_l.
     from paper_2010_05872_gb300.binding import mgard_num_levels  # noqa: F401
     sizes = []
