@@ -46,6 +46,20 @@ BOUNDS = (1e-2, 1e-3, 1e-4, 1e-5)
 FALLBACK_HBM = 6800.0
 
 
+# The paper's own figures with the hardware it names (Section 6; one core of
+# a 2x8-core Xeon E5-2650 node of the Rhea cluster, FP32): context only, not
+# a target and not comparable to this GPU's throughput.
+PAPER_CONTEXT = {
+    "hardware": "Rhea cluster node, 2x8-core Intel Xeon E5-2650, 128 GB (CPU, per core)",
+    "decomposition_speedup_vs_mgard": {"Hurricane": 20, "NYX": 28, "SCALE-LETKF": 39, "QMCPACK": 71},
+    "recomposition_speedup_vs_mgard": {"Hurricane": 22, "NYX": 30, "SCALE-LETKF": 41, "QMCPACK": 80},
+    "whole_compressor_mb_per_s_at_psnr_60": {"Hurricane": 96.03, "NYX": 94.23, "SCALE-LETKF": 104.82,
+                                             "QMCPACK": 100.30},
+    "note": "Fig. 7 and Table 5 of the paper; another machine and a wider pipeline (SZ and a "
+            "lossless back end included in the whole-compressor figure)",
+}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -749,6 +763,7 @@ def run_gpu(args, rank, world, local_rank):
         "progressive": progressive,
         "nd4": nd4,
         "huffman": huffman,
+        "paper_context": PAPER_CONTEXT,
         "linf_over_tau": linf,
         "top_kernels": kernels,
         "kinds_ms_per_step": {k: round(v, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1])},
