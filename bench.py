@@ -434,7 +434,6 @@ def run_gpu(args, rank, world, local_rank):
     }
     # Whole-path roofline on the path's algorithmic byte count
     # B_alg = 2 (decompose + recompose) x 2 s sum_{l<=L} #N_l.
-    from paper_2010_05872_gb300.binding import mgard_num_levels  # noqa: F401
     sizes = []
     n = list(DIMS)
     while min(n) > 3:
