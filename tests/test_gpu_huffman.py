@@ -118,3 +118,20 @@ def test_huffman_invalid_streams_refused(cuda):
     with pytest.raises(B.MgardError) as e:
         B.huffman_decode(bad, 5000)
     assert e.value.code == -1
+
+
+def test_huffman_capacity_checked_before_writing(cuda):
+    """A destination smaller than the stream is refused (MGARD_ERR_WORKSPACE)
+    and nothing is written past it."""
+    import ctypes
+    torch = cuda
+    n = 5000
+    x = torch.from_numpy(_labels(n, 21)).cuda()
+    full = B.huffman_encode(x).numel()
+    for cap in (100, full - 8):
+        buf = torch.full((cap + 4096,), 0xA5, dtype=torch.uint8, device="cuda")
+        nb = ctypes.c_size_t()
+        rc = B.lib().mgard_huffman_encode(n, x.data_ptr(), buf.data_ptr(), cap, ctypes.byref(nb), 0)
+        torch.cuda.synchronize()
+        assert rc == -5
+        assert bool((buf[cap:] == 0xA5).all().item())
