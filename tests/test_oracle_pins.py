@@ -373,7 +373,7 @@ def test_linf_constant_uniform_limit():
     """Large uniform grids: |A|_inf -> 1 + sqrt(3)/2 per axis (the rows of
     M_c^{-1} decay with ratio 2 - sqrt(3)), so C -> (1 + sqrt(3)/2)^d."""
     lim = 1 + np.sqrt(3) / 2
-    for d in (1, 2, 3):
+    for d in (1, 2, 3, 4):
         C = O.linf_constant(O.Hierarchy((129,) * d))
         assert C == pytest.approx(lim ** d, rel=1e-9)
 
@@ -399,6 +399,40 @@ def test_linf_constant_is_an_upper_bound_1d():
     assert abs(err[pos]) == pytest.approx(np.abs(K[k]).sum(), rel=1e-12)
     C = O.linf_constant(H, l - 1)
     assert C >= 1 + np.abs(K[k]).sum() - 1e-12
+    assert C >= np.abs(err).max()
+
+
+@pytest.mark.parametrize("dims,nonuni", [((9, 7), False), ((5, 6, 5), True), ((5, 5, 4, 5), False),
+                                         ((5, 4, 5, 5), True)])
+def test_linf_constant_bounds_the_dense_operator(dims, nonuni):
+    """In 2-4D the telescoping sum is an upper bound, not the exact norm:
+    C_Linf must be at least 1 + the largest absolute row sum of the dense
+    operator K (the Kronecker product of the axes' projections restricted to
+    the coefficient columns) that maps the finest level's coefficients to
+    the correction of the coarse values."""
+    coords = [F.geometric_coords(n, 1.1) for n in dims] if nonuni else None
+    H = O.Hierarchy(dims, coords)
+    l = H.L
+    ops = H.ops(l)
+    A = O.projection_matrix(ops[0])
+    for op in ops[1:]:
+        A = np.kron(A, O.projection_matrix(op))
+    coarse = np.zeros(dims, dtype=bool)
+    coarse[np.ix_(*[op.keep for op in ops])] = True
+    K = A[:, ~coarse.ravel()]
+    true_norm = np.abs(K).sum(axis=1).max()
+    C = O.linf_constant(H, l - 1)
+    assert C >= 1 + true_norm - 1e-12
+    # And the worst-case sign pattern of that row is reproduced by a
+    # recomposition of coefficient errors alone.
+    k = np.argmax(np.abs(K).sum(axis=1))
+    e = np.zeros(int(np.prod(dims)))
+    e[~coarse.ravel()] = np.sign(K[k])
+    umc = np.zeros(dims)
+    umc[np.ix_(*H.index[l])] = e.reshape(dims)
+    err = O.recompose(umc, H, l - 1)
+    pos = tuple(H.index[l - 1][d][i] for d, i in enumerate(np.unravel_index(k, H.levels[l - 1])))
+    assert abs(err[pos]) == pytest.approx(true_norm, rel=1e-12)
     assert C >= np.abs(err).max()
 
 
