@@ -96,7 +96,7 @@ huff_hist_kernel(const int64_t* __restrict__ labels, int64_t n, unsigned long lo
 // The zigzag codes of 2^15 and above, compacted in any order (the entropy
 // counts their distinct values).
 __global__ void __launch_bounds__(256)
-huff_escapes_kernel(const int64_t* __restrict__ labels, int64_t n, uint64_t* __restrict__ out,
+huff_large_codes_kernel(const int64_t* __restrict__ labels, int64_t n, uint64_t* __restrict__ out,
                     unsigned long long* __restrict__ count, unsigned long long cap) {
   grid_dep_enter();
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
@@ -575,7 +575,7 @@ int entropy(int64_t n, const int64_t* labels, double* out, cudaStream_t s) {
     unsigned long long* d_cnt = sc.get<unsigned long long>(1);
     if (!d_big || !d_cnt) return MGARD_ERR_CUDA;
     HUFF_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
-    HUFF_TRY(launch_pdl(huff_escapes_kernel, dim3(grid_for(n, 256 * 16)), dim3(256), 0, s, labels, n,
+    HUFF_TRY(launch_pdl(huff_large_codes_kernel, dim3(grid_for(n, 256 * 16)), dim3(256), 0, s, labels, n,
                         d_big, d_cnt, static_cast<unsigned long long>(nlarge)));
     std::vector<uint64_t> big(nlarge);
     HUFF_TRY(cudaMemcpyAsync(big.data(), d_big, 8 * nlarge, cudaMemcpyDeviceToHost, s));
