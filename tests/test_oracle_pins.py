@@ -949,3 +949,24 @@ def test_huffman_round_trip():
         off += (-off) % 8
         payload_bits = 8 * (len(buf) - off)
         assert payload_bits <= n * (O.label_entropy(sym) + 1) + extra + 64 * nchunks
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_huffman_cost_matches_heap_construction(seed):
+    """Any Huffman construction gives the same total cost: the sum of the
+    weights of the merged nodes.  A textbook heap-based merge (independent of
+    the two-queue form used by the oracle) must give the cost of the
+    oracle's lengths, on alphabets of hundreds of symbols."""
+    import heapq
+    rng = _rng(500 + seed)
+    counts = [int(c) for c in rng.integers(1, 10 ** 6, int(rng.integers(50, 600)))]
+    L = O.huffman_lengths(counts)
+    heap = list(counts)
+    heapq.heapify(heap)
+    cost = 0
+    while len(heap) > 1:
+        a = heapq.heappop(heap)
+        b = heapq.heappop(heap)
+        cost += a + b
+        heapq.heappush(heap, a + b)
+    assert sum(c * l for c, l in zip(counts, L)) == cost
