@@ -71,7 +71,8 @@ def parse_args():
                     help="single: the 513^3 field (default); batched: 256 uneven fields; "
                          "serving: a Poisson request stream")
     ap.add_argument("--serving-requests", type=int, default=2000, help=argparse.SUPPRESS)
-    ap.add_argument("--case-dims", default="513x513x513", help=argparse.SUPPRESS)
+    ap.add_argument("--case-dims", default="513x513x513",
+                    help="field shape of --kernel-case, e.g. 513x513x257 or 288x115x69x69")
     ap.add_argument("--batch-count", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-case", action="store_true",
                     help="only one compression round trip of a --case-dims FP32 field, 3D or "
