@@ -218,3 +218,36 @@ def test_device_helpers_refuse_cpu_tensors(lib):
             fn(x)
     with pytest.raises(ValueError):
         B.decompose_4d(torch.zeros((3, 3, 3, 3)))
+
+
+def _declared_prototypes():
+    """name -> (return type, parameter count) from the header's prototypes."""
+    out = {}
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"([A-Za-z_][\w \*]*?)\b(mgard_\w+)\s*\(([^;{]*?)\)\s*;", text, re.S):
+            ret, name, params = m.group(1).strip(), m.group(2), " ".join(m.group(3).split())
+            n = 0 if params in ("", "void") else params.count(",") + 1
+            out[name] = (ret, n)
+    return out
+
+
+def test_binding_signatures_match_header(lib):
+    # A ctypes argument list that disagrees with the C prototype would pass
+    # garbage silently; every binding signature must have the header's arity
+    # and return kind.
+    protos = _declared_prototypes()
+    assert set(protos) == set(B.exported_symbols())
+    for name, (res, args) in B._SIGNATURES.items():
+        ret, n = protos[name]
+        assert len(args) == n, (name, len(args), n)
+        if ret.startswith("const char"):
+            assert res is ctypes.c_char_p, name
+        elif ret == "int64_t":
+            assert res is ctypes.c_int64, name
+        else:
+            assert ret == "int" and res is ctypes.c_int, (name, ret)
