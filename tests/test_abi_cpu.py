@@ -231,9 +231,19 @@ def _declared_prototypes():
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"([A-Za-z_][\w \*]*?)\b(mgard_\w+)\s*\(([^;{]*?)\)\s*;", text, re.S):
             ret, name, params = m.group(1).strip(), m.group(2), " ".join(m.group(3).split())
-            n = 0 if params in ("", "void") else params.count(",") + 1
-            out[name] = (ret, n)
+            plist = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+            out[name] = (ret, len(plist), plist)
     return out
+
+
+def _ctype_matches(param, ct):
+    """Whether a ctypes argument type fits a C parameter declaration."""
+    if "*" in param:
+        return ct in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(ct, "_type_") and \
+            issubclass(ct, ctypes._Pointer)
+    base = param.replace("const ", "").split()[0]
+    return {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "size_t": ctypes.c_size_t,
+            "double": ctypes.c_double, "uint64_t": ctypes.c_uint64}.get(base) is ct
 
 
 def test_binding_signatures_match_header(lib):
@@ -243,8 +253,10 @@ def test_binding_signatures_match_header(lib):
     protos = _declared_prototypes()
     assert set(protos) == set(B.exported_symbols())
     for name, (res, args) in B._SIGNATURES.items():
-        ret, n = protos[name]
+        ret, n, plist = protos[name]
         assert len(args) == n, (name, len(args), n)
+        for param, ct in zip(plist, args):
+            assert _ctype_matches(param, ct), (name, param, ct)
         if ret.startswith("const char"):
             assert res is ctypes.c_char_p, name
         elif ret == "int64_t":
