@@ -263,3 +263,24 @@ def test_binding_signatures_match_header(lib):
             assert res is ctypes.c_int64, name
         else:
             assert ret == "int" and res is ctypes.c_int, (name, ret)
+
+
+def test_product_never_reaches_the_oracle():
+    # The oracle is test infrastructure: the package (binding, build, inputs)
+    # and the CUDA sources neither import nor name it, and bench.py imports
+    # it only in its oracle leg (the CPU baseline and the reference arm).
+    pkg = os.path.join(ROOT, "paper_2010_05872_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".hpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+                assert "mgard_oracle" not in text, f
+    bench = open(os.path.join(ROOT, "bench.py")).read()
+    imports = [m.start() for m in re.finditer(r"from oracle import", bench)]
+    assert len(imports) == 1
+    start = bench.index("def oracle_sample(")
+    end = bench.index("\ndef ", start + 1)
+    assert start < imports[0] < end
