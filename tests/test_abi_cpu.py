@@ -278,6 +278,11 @@ def test_product_never_reaches_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "mgard_oracle" not in text, f
+    # Nor does the oracle import the product (it shares no code with it).
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2010_05872_gb300" not in text and "libmgardgb" not in text, f
     bench = open(os.path.join(ROOT, "bench.py")).read()
     imports = [m.start() for m in re.finditer(r"from oracle import", bench)]
     assert len(imports) == 1
