@@ -744,6 +744,88 @@ def test_l2_bound_holds_for_worst_errors(dims, kind, stop):
         assert O.l2_error(err, H) <= tau * (1 + 1e-12)
 
 
+@pytest.mark.parametrize("n,h", [(5, 1.0), (9, 0.25), (17, 3.0)])
+def test_l2_error_unit_hat_closed_form(n, h):
+    # One unit nodal value at an interior node of a uniform 1D grid of
+    # spacing h is a hat function: its squared L2 norm is 2h/3.  The norm
+    # (not its square) is returned, and h enters to the power 1/2.
+    H = O.Hierarchy((n,), [h * np.arange(n, dtype=np.float64)])
+    e = np.zeros(n)
+    e[n // 2] = 1.0
+    assert O.l2_error(e, H) == pytest.approx(math.sqrt(2.0 * h / 3.0), rel=1e-14)
+    # An end node carries half a hat: h/3.
+    e = np.zeros(n)
+    e[0] = 1.0
+    assert O.l2_error(e, H) == pytest.approx(math.sqrt(h / 3.0), rel=1e-14)
+
+
+@pytest.mark.parametrize("dims", [(7,), (9, 5), (5, 6, 7), (4, 5, 3, 6)])
+def test_l2_error_constant_on_unit_box(dims):
+    # A constant c on [0,1]^d (any node spacing) has L2 norm |c|: every axis
+    # of the tensor mass product must contribute its full length 1.
+    rng = _rng(11)
+    coords = [np.concatenate([[0.0], np.sort(rng.uniform(0, 1, n - 2)), [1.0]]) for n in dims]
+    H = O.Hierarchy(dims, coords)
+    c = -2.75
+    assert O.l2_error(np.full(dims, c), H) == pytest.approx(abs(c), rel=1e-13)
+    # On a box of side lengths a_d the norm is |c| sqrt(prod a_d).
+    a = [1.0 + 0.5 * d for d in range(len(dims))]
+    H = O.Hierarchy(dims, [a[d] * coords[d] for d in range(len(dims))])
+    assert O.l2_error(np.full(dims, c), H) == pytest.approx(abs(c) * math.sqrt(np.prod(a)),
+                                                             rel=1e-13)
+
+
+def test_l2_error_multilinear_product_closed_form():
+    # A product of linear factors is reproduced exactly by the P1 function,
+    # so its norm is the product of the 1D integrals (closed form) on a
+    # nonuniform 3D grid: int_0^1 (1 + 2x)^2 = 13/3, int_0^1 y^2 = 1/3,
+    # int_0^1 (2 - z)^2 = 7/3.
+    dims = (6, 7, 5)
+    coords = [np.concatenate([[0.0], np.sort(_rng(s).uniform(0, 1, n - 2)), [1.0]])
+              for s, n in zip((3, 4, 5), dims)]
+    H = O.Hierarchy(dims, coords)
+    X, Y, Z = np.meshgrid(*coords, indexing="ij")
+    e = (1 + 2 * X) * Y * (2 - Z)
+    exact = math.sqrt(13.0 / 3.0 * 1.0 / 3.0 * 7.0 / 3.0)
+    assert O.l2_error(e, H) == pytest.approx(exact, rel=1e-13)
+
+
+def test_l2_error_piecewise_linear_by_quadrature():
+    # An arbitrary P1 function on nonuniform 1D and 2D grids, integrated
+    # cell by cell with 3-point Gauss-Legendre quadrature (exact for the
+    # squared piecewise-(bi)linear integrand) by an evaluator that does not
+    # use the mass matrix.
+    gx, gw = np.polynomial.legendre.leggauss(3)
+    rng = _rng(21)
+    x = np.cumsum(rng.uniform(0.2, 1.5, 8))
+    y = np.cumsum(rng.uniform(0.3, 1.1, 6))
+    e2 = rng.standard_normal((8, 6))
+    e1 = e2[:, 2].copy()
+
+    def cell_pts(a, b):
+        return 0.5 * (b - a) * gx + 0.5 * (a + b), 0.5 * (b - a) * gw
+
+    s1 = 0.0
+    for i in range(len(x) - 1):
+        p, w = cell_pts(x[i], x[i + 1])
+        t = (p - x[i]) / (x[i + 1] - x[i])
+        s1 += float(np.sum(w * ((1 - t) * e1[i] + t * e1[i + 1]) ** 2))
+    assert O.l2_error(e1, O.Hierarchy((8,), [x])) == pytest.approx(math.sqrt(s1), rel=1e-13)
+
+    s2 = 0.0
+    for i in range(len(x) - 1):
+        px, wx = cell_pts(x[i], x[i + 1])
+        tx = (px - x[i]) / (x[i + 1] - x[i])
+        for j in range(len(y) - 1):
+            py, wy = cell_pts(y[j], y[j + 1])
+            ty = (py - y[j]) / (y[j + 1] - y[j])
+            TX, TY = np.meshgrid(tx, ty, indexing="ij")
+            f = ((1 - TX) * (1 - TY) * e2[i, j] + TX * (1 - TY) * e2[i + 1, j]
+                 + (1 - TX) * TY * e2[i, j + 1] + TX * TY * e2[i + 1, j + 1])
+            s2 += float(np.sum(np.outer(wx, wy) * f ** 2))
+    assert O.l2_error(e2, O.Hierarchy((8, 6), [x, y])) == pytest.approx(math.sqrt(s2), rel=1e-13)
+
+
 @pytest.mark.parametrize("dims,kind,stop", [((17, 17, 9), "u", 0), ((12, 10, 9), "g", 1)])
 def test_linf_optimal_widths(dims, kind, stop):
     coords = None if kind == "u" else [F.geometric_coords(n, 1.08) for n in dims]
