@@ -418,6 +418,18 @@ int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, v
 int mgard_batch_release(void);
 int mgard_batch_stats(uint64_t* out, int n);
 
+/* Test support for the bounded device-side waits (no counterpart in the
+ * paper).  Launches the batched kernel with a one-item schedule whose
+ * dependency can never be met (the item waits for a tile of its own stage)
+ * and a wait limit of `limit_ns` (0 < limit_ns <= 1e9) instead of 2 s: the
+ * kernel's wait gives up, sets the per-device status word and ends without
+ * running a tile, so the next mgard_quantize / mgard_value_range on this
+ * device returns MGARD_ERR_TIMEOUT (and clears the word).  Allocates and
+ * frees a few hundred bytes of device memory; synchronizes `stream`.
+ * Returns MGARD_ERR_ARG for a limit out of range, MGARD_ERR_CUDA on a CUDA
+ * error, else MGARD_OK. */
+int mgard_batch_wait_selftest(int64_t limit_ns, void* stream);
+
 /* Serving: a request loop with continuous batching on the current device
  * (an interface of this library; the paper compresses one field per call).
  * A request is a whole compression (host field -> value range, decomposition
@@ -464,32 +476,39 @@ int mgard_server_drain(void* server, double timeout_s);
 int mgard_server_counters(void* server, int64_t* out5);
 int mgard_server_destroy(void* server);
 
-/* Allocation-free decomposition (the paper has no counterpart; an interface
- * choice).  Same result as mgard_decompose (Section 2, decomposition;
- * Algorithm 1 lines 12-16) with the same kernels, for callers that must not
- * allocate device memory while they compress -- e.g. an in-situ simulation
- * that has reserved nearly all of HBM for its own state, where a cudaMalloc
- * could fail and may wait for work in flight on other streams.
+/* Allocation-free decomposition.  The paper has no counterpart: this is an
+ * interface for callers that must not allocate device memory while they
+ * compress -- e.g. an in-situ simulation that has reserved nearly all of HBM
+ * for its own state, where a cudaMalloc could fail and may wait for work in
+ * flight on other streams.  The result equals mgard_decompose's (same
+ * kernels, same rounding).
  *  - No workspace argument: the level workspace and the plan tables live in
  *    one static device array of 32 MiB per device.  Shapes whose tables plus
  *    workspace (about 2/7 of the field in 3D) do not fit are rejected with
  *    MGARD_ERR_WORKSPACE before any work is enqueued (e.g. up to ~110 MB of
  *    FP32 field).
- *  - Nothing is allocated: no cudaMalloc, cudaFree, pinned host memory or
- *    allocating library.  The first call on a device looks up the array's
- *    device address (cudaGetSymbolAddress, checked); a call with a new
- *    (dims, coords, dtype) builds host tables and copies them into the array
- *    with cudaMemcpyAsync from pageable memory.  Make the first call for a
- *    shape outside any stream capture.
+ *  - The calls allocate nothing: no cudaMalloc, cudaFree, pinned host
+ *    memory or allocating library.  The array and this library's kernels
+ *    are part of the library's device code, which the CUDA runtime loads
+ *    when it is first needed (lazily, the default since CUDA 12.2): the
+ *    first call on a device, which also looks up the array's device address
+ *    (cudaGetSymbolAddress, checked), is where the 32 MiB and the code are
+ *    reserved (at library load under CUDA_MODULE_LOADING=EAGER).  Make one
+ *    small warm-up call at start-up, before the memory is committed
+ *    elsewhere and outside any stream capture; later calls reserve nothing.
+ *    A call with a new (dims, coords, dtype) builds host tables and copies
+ *    them into the array with cudaMemcpyAsync from pageable memory.
  *  - Only the array's first word (the wait-timeout status) must start at
  *    zero; each call clears it on `stream` before its kernels run.
  *  - Calls share the one array per device: two calls whose work overlaps on
  *    the device (other streams, other host threads, or a new shape while an
  *    earlier call's kernels still run) race on it.  Order them on one stream
  *    or synchronize between them.
- *  - `timed_out` may be NULL (the call returns once the work is enqueued).
- *    Otherwise the call waits for `stream`, sets *timed_out to 1 if a bounded
- *    device-side wait gave up (then returns MGARD_ERR_TIMEOUT), else 0.
+ *  - `timed_out` may be NULL: the call returns once the work is enqueued and
+ *    a bounded device-side wait that gave up is not reported (the next call
+ *    clears the status word; the field may then be partly transformed).
+ *    Otherwise the call waits for `stream`, sets *timed_out to 1 if such a
+ *    wait gave up (then returns MGARD_ERR_TIMEOUT), else 0.
  * Arguments, layout and the other errors are those of mgard_decompose. */
 int mgard_decompose_noalloc(int ndim, const int64_t* dims, const double* const* coords, int dtype,
                             int stop_level, void* data, int* timed_out, void* stream);

@@ -122,6 +122,7 @@ _SIGNATURES = {
     "mgard_batch_autotune": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(_VP), _VP,
                                             ctypes.c_size_t, _VP, ctypes.POINTER(ctypes.c_int)]),
     "mgard_batch_release": (ctypes.c_int, []),
+    "mgard_batch_wait_selftest": (ctypes.c_int, [ctypes.c_int64, _VP]),
     "mgard_batch_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "mgard_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
     "mgard_server_submit": (ctypes.c_int, [_VP, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
@@ -305,6 +306,13 @@ def mgard_batch_stats():
 
 def mgard_batch_release() -> int:
     return lib().mgard_batch_release()
+
+
+def mgard_batch_wait_selftest(limit_ns: int, stream) -> int:
+    """Run the batched kernel on a schedule whose dependency is never met,
+    with a wait limit of limit_ns; the next quantize / value-range call on
+    the device reports the timeout."""
+    return lib().mgard_batch_wait_selftest(int(limit_ns), stream)
 
 
 OP_COMPRESS, OP_DECOMPRESS = 1, 2

@@ -1182,6 +1182,11 @@ int noalloc_tables(DevPlan& p, char* dst, size_t cap, size_t* used, cudaStream_t
   else fill_levels<double>(p, offs, dst, p.lvd);
   for (int a = 0; a < 3; ++a) p.lev[a] = reinterpret_cast<const uint8_t*>(dst + lev_off[a]);
   p.lev01 = reinterpret_cast<const uint8_t*>(dst + lev01_off);
+  // Node positions and coordinates complete the plan as upload() does.
+  p.pos.assign(h.L + 1, {});
+  for (int l = 0; l <= h.L; ++l)
+    for (int a = 0; a < 3; ++a) p.pos[l][a] = reinterpret_cast<const int32_t*>(dst + pos_off[l][a]);
+  for (int a = 0; a < 3; ++a) p.xc[a] = reinterpret_cast<const double*>(dst + x_off[a]);
   *used = total;
   return MGARD_OK;
 }

@@ -85,7 +85,8 @@ constexpr int kFinNS = 4, kFinT1 = FinishCfg<float>::T1;
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ items, int nitems,
              unsigned int* __restrict__ head, unsigned int* __restrict__ done,
-             unsigned int* __restrict__ status, unsigned long long* __restrict__ stats) {
+             unsigned int* __restrict__ status, unsigned long long* __restrict__ stats,
+             unsigned long long wait_limit_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ int s_abort;
@@ -105,7 +106,7 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
       const uint64_t t0 = global_ns();
       while (ld_acquire_gpu(done + item.z) < static_cast<unsigned>(item.w)) {
         __nanosleep(256);
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > wait_limit_ns) {
           *reinterpret_cast<volatile unsigned*>(status) = 2u;
           s_abort = 1;
           break;
@@ -429,7 +430,8 @@ int build_batch(int n, const int64_t* dims3, void* const* data, char* ws, size_t
   unsigned* a_done = bp.d_counters + 1;
   unsigned* a_status = status;
   unsigned long long* a_stats = bp.d_stats;
-  void* args[] = {&a_st, &a_it, &a_n, &a_head, &a_done, &a_status, &a_stats};
+  unsigned long long a_wait = kWaitLimitNs;
+  void* args[] = {&a_st, &a_it, &a_n, &a_head, &a_done, &a_status, &a_stats, &a_wait};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof kp);
   kp.func = reinterpret_cast<void*>(batch_kernel);
@@ -593,6 +595,39 @@ int mgard_batch_autotune(int nfields, const int64_t* dims3, void* const* data, v
     choice_out[3] = best.groups;
   }
   return MGARD_OK;
+}
+
+int mgard_batch_wait_selftest(int64_t limit_ns, void* stream) {
+  if (limit_ns <= 0 || limit_ns > 1000000000LL) return MGARD_ERR_ARG;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // One stage (never run: the only item aborts in its wait), one item that
+  // waits for one finished tile of its own stage, counters and stats at 0.
+  const size_t b_st = up(sizeof(BatchStage), 256);
+  const size_t b_it = up(sizeof(int4), 256);
+  const size_t b_ct = up(2 * sizeof(unsigned), 256);
+  const size_t b_sx = up(sizeof(unsigned long long) * 3 * kBKinds, 256);
+  void* dmem = nullptr;
+  if (cudaMalloc(&dmem, b_st + b_it + b_ct + b_sx) != cudaSuccess) return MGARD_ERR_CUDA;
+  char* d = static_cast<char*>(dmem);
+  const int4 item = make_int4(0, 0, 0, 1);
+  int rc = MGARD_OK;
+  if (cudaMemsetAsync(d, 0, b_st + b_it + b_ct + b_sx, s) != cudaSuccess ||
+      cudaMemcpyAsync(d + b_st, &item, sizeof item, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    rc = MGARD_ERR_CUDA;
+  } else {
+    batch_kernel<<<1, kBatchThreads, 0, s>>>(
+        reinterpret_cast<const BatchStage*>(d), reinterpret_cast<const int4*>(d + b_st), 1,
+        reinterpret_cast<unsigned*>(d + b_st + b_it),
+        reinterpret_cast<unsigned*>(d + b_st + b_it) + 1, c->flags + 1,
+        reinterpret_cast<unsigned long long*>(d + b_st + b_it + b_ct),
+        static_cast<unsigned long long>(limit_ns));
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      rc = MGARD_ERR_CUDA;
+  }
+  cudaFree(dmem);
+  return rc;
 }
 
 int mgard_batch_release(void) {

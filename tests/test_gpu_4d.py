@@ -3,23 +3,18 @@ oracle: decomposition and recomposition element by element, the level-wise
 quantizer bit-exact given the same coefficients and tolerances, and the
 compressed round trip within the L-inf bound.
 
-Tolerances as for 1-3D: FP64 within 1e-12 max|u|, FP32 within
-2e-5 (L + 1) max|u| (four axes of operators with max norm < 2 and a few
-dozen roundings per value and level)."""
+Tolerances as for 1-3D (tests/tolerances.py): FP64 within 1e-12 max|u|,
+FP32 within 24 u (L + 1) max|u| with u = 2^-24 (four axes of operators with
+max norm < 2 and a few dozen roundings per value and level)."""
 import numpy as np
 import pytest
 
 from oracle import mgard_oracle as O
 from paper_2010_05872_gb300 import binding as B
 from paper_2010_05872_gb300 import fields as F
+from tolerances import TOL64, tol32
 
 pytestmark = pytest.mark.gpu
-
-TOL64 = 1e-12
-
-
-def tol32(L):
-    return 2e-5 * (L + 1)
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -8,12 +8,9 @@ import pytest
 from oracle import mgard_oracle as O
 from paper_2010_05872_gb300 import binding as B
 from paper_2010_05872_gb300 import fields as F
+from tolerances import tol32
 
 pytestmark = pytest.mark.gpu
-
-
-def tol32(L):
-    return 2e-5 * (L + 1)
 
 
 @pytest.fixture(scope="module")
@@ -96,3 +93,29 @@ def test_batch_rejects_bad_arguments(cuda):
     assert B.mgard_batch_decompose(shapes, ptrs, ws.data_ptr(), ws.numel() - 512, 0) == -5
     assert B.mgard_batch_decompose([(33, 33, 2)], ptrs, ws.data_ptr(), ws.numel(), 0) == -2
     assert B.mgard_batch_decompose(shapes, [x.data_ptr() + 2], ws.data_ptr(), ws.numel(), 0) == -1
+
+
+def test_bounded_wait_runs_out_and_is_reported(cuda):
+    """A batched schedule whose dependency is never met, with a 5 ms wait
+    limit: the kernel's wait gives up instead of spinning, the next value
+    range call reports MGARD_ERR_TIMEOUT, and the call after it (and the
+    transforms) work again."""
+    import time
+    torch = cuda
+    stream = torch.cuda.current_stream().cuda_stream
+    x = torch.from_numpy(F.grf_field((33, 33, 33), seed=3)).cuda()
+    torch.cuda.synchronize()
+    assert B.mgard_batch_wait_selftest(0, stream) == -1
+    t0 = time.perf_counter()
+    assert B.mgard_batch_wait_selftest(5_000_000, stream) == 0
+    assert time.perf_counter() - t0 < 1.0
+    with pytest.raises(B.MgardError) as e:
+        B.value_range(x)
+    assert e.value.code == -9
+    lo, hi = B.value_range(x)
+    assert lo == x.min().item() and hi == x.max().item()
+    r = x.clone()
+    B.decompose(r)
+    B.recompose(r)
+    torch.cuda.synchronize()
+    assert (r - x).abs().max().item() <= tol32(4) * x.abs().max().item()

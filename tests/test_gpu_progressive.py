@@ -2,7 +2,7 @@
 decomposed field) and of the iso-surface area with the FP64 oracle.
 
 Tolerances: partial recomposition as the transform (FP64 1e-12, FP32
-2e-5 (L + 1) relative to max |u|); the iso area relative 1e-10 in FP64 and
+tol32(L) = 24 u (L + 1) relative to max |u|, u = 2^-24); the iso area relative 1e-10 in FP64 and
 1e-5 in FP32 (the vertex classification is exact in both; the crossing
 points and areas carry the data's rounding)."""
 import numpy as np
@@ -11,6 +11,7 @@ import pytest
 from oracle import mgard_oracle as O
 from paper_2010_05872_gb300 import binding as B
 from paper_2010_05872_gb300 import fields as F
+from tolerances import tol32
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +44,7 @@ def test_recompose_partial_matches_oracle(cuda, dims, kind, stop, dtype):
     umc = O.decompose(u, H, stop).astype(dtype)
     x = torch.from_numpy(np.ascontiguousarray(umc)).cuda()
     scale = np.abs(u).max()
-    tol = 1e-12 if dtype == np.float64 else 2e-5 * (H.L + 1)
+    tol = 1e-12 if dtype == np.float64 else tol32(H.L)
     for k in range(stop, H.L + 1):
         got = B.recompose_partial(x, k, coords, stop).cpu().numpy().astype(np.float64)
         exp = O.recompose_partial(umc.astype(np.float64), H, stop, k)
@@ -103,7 +104,7 @@ def test_full_size_513_cubed_progressive(cuda):
     x = u.clone()
     B.decompose(x)
     scale = u.abs().max().item()
-    tol = 2e-5 * (L + 1)
+    tol = tol32(L)
     full = B.recompose_partial(x, L)
     assert (full - u).abs().max().item() / scale <= tol
     del full

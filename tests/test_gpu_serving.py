@@ -1,13 +1,15 @@
 """GPU tests of the serving loop (continuous batching): every request of a
 mixed compress/decompress stream completes, each result equals the same
 request run alone through the blocking host entry points, decompressed
-fields meet their bound, and admission keeps the device memory in use within
-the budget."""
+fields meet their bound, served results agree with the FP64 oracle, and
+admission keeps the device memory in use within the budget."""
 import numpy as np
 import pytest
 
+from oracle import mgard_oracle as O
 from paper_2010_05872_gb300 import binding as B
 from paper_2010_05872_gb300 import fields as F
+from tolerances import tol32
 
 pytestmark = pytest.mark.gpu
 
@@ -86,6 +88,59 @@ def test_mixed_stream_matches_alone(cuda):
                 assert torch.equal(out, alone)
                 err = (out.double() - fields[i].double()).abs().max().item()
                 assert err <= arg
+    finally:
+        srv.close()
+
+
+def test_served_results_match_the_oracle(cuda):
+    """Eight served requests (2D and 3D; four compress, four decompress)
+    checked against the FP64 oracle: compressed labels are the oracle's
+    quantization (Section 4.1) of the device coefficients, which match the
+    oracle's decomposition; the oracle's own dequantization and
+    recomposition of the served labels meet the bound; decompressed fields
+    match the oracle's recomposition of the same labels."""
+    torch = cuda
+    shapes = [(257, 300), (1025, 129), (65, 65, 65), (33, 40, 57)]
+    rels = [1e-2, 1e-3, 1e-4, 1e-3]
+    srv = B.Server(hbm_budget=2 << 30, slots=4)
+    try:
+        us = [F.grf_field(s, seed=70 + i) for i, s in enumerate(shapes)]
+        fields = [torch.from_numpy(u.ravel()).pin_memory() for u in us]
+        comp = []
+        for i, s in enumerate(shapes):
+            out = torch.empty(fields[i].numel(), dtype=torch.int64).pin_memory()
+            comp.append((srv.submit(B.OP_COMPRESS, s, fields[i], out, rel_bound=rels[i]), out))
+        srv.drain()
+        taus = {rid: tau for rid, st, _, tau in srv.poll() if st == 0}
+        assert len(taus) == len(shapes)
+        dec = []
+        for i, s in enumerate(shapes):
+            rid, labels = comp[i]
+            out = torch.empty(fields[i].numel(), dtype=torch.float32).pin_memory()
+            dec.append((srv.submit(B.OP_DECOMPRESS, s, labels, out, tau=taus[rid]), out))
+        srv.drain()
+        assert all(st == 0 for _, st, _, _ in srv.poll())
+        for i, s in enumerate(shapes):
+            H = O.Hierarchy(s)
+            u = us[i].astype(np.float64)
+            rid, labels = comp[i]
+            tau = taus[rid]
+            assert tau == pytest.approx(rels[i] * O.value_range(u), rel=1e-15)
+            t = B.mgard_level_tolerances(s, None, 0, tau)
+            np.testing.assert_allclose(t, O.level_tolerances(H, 0, tau), rtol=1e-12)
+            lab = labels.numpy().reshape(s)
+            x = torch.from_numpy(us[i]).cuda()
+            B.decompose(x)
+            coeffs = x.cpu().numpy().astype(np.float64)
+            assert np.array_equal(lab, O.quantize(coeffs, H, 0, t))
+            exp = O.decompose(u, H)
+            assert np.abs(coeffs - exp).max() <= tol32(H.L) * np.abs(u).max()
+            deq = O.dequantize(lab, H, 0, t, dtype=np.float32).astype(np.float64)
+            rec_o = O.recompose(deq, H)
+            assert np.abs(rec_o - u).max() <= tau
+            got = dec[i][1].numpy().reshape(s).astype(np.float64)
+            assert np.abs(got - rec_o).max() <= tol32(H.L) * np.abs(u).max()
+            assert np.abs(got - u).max() <= tau
     finally:
         srv.close()
 
