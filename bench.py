@@ -44,6 +44,7 @@ METRIC = ("decompose+recompose GB/s and % HBM roofline (FP32 vs FP64 GPU, at sta
 DIMS = (513, 513, 513)
 BOUNDS = (1e-2, 1e-3, 1e-4, 1e-5)
 FALLBACK_HBM = 6800.0
+QUANT_KERNELS = ("quantize_kernel", "dequantize_kernel", "minmax_partial_kernel")
 
 
 # The paper's own figures with the hardware it names (Section 6; one core of
@@ -117,6 +118,39 @@ def oracle_sample(n: int, reps: int):
         times.append(time.perf_counter() - t0)
         assert np.abs(rec - u).max() <= tau
     return u.nbytes, times
+
+
+def oracle_parity(cases):
+    """The FP32 (or FP64) GPU results of the benchmarked configurations
+    against the FP64 oracle, after every timed region: per case, the
+    decomposition's max error relative to max|u|, and per bound the GPU
+    recomposition of the bound's dequantized labels against the oracle's
+    recomposition of the same labels (relative to max|u| and to tau).  Each
+    case: {"name", "u" (host field), "coords", "stop", "coeffs" (GPU
+    decomposition), "bounds": {rel: (tau, dequantized labels, GPU
+    reconstruction)}}."""
+    import numpy as np
+    from oracle import mgard_oracle as O
+    out = {}
+    for c in cases:
+        u = c["u"].astype(np.float64)
+        H = O.Hierarchy(u.shape, c["coords"])
+        scale = float(np.abs(u).max())
+        t0 = time.perf_counter()
+        exp = O.decompose(u, H, c["stop"])
+        res = {"decompose_rel": float(np.abs(c["coeffs"].astype(np.float64) - exp).max()) / scale}
+        del exp
+        per = {}
+        for rel, (tau, deq, rec) in c["bounds"].items():
+            rec_o = O.recompose(deq.astype(np.float64), H, c["stop"])
+            d = float(np.abs(rec.astype(np.float64) - rec_o).max())
+            per[f"{rel:g}"] = {"recompose_same_labels_rel": d / scale,
+                               "recompose_same_labels_over_tau": d / tau,
+                               "linf_over_tau": float(np.abs(rec.astype(np.float64) - u).max()) / tau}
+        res["bounds"] = per
+        res["oracle_seconds"] = time.perf_counter() - t0
+        out[c["name"]] = res
+    return out
 
 
 def cpu_baseline_subprocess(n: int, reps: int):
@@ -353,6 +387,29 @@ def run_gpu(args, rank, world, local_rank):
         linf[f"{rel:g}"] = err / tau
         assert err <= tau, (rel, err, tau)
 
+    # The results the oracle leg compares with the FP64 oracle (after every
+    # timed region): the decomposition and, per bound, the dequantized labels
+    # and the reconstruction.
+    want_parity = rank == 0 and world == 1 and not args.no_cpu_baseline
+    parity_cases = []
+    if want_parity:
+        lo2, hi2 = B.value_range(u)
+        x.copy_(u)
+        B.decompose(x, None, 0, ws)
+        c2 = {"name": "513cubed_fp32", "u": u_host, "coords": None, "stop": 0,
+              "coeffs": x.cpu().numpy(), "bounds": {}}
+        for rel in BOUNDS:
+            tau = rel * (hi2 - lo2)
+            x.copy_(u)
+            B.decompose(x, None, 0, ws)
+            B.quantize(x, tau, None, 0, labels)
+            B.dequantize(labels, tau, x.dtype, None, 0, out=x)
+            deq = x.cpu().numpy()
+            B.recompose(x, None, 0, ws)
+            c2["bounds"][rel] = (tau, deq, x.cpu().numpy())
+        parity_cases.append(c2)
+    x.copy_(u)
+
     def barrier():
         if world > 1:
             torch.distributed.barrier()
@@ -382,7 +439,12 @@ def run_gpu(args, rank, world, local_rank):
     for e in evs:
         for j, k in enumerate(phase):
             phase[k] += e[j].elapsed_time(e[j + 1]) / kb
-    top = max(trace, key=lambda r: r["total_ms"])
+    # The metric is decompose + recompose: the roofline block describes the
+    # transform kernel with the largest summed device time; the quantizer's
+    # largest kernel is reported beside it.
+    transform = [r for r in trace if r["kernel"] not in QUANT_KERNELS]
+    top = max(transform, key=lambda r: r["total_ms"])
+    qtop = max((r for r in trace if r["kernel"] in QUANT_KERNELS), key=lambda r: r["total_ms"])
 
     # Timed region: K steps; only the dominant kernel's launches bracketed.
     barrier()
@@ -423,6 +485,13 @@ def run_gpu(args, rank, world, local_rank):
     tt = timed_top
     achieved = (tt["bytes"] / tt["launches"]) / (tt["total_ms"] / tt["launches"] * 1e-3) / 1e9
     total_kernel_ms = sum(r["total_ms"] for r in trace)
+    # Whole-path roofline on the path's algorithmic byte count
+    # B_alg = 2 (decompose + recompose) x 2 s sum_{l > l~} #N_l.
+    b_alg = path_bytes(DIMS, 0, 4)
+    dec_rec_ms = phase["decompose"] + phase["recompose"]
+    path_frac = b_alg / (dec_rec_ms * 1e-3) / 1e9 / peak
+    # The same against the nominal HBM3e bandwidth (7.9 TB/s), as a second column.
+    path_frac_nominal = b_alg / (dec_rec_ms * 1e-3) / 1e9 / 7900.0
     roofline = {
         "bound": "hbm", "kernel": top["kernel"], "level": top["level"],
         "achieved": achieved, "peak": peak, "peak_source": f"{peak_src} HBM copy bandwidth",
@@ -432,18 +501,15 @@ def run_gpu(args, rank, world, local_rank):
         "avg_launch_ms": tt["total_ms"] / tt["launches"],
         "launches_timed": tt["launches"],
         "share_of_kernel_time": top["total_ms"] / total_kernel_ms,
+        "path": {"what": "decompose + recompose of the 513^3 FP32 field (the metric's path)",
+                 "alg_bytes": b_alg, "ms": dec_rec_ms, "achieved": b_alg / (dec_rec_ms * 1e-3) / 1e9,
+                 "frac": path_frac},
+        "quantizer_top": {"kernel": qtop["kernel"], "level": qtop["level"],
+                          "achieved": qtop["bytes"] / (qtop["total_ms"] * 1e-3) / 1e9,
+                          "frac": qtop["bytes"] / (qtop["total_ms"] * 1e-3) / 1e9 / peak,
+                          "traffic": traffic_for(qtop["kernel"], qtop["level"]),
+                          "source": "breakdown pass (every launch event-timed)"},
     }
-    # Whole-path roofline on the path's algorithmic byte count
-    # B_alg = 2 (decompose + recompose) x 2 s sum_{l<=L} #N_l.
-    sizes = []
-    n = list(DIMS)
-    while min(n) > 3:
-        sizes.append(int(np.prod(n)))
-        n = [v // 2 + 1 for v in n]
-    b_alg = 2 * 2 * 4 * sum(sizes)
-    path_frac = b_alg / ((phase["decompose"] + phase["recompose"]) * 1e-3) / 1e9 / peak
-    # The same against the nominal HBM3e bandwidth (7.9 TB/s), as a second column.
-    path_frac_nominal = b_alg / ((phase["decompose"] + phase["recompose"]) * 1e-3) / 1e9 / 7900.0
 
     kinds = {}
     for r in trace:
@@ -476,14 +542,66 @@ def run_gpu(args, rank, world, local_rank):
     t64 = sum(ph64.values()) / k64
     x64.copy_(u64)
     tau64 = step(x64, 1e-3)
+    # The FP64 path against both roofs: HBM on its own bytes (8 B per value)
+    # and the measured FP64 FMA rate on the path's algorithmic flops.
+    dr64 = (ph64["decompose"] + ph64["recompose"]) / k64
+    dfma = B.mgard_trace_fma_rate(B.F64)
+    flops = path_flops(DIMS, 0)
+    b64 = path_bytes(DIMS, 0, 8)
+    t_hbm, t_alu = b64 / (peak * 1e9), flops / dfma
     fp64 = {
         "ms_per_step": t64, "value_gbs_f32_bytes": nbytes / (t64 * 1e-3) / 1e9,
         "value_gbs_own_bytes": 2 * nbytes / (t64 * 1e-3) / 1e9,
-        "dec_rec_ms": (ph64["decompose"] + ph64["recompose"]) / k64,
+        "dec_rec_ms": dr64,
+        "dec_rec_gbs": nbytes / (dr64 * 1e-3) / 1e9,
         "linf_over_tau_1e-3": (x64 - u64).abs().max().item() / tau64,
         "steps": k64,
+        "roofline": {
+            **({"bound": "alu", "achieved": flops / (dr64 * 1e-3) / 1e12, "peak": dfma / 1e12,
+                "unit": "TFLOP/s", "frac": t_alu / (dr64 * 1e-3)} if t_alu > t_hbm else
+               {"bound": "hbm", "achieved": b64 / (dr64 * 1e-3) / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": t_hbm / (dr64 * 1e-3)}),
+            "alg_flops": flops, "alg_bytes": b64,
+            "fp64_fma_peak_tflops": dfma / 1e12,
+            "fp32_fma_peak_tflops": B.mgard_trace_fma_rate(B.F32) / 1e12,
+            "roof_ms": {"hbm": t_hbm * 1e3, "fp64_fma": t_alu * 1e3},
+            "hbm_frac": t_hbm / (dr64 * 1e-3),
+            "note": ("decompose + recompose of the 513^3 field in FP64; FMA peaks measured live "
+                     "(mgard_trace_fma_rate: independent dependent-FMA chains, best of 3); flops "
+                     "counted per level from the method's steps (bench.path_flops)"),
+        },
     }
     del x64, u64, labels
+
+    # The other single-field configurations: 500x500x100 FP32 with geometric
+    # z (stopping levels 3 and 0) and 65^3 FP64 (full depth), each timed
+    # (median of untimed-region runs) with its L-inf check at 1e-3 x range.
+    nonuniform = {}
+    dims3 = (500, 500, 100)
+    coords3 = [F.uniform_coords(500), F.uniform_coords(500), F.geometric_coords(100, 1.03)]
+    u3h = F.front_field(dims3, coords3)
+    for stop3 in (3, 0):
+        r3, c3 = measure_config(B, torch, stream, u3h, coords3, stop3, reps=10,
+                                keep=want_parity)
+        r3["path_roofline_frac_dec_rec"] = (path_bytes(dims3, stop3, 4) /
+                                            ((r3["decompose_ms"] + r3["recompose_ms"]) * 1e-3)
+                                            / 1e9 / peak)
+        r3["alg_bytes"] = path_bytes(dims3, stop3, 4)
+        nonuniform[f"stop{stop3}"] = r3
+        if c3:
+            c3["name"] = f"500x500x100_fp32_stop{stop3}"
+            parity_cases.append(c3)
+    nonuniform["note"] = ("500x500x100 FP32, x/y uniform, z geometric (ratio 1.03), sinusoids + "
+                          "tanh front; stands in for the paper's Hurricane shape; median of 10 "
+                          "runs per direction; path fraction on 2 x 2 s sum_{l>l~} #N_l of "
+                          "measured HBM")
+    u1h = F.sinusoid_field((65, 65, 65), seed=F.SEED_TINY)
+    tiny, c1 = measure_config(B, torch, stream, u1h, None, 0, reps=20, keep=want_parity)
+    tiny["note"] = ("65^3 FP64 sinusoids + noise, full depth (L=5); latency-bound, so reported "
+                    "as time: decompose + quantize + dequantize + recompose")
+    if c1:
+        c1["name"] = "65cubed_fp64"
+        parity_cases.append(c1)
 
     # Adaptive stopping level (Algorithm 1): the level chosen per bound, and
     # at 1e-3 x range the time of the adaptive decomposition against the
@@ -738,9 +856,17 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return
     cpu = cpu_all = None
+    fp32_err = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_subprocess(257, 3)
         cpu_all = cpu_baseline_all_cores(257, os.cpu_count() or 1)
+        fp32_err = oracle_parity(parity_cases)
+        fp32_err["note"] = ("GPU results against the FP64 oracle, computed after the timed "
+                            "regions: decompose_rel = max |GPU decomposition - oracle| / max|u|; "
+                            "per bound, the GPU recomposition of the GPU's dequantized labels "
+                            "against the oracle's recomposition of the same labels, and the "
+                            "GPU reconstruction's L-inf error over tau")
+        del parity_cases
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -758,7 +884,10 @@ def run_gpu(args, rank, world, local_rank):
         "quality": quality,
         "gpu_launches": launches,
         "clocks": clocks.summary(t0, t1),
+        "fp32_err_vs_oracle": fp32_err,
         "fp64": fp64,
+        "nonuniform": nonuniform,
+        "tiny": tiny,
         "adaptive": adaptive,
         "progressive": progressive,
         "nd4": nd4,
@@ -771,6 +900,61 @@ def run_gpu(args, rank, world, local_rank):
         "src_hash": src_hash(),
     }
     print(json.dumps(line))
+
+
+def measure_config(B, torch, stream, u_host, coords, stop, reps, keep):
+    """Time decompose, quantize, dequantize and recompose of one field at
+    1e-3 x range (median of `reps` runs, events on the stream) and check the
+    L-inf bound.  With `keep`, also return the field, the decomposition, the
+    dequantized labels and the reconstruction for the oracle comparison."""
+    import numpy as np
+    dims = u_host.shape
+    dt = torch.float64 if u_host.dtype == np.float64 else torch.float32
+    u = torch.from_numpy(u_host).cuda()
+    x = u.clone()
+    ws = B.workspace(dims, dt)
+    labels = torch.empty(dims, dtype=torch.int64, device=u.device)
+    lo, hi = B.value_range(u)
+    tau = 1e-3 * (hi - lo)
+    B.decompose(x, coords, stop, ws)
+    B.recompose(x, coords, stop, ws)
+    ph = {k: [] for k in ("decompose", "quantize", "dequantize", "recompose")}
+    for _ in range(reps):
+        x.copy_(u)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        B.decompose(x, coords, stop, ws)
+        ev[1].record(stream)
+        B.quantize(x, tau, coords, stop, labels)
+        ev[2].record(stream)
+        B.dequantize(labels, tau, dt, coords, stop, out=x)
+        ev[3].record(stream)
+        B.recompose(x, coords, stop, ws)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for j, k in enumerate(ph):
+            ph[k].append(ev[j].elapsed_time(ev[j + 1]))
+    med = {k: statistics.median(v) for k, v in ph.items()}
+    err = float((x.double() - u.double()).abs().max().item())
+    assert err <= tau, (dims, stop, err, tau)
+    nbytes = u_host.nbytes
+    res = {"dims": list(dims), "stop_level": stop, "dtype": "f64" if dt == torch.float64 else "f32",
+           "decompose_ms": med["decompose"], "recompose_ms": med["recompose"],
+           "quantize_ms": med["quantize"], "dequantize_ms": med["dequantize"],
+           "total_ms": sum(med.values()),
+           "dec_rec_gbs": nbytes / ((med["decompose"] + med["recompose"]) * 1e-3) / 1e9,
+           "linf_over_tau_1e-3": err / tau, "tau": tau}
+    case = None
+    if keep:
+        rec = x.cpu().numpy()
+        x.copy_(u)
+        B.decompose(x, coords, stop, ws)
+        coeffs = x.cpu().numpy()
+        B.quantize(x, tau, coords, stop, labels)
+        B.dequantize(labels, tau, dt, coords, stop, out=x)
+        case = {"u": u_host, "coords": coords, "stop": stop, "coeffs": coeffs,
+                "bounds": {1e-3: (tau, x.cpu().numpy(), rec)}}
+    return res, case
 
 
 def run_kernel_case(args):
@@ -819,6 +1003,52 @@ def run_kernel_case(args):
     err = (x - u).abs().max().item() / (u.max() - u.min()).item()
     print(json.dumps({"kernel_case": "x".join(map(str, dims)) + " FP32 range+dec+quant+dequant+rec",
                       "ms_per_step": ms, "linf_over_range": err}))
+
+
+def level_sizes(dims):
+    """Node counts of the levels L, L-1, ..., 0 of a grid (every axis
+    coarsened n -> n // 2 + 1 until the smallest axis has 3 nodes)."""
+    out, n = [], list(dims)
+    while True:
+        out.append(list(n))
+        if min(n) <= 3:
+            return out
+        n = [v // 2 + 1 for v in n]
+
+
+def path_bytes(dims, stop, es):
+    """Algorithmic bytes of decompose + recompose: one read and one write of
+    every decomposed level's grid per direction, 2 x 2 s sum_{l > l~} #N_l."""
+    shapes = level_sizes(dims)
+    L = len(shapes) - 1
+    return 2 * 2 * es * sum(int(np_prod(shapes[L - l])) for l in range(stop + 1, L + 1))
+
+
+def path_flops(dims, stop):
+    """Algorithmic flops of decompose + recompose of a 3D grid (an FMA counts
+    2), per level l with fine sizes n and coarse sizes m: the multilinear
+    interpolant and the coefficient subtraction, 3 per coefficient node
+    (2 per interpolated value along one axis, 1 for the difference); the
+    load vector, 10 per output of a 5-tap restriction along each axis
+    (outputs n0 n1 m2, n0 m1 m2, m0 m1 m2); the tridiagonal solves, 4 per
+    coarse node per axis; the correction, 1 per coarse node.  Recomposition
+    has the same count."""
+    shapes = level_sizes(dims)
+    L = len(shapes) - 1
+    total = 0
+    for l in range(stop + 1, L + 1):
+        n, m = shapes[L - l], shapes[L - l + 1]
+        nf, nc = np_prod(n), np_prod(m)
+        total += (3 * (nf - nc) + 10 * (n[0] * n[1] * m[2] + n[0] * m[1] * m[2] + nc)
+                  + 12 * nc + nc)
+    return 2 * total
+
+
+def np_prod(v):
+    out = 1
+    for x in v:
+        out *= int(x)
+    return out
 
 
 def level_nodes(dims):

@@ -538,6 +538,16 @@ int mgard_trace_read(int max_rows, int* kind, int* level, int64_t* launches, dou
                      double* bytes, int* rows_out);
 const char* mgard_trace_kernel_name(int kind);
 
+/* Arithmetic roof of an element type on the current device (measurement
+ * support; no counterpart in the paper): times a kernel of independent
+ * dependent-FMA chains (8 per thread, 8 CTAs of 256 threads per SM) with
+ * CUDA events on `stream` and writes the best of three runs in flop/s (an
+ * FMA counts 2) to *flops_per_s.  The FP64 path of this library is bound by
+ * this rate rather than by HBM bandwidth on parts with few FP64 units.
+ * Allocates a small device buffer; synchronizes `stream`.  MGARD_ERR_ARG
+ * for a bad dtype or a NULL output, MGARD_ERR_CUDA on a CUDA error. */
+int mgard_trace_fma_rate(int dtype, double* flops_per_s, void* stream);
+
 /* Static description of an error code. */
 const char* mgard_error_string(int code);
 

@@ -122,6 +122,7 @@ _SIGNATURES = {
     "mgard_batch_autotune": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.POINTER(_VP), _VP,
                                             ctypes.c_size_t, _VP, ctypes.POINTER(ctypes.c_int)]),
     "mgard_batch_release": (ctypes.c_int, []),
+    "mgard_trace_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
     "mgard_batch_wait_selftest": (ctypes.c_int, [ctypes.c_int64, _VP]),
     "mgard_batch_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "mgard_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
@@ -537,6 +538,14 @@ def mgard_trace_select(kind=-1, level=None) -> int:
                                   1 if level is None else 0)
     _check(rc, "mgard_trace_select")
     return rc
+
+
+def mgard_trace_fma_rate(dtype: int, stream=None) -> float:
+    """Measured FMA throughput (flop/s) of the element type on this device."""
+    out = ctypes.c_double()
+    _check(lib().mgard_trace_fma_rate(dtype, ctypes.byref(out), _stream(stream)),
+           "mgard_trace_fma_rate")
+    return out.value
 
 
 def mgard_trace_kernel_launches() -> int:

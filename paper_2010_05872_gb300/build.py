@@ -63,11 +63,17 @@ def build(verbose: bool = False) -> str:
     srcs, headers = _sources()
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(lambda s: _compile(s, headers, verbose), srcs))
-    if _stale(LIB, objs):
+    # Relink when an object changed or the set of translation units did.
+    manifest = os.path.join(BUILD, "objects.txt")
+    listed = open(manifest).read() if os.path.exists(manifest) else ""
+    names = "\n".join(os.path.basename(o) for o in objs)
+    if _stale(LIB, objs) or listed != names:
         cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
+        with open(manifest, "w") as fh:
+            fh.write(names)
     return LIB
 
 

@@ -147,3 +147,72 @@ const char* mgard_trace_kernel_name(int kind) { return kernel_kind_name(kind); }
 int64_t mgard_trace_kernel_launches(void) { return g_kernels.load(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Arithmetic roof of the element type: the FMA rate of this device, measured
+// with independent dependent-FMA chains per thread (8 chains of `steps` FMAs,
+// 2 flops each) on a grid of 8 CTAs of 256 threads per SM.
+// ---------------------------------------------------------------------------
+namespace mgb {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_rate_kernel(T* out, int steps, T a, T b) {
+  constexpr int K = 8;
+  T x[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) x[k] = T(threadIdx.x + k) * T(1e-3);
+  for (int i = 0; i < steps; ++i) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) x[k] = fma(x[k], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+
+template <typename T>
+int fma_rate(double* flops_per_s, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MGARD_ERR_CUDA;
+  const int blocks = 8 * sms, threads = 256, steps = sizeof(T) == 8 ? 2048 : 16384;
+  T* out = nullptr;
+  if (cudaMalloc(&out, sizeof(T) * blocks * threads) != cudaSuccess) return MGARD_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MGARD_OK;
+  float best = 1e30f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = MGARD_ERR_CUDA;
+  } else {
+    for (int r = 0; r < 4 && rc == MGARD_OK; ++r) {  // the first run warms up
+      cudaEventRecord(e0, s);
+      fma_rate_kernel<T><<<blocks, threads, 0, s>>>(out, steps, T(0.999999), T(1e-7));
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = MGARD_ERR_CUDA;
+      else if (r > 0 && ms < best)
+        best = ms;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (rc == MGARD_OK)
+    *flops_per_s = 2.0 * 8.0 * double(steps) * double(blocks) * threads / (double(best) * 1e-3);
+  return rc;
+}
+
+}  // namespace
+}  // namespace mgb
+
+extern "C" int mgard_trace_fma_rate(int dtype, double* flops_per_s, void* stream) {
+  if (flops_per_s == nullptr || (dtype != MGARD_F32 && dtype != MGARD_F64)) return MGARD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dtype == MGARD_F64 ? mgb::fma_rate<double>(flops_per_s, s)
+                            : mgb::fma_rate<float>(flops_per_s, s);
+}
