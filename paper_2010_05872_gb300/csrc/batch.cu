@@ -79,7 +79,7 @@ struct BatchStage {
 };
 
 constexpr int kBatchThreads = 288;
-constexpr int kLvNS = 4, kLvT1 = MarchCfg<float>::T1;
+constexpr int kLvNS = 4, kLvT1 = 4;  // the batched tiles keep their own shape
 constexpr int kFinNS = 4, kFinT1 = FinishCfg<float>::T1;
 
 __global__ void __launch_bounds__(kBatchThreads, 2)
@@ -256,7 +256,7 @@ int field_stages(const DevPlan& p, float* data, char* ws, int dir, const Tuning&
   };
   auto lv_stage = [&](int l, bool dec) -> int {
     BatchStage s = base(dec ? kBLoadVecDec : kBLoadVecRec, l);
-    if (!plan_geometry(s.lv, s.mg, 1) || s.mg.threads > kBatchThreads) return MGARD_ERR_SHAPE;
+    if (!plan_geometry(s.lv, s.mg, 1, kLvT1, kLvNS) || s.mg.threads > kBatchThreads) return MGARD_ERR_SHAPE;
     const int c0 = s.lv.ax[0].nc;
     s.mg.t0 = std::max(1, std::min(tu.lv_t0, c0));
     s.mg.nb0 = (c0 + s.mg.t0 - 1) / s.mg.t0;

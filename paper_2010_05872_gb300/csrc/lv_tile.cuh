@@ -27,7 +27,9 @@ template <typename T>
 struct MarchCfg;
 template <>
 struct MarchCfg<float> {
-  static constexpr int NS = 3, T1 = 4;
+  // Measured at 513^3 on GB300 (NS, T1) in {2, 3, 4} x {2, 4, 6, 8}: two
+  // plane buffers of 2 T1 + 3 = 15 rows gave the shortest finest-level launch.
+  static constexpr int NS = 2, T1 = 6;
 };
 template <>
 struct MarchCfg<double> {
@@ -390,18 +392,20 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
 }
 
-// Tile shape of a level for CPT coarse columns per thread.
+// Tile shape of a level for CPT coarse columns per thread, T1 coarse rows per
+// tile and NS plane buffers (the per-level kernel's MarchCfg by default; the
+// batched kernel passes its own).
 template <typename T>
-inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g, int cpt = 2) {
-  using C = MarchCfg<T>;
+inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g, int cpt = 2, int t1 = MarchCfg<T>::T1,
+                          int ns = MarchCfg<T>::NS) {
   const int n1 = lv.ax[1].n, n2 = lv.ax[2].n, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   const int vec = 16 / static_cast<int>(sizeof(T));
   if (n1 > 1) {
     if (c2 > cpt * kLvMaxThreads) return false;  // rows too wide for one CTA
-    g.t1 = C::T1;
+    g.t1 = t1;
     g.tc2 = c2;
     g.pitch = n2;
-    g.BUF = ((4 * vec + (2 * C::T1 + 3) * n2 + 4 + vec - 1) / vec) * vec;
+    g.BUF = ((4 * vec + (2 * t1 + 3) * n2 + 4 + vec - 1) / vec) * vec;
   } else {
     g.t1 = 1;
     g.tc2 = c2 <= cpt * kLvMaxThreads ? c2 : cpt * kLvMaxThreads / 2;
@@ -411,7 +415,7 @@ inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g, int cpt = 2) {
   g.nb2 = (c2 + g.tc2 - 1) / g.tc2;
   g.nb1 = (c1 + g.t1 - 1) / g.t1;
   g.threads = 32 * (((g.tc2 + cpt - 1) / cpt + 31) / 32);
-  return g.threads <= kLvMaxThreads && sizeof(T) * static_cast<size_t>(C::NS) * g.BUF <= 200 * 1024;
+  return g.threads <= kLvMaxThreads && sizeof(T) * static_cast<size_t>(ns) * g.BUF <= 200 * 1024;
 }
 
 
