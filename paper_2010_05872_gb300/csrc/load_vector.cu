@@ -58,39 +58,45 @@ load_vector_march_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict
 
 }  // namespace
 
+// Whether a level's grid stays in L2 (it then takes the MarchCfg *_L2 shape
+// and short marches).
+template <typename T>
+bool l2_resident(const LevelK<T>& lv) {
+  const uint64_t count = uint64_t(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
+  return count * sizeof(T) <= kL2ResidentBytes;
+}
+
 template <typename T>
 bool load_vector_march_supported(const LevelK<T>& lv_in) {
   // 2D and 3D levels large enough to fill the GPU (1D and tiny levels use
   // the generic tiled kernel).
+  using C = MarchCfg<T>;
   const int64_t nf = int64_t(lv_in.ax[0].n) * lv_in.ax[1].n * lv_in.ax[2].n;
   if (lv_in.ax[0].n == 1 && lv_in.ax[1].n == 1) return false;
   if (nf < (int64_t(1) << 17)) return false;
   LevelK<T> lv = lv_in;
   if (lv.ax[0].n == 1) std::swap(lv.ax[0], lv.ax[1]);
   MarchGeom g{};
-  return plan_geometry(lv, g);
+  return l2_resident(lv) ? plan_geometry(lv, g, 2, C::T1_L2, C::NS_L2)
+                         : plan_geometry(lv, g, 2, C::T1, C::NS);
 }
 
-template <typename T>
-cudaError_t launch_load_vector_march(const LevelK<T>& lv_in, bool dec, const T* fine, T* coarse,
-                                     T* F, unsigned int* status, cudaStream_t s) {
-  using C = MarchCfg<T>;
-  // A 2D level (1, n1, n2) marches along its rows: view it as (n1, 1, n2).
-  LevelK<T> lv = lv_in;
-  if (lv.ax[0].n == 1) std::swap(lv.ax[0], lv.ax[1]);
+template <typename T, int NS, int T1C>
+cudaError_t launch_march_shape(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
+                               unsigned int* status, cudaStream_t s) {
   const int c0 = lv.ax[0].nc;
   MarchGeom g{};
-  if (!plan_geometry(lv, g)) return cudaErrorInvalidConfiguration;
+  if (!plan_geometry(lv, g, 2, T1C, NS)) return cudaErrorInvalidConfiguration;
   const bool three = lv.ax[1].n > 1;
-  const size_t smem = sizeof(T) * static_cast<size_t>(C::NS) * g.BUF;
+  const size_t smem = sizeof(T) * static_cast<size_t>(NS) * g.BUF;
   using KernelFn = void (*)(LevelK<T>, const T*, T*, T*, MarchGeom, uint64_t, unsigned int*);
   KernelFn kernel;
   if (three)
-    kernel = dec ? load_vector_march_kernel<T, true, C::NS, C::T1, true>
-                 : load_vector_march_kernel<T, false, C::NS, C::T1, true>;
+    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, true>
+                 : load_vector_march_kernel<T, false, NS, T1C, true>;
   else
-    kernel = dec ? load_vector_march_kernel<T, true, C::NS, C::T1, false>
-                 : load_vector_march_kernel<T, false, C::NS, C::T1, false>;
+    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, false>
+                 : load_vector_march_kernel<T, false, NS, T1C, false>;
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
@@ -100,12 +106,23 @@ cudaError_t launch_load_vector_march(const LevelK<T>& lv_in, bool dec, const T* 
   // that stays in L2, the shortest longest march (a CTA marches 2 t0 + 3
   // fine planes).
   const uint64_t count = uint64_t(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
-  g.t0 = march_chunk(c0, g.nb2 * g.nb1, 152 * per_sm, 8, 2,
-                     count * sizeof(T) <= kL2ResidentBytes);
+  g.t0 = march_chunk(c0, g.nb2 * g.nb1, 152 * per_sm, 8, 2, l2_resident(lv));
   g.nb0 = (c0 + g.t0 - 1) / g.t0;
   const unsigned grid = static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2);
   launch_pdl(kernel, dim3(grid), dim3(g.threads), smem, s, lv, fine, coarse, F, g, count, status);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_load_vector_march(const LevelK<T>& lv_in, bool dec, const T* fine, T* coarse,
+                                     T* F, unsigned int* status, cudaStream_t s) {
+  using C = MarchCfg<T>;
+  // A 2D level (1, n1, n2) marches along its rows: view it as (n1, 1, n2).
+  LevelK<T> lv = lv_in;
+  if (lv.ax[0].n == 1) std::swap(lv.ax[0], lv.ax[1]);
+  return l2_resident(lv)
+             ? launch_march_shape<T, C::NS_L2, C::T1_L2>(lv, dec, fine, coarse, F, status, s)
+             : launch_march_shape<T, C::NS, C::T1>(lv, dec, fine, coarse, F, status, s);
 }
 
 template bool load_vector_march_supported<float>(const LevelK<float>&);

@@ -27,13 +27,17 @@ template <typename T>
 struct MarchCfg;
 template <>
 struct MarchCfg<float> {
-  // Measured at 513^3 on GB300 (NS, T1) in {2, 3, 4} x {2, 4, 6, 8}: two
-  // plane buffers of 2 T1 + 3 = 15 rows gave the shortest finest-level launch.
+  // Levels larger than L2: measured at 513^3 on GB300, (NS, T1) in {2, 3, 4}
+  // x {2, 4, 6, 8}, two plane buffers of 2 T1 + 3 = 15 rows gave the shortest
+  // finest-level launch.  Levels that stay in L2 march a few planes per CTA,
+  // so their shape favours planes in flight (NS_L2, T1_L2).
   static constexpr int NS = 2, T1 = 6;
+  static constexpr int NS_L2 = 3, T1_L2 = 4;
 };
 template <>
 struct MarchCfg<double> {
   static constexpr int NS = 3, T1 = 4;
+  static constexpr int NS_L2 = 3, T1_L2 = 4;
 };
 
 // One tile (CTA work unit) of the marching load vector; `tile` plays the

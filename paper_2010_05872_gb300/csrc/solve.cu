@@ -91,12 +91,16 @@ solve_contig_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t n
 }
 
 // The per-level form keeps its own body (one 32-line group per CTA of
-// exactly nseg warps); solve_seg_tile is the same method for the persistent
-// batched kernel, with several groups side by side.
-template <typename T>
+// exactly nseg warps; short-lived CTAs let the scheduler overlap one group's
+// loads with another's arithmetic); solve_seg_tile is the same method for
+// the persistent batched kernel, with several groups side by side.  Here
+// warp 0 carries the boundary values across all segments (one pass per
+// recurrence) instead of every warp walking the segments before it, and
+// offsets are of type IDX (32-bit whenever the coarse grid allows).
+template <typename T, typename IDX>
 __global__ void __launch_bounds__(32 * kSegWarps, 2)
-solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlines, int64_t S,
-                 int64_t block_stride, int mode) {
+solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, IDX nlines, IDX S,
+                 IDX block_stride, int mode) {
   grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int nc = ax.nc, L = ax.seg_len;
@@ -106,7 +110,8 @@ solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlin
   T* s_sg = s_sb + nc;
   T* s_sy = s_sg + nc;
   T* s_sh = s_sy + nc;
-  T* s_c = s_sh + nc;  // nseg x 32 boundary values
+  T* s_c = s_sh + nc;            // nseg x 32 local boundary values
+  T* s_y = s_c + nseg * 32;      // nseg x 32 carried boundary values
   const int tid = threadIdx.x, lane = tid & 31, sgi = tid >> 5;
   for (int k = tid; k < nc; k += blockDim.x) {
     s_tm[k] = ax.tm[k];
@@ -115,20 +120,15 @@ solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlin
     s_sy[k] = ax.sy[k];
     s_sh[k] = ax.sh[k];
   }
-  const int64_t line = static_cast<int64_t>(blockIdx.x) * 32 + lane;
+  const IDX line = static_cast<IDX>(blockIdx.x) * 32 + lane;
   const bool valid = line < nlines;
-  const int64_t o = valid ? line / S : 0, in = valid ? line - o * S : 0;
-  const int64_t base = o * block_stride + in;
+  const IDX o = valid ? line / S : 0, in = valid ? line - o * S : 0;
   const int k0 = sgi * L, len = max(0, min(L, nc - k0));
+  const IDX base = o * block_stride + in + static_cast<IDX>(k0) * S;
   T v[kSegMax];
-  {
-    const T* p = F + base + static_cast<int64_t>(k0) * S;
 #pragma unroll
-    for (int j = 0; j < kSegMax; ++j) {
-      v[j] = (valid && j < len) ? *p : T(0);
-      p += S;
-    }
-  }
+  for (int j = 0; j < kSegMax; ++j)
+    v[j] = (valid && j < len) ? F[base + static_cast<IDX>(j) * S] : T(0);
   __syncthreads();
   // Forward from a zero boundary value.
   T y = T(0);
@@ -141,12 +141,20 @@ solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlin
   }
   s_c[sgi * 32 + lane] = y;
   __syncthreads();
-  T Y = T(0);  // final y at the end of the previous segment
-  for (int q = 0; q < sgi; ++q) Y = s_c[q * 32 + lane] + s_sg[min(q * L + L, nc) - 1] * Y;
+  if (sgi == 0) {  // the final y entering each segment
+    T Y = T(0);
+    for (int q = 0; q < nseg; ++q) {
+      s_y[q * 32 + lane] = Y;
+      Y = s_c[q * 32 + lane] + s_sg[min(q * L + L, nc) - 1] * Y;
+    }
+  }
+  __syncthreads();
+  {
+    const T Y = s_y[sgi * 32 + lane];
 #pragma unroll
-  for (int j = 0; j < kSegMax; ++j)
-    if (j < len) v[j] += s_sg[k0 + j] * Y;
-  __syncthreads();  // every read of the forward boundary values is done
+    for (int j = 0; j < kSegMax; ++j)
+      if (j < len) v[j] += s_sg[k0 + j] * Y;
+  }
   // Backward from a zero boundary value.
   T x = T(0);
 #pragma unroll
@@ -158,42 +166,46 @@ solve_seg_kernel(AxisK<T> ax, T* __restrict__ F, T* __restrict__ B, int64_t nlin
   }
   s_c[sgi * 32 + lane] = x;
   __syncthreads();
-  T X = T(0);  // final x at the start of the next segment
-  for (int q = nseg - 1; q > sgi; --q) X = s_c[q * 32 + lane] + s_sh[q * L] * X;
+  if (sgi == 0) {  // the final x entering each segment from above
+    T X = T(0);
+    for (int q = nseg - 1; q >= 0; --q) {
+      s_y[q * 32 + lane] = X;
+      X = s_c[q * 32 + lane] + s_sh[q * L] * X;
+    }
+  }
+  __syncthreads();
   if (!valid) return;
+  {
+    const T X = s_y[sgi * 32 + lane];
 #pragma unroll
-  for (int j = 0; j < kSegMax; ++j)
-    if (j < len) v[j] += s_sh[k0 + j] * X;
-  T* pf = F + base + static_cast<int64_t>(k0) * S;
+    for (int j = 0; j < kSegMax; ++j)
+      if (j < len) v[j] += s_sh[k0 + j] * X;
+  }
   if (mode == kApplyNone) {
 #pragma unroll
-    for (int j = 0; j < kSegMax; ++j) {
-      if (j < len) *pf = v[j];
-      pf += S;
-    }
+    for (int j = 0; j < kSegMax; ++j)
+      if (j < len) F[base + static_cast<IDX>(j) * S] = v[j];
     return;
   }
   // Apply in groups of 8 (B loads in flight together).
-  T* pb = B + base + static_cast<int64_t>(k0) * S;
 #pragma unroll
   for (int j0 = 0; j0 < kSegMax; j0 += 8) {
     T bv[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) bv[u] = (j0 + u < len) ? pb[static_cast<int64_t>(u) * S] : T(0);
+    for (int u = 0; u < 8; ++u)
+      bv[u] = (j0 + u < len) ? B[base + static_cast<IDX>(j0 + u) * S] : T(0);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       if (j0 + u < len) {
-        const int64_t off = static_cast<int64_t>(u) * S;
+        const IDX off = base + static_cast<IDX>(j0 + u) * S;
         if (mode == kApplyDecompose) {
-          pb[off] = bv[u] + v[j0 + u];
-          pf[off] = bv[u];
+          B[off] = bv[u] + v[j0 + u];
+          F[off] = bv[u];
         } else {
-          pb[off] = bv[u] - v[j0 + u];
+          B[off] = bv[u] - v[j0 + u];
         }
       }
     }
-    pb += 8 * S;
-    pf += 8 * S;
   }
 }
 
@@ -346,9 +358,14 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
       const int nseg = (nc + lv.ax[a].seg_len - 1) / lv.ax[a].seg_len;
       const int64_t S = (a == 0) ? c1 * c2 : c2;
       const int64_t nlines = (a == 0) ? S : c0 * S;
-      const size_t smem = sizeof(T) * (5 * static_cast<size_t>(nc) + 32 * static_cast<size_t>(nseg));
-      launch_pdl(solve_seg_kernel<T>, dim3(ceil_div(nlines, 32)), dim3(32 * nseg), smem, s,
-                 lv.ax[a], F, B, nlines, S, nc * S, m);
+      const size_t smem = sizeof(T) * (5 * static_cast<size_t>(nc) + 64 * static_cast<size_t>(nseg));
+      if (c0 * c1 * c2 < (int64_t(1) << 31))
+        launch_pdl(solve_seg_kernel<T, int32_t>, dim3(ceil_div(nlines, 32)), dim3(32 * nseg), smem, s,
+                   lv.ax[a], F, B, static_cast<int32_t>(nlines), static_cast<int32_t>(S),
+                   static_cast<int32_t>(nc * S), m);
+      else
+        launch_pdl(solve_seg_kernel<T, int64_t>, dim3(ceil_div(nlines, 32)), dim3(32 * nseg), smem, s,
+                   lv.ax[a], F, B, nlines, S, nc * S, m);
     } else {
       // Strided lines; contiguous lines too long for shared memory go here
       // too, as lines of stride 1.
