@@ -27,7 +27,7 @@
 namespace mgb {
 namespace {
 
-constexpr int kSmallThreads = 1024;
+constexpr int kSmallThreads = 512;
 
 template <typename T>
 struct SmallLevels {
@@ -38,86 +38,114 @@ __device__ __forceinline__ int grid_size(const int n[3]) { return n[0] * n[1] * 
 
 // F = R v - X v_c on the coarse grid of one transition; v is the fine grid,
 // v_c its values on the coarse nodes (read from the nodal positions of v).
+// Tap positions are clamped into the grid under zero weights, so every load
+// of a node is unconditional and a thread's loads pipeline.
 template <typename T>
 __device__ void load_vector_small(const LevelK<T>& L, bool dec, const T* v, T* F) {
-  const int n0 = L.ax[0].n, n1 = L.ax[1].n, n2 = L.ax[2].n;
-  const int c0 = L.ax[0].nc, c1 = L.ax[1].nc, c2 = L.ax[2].nc;
-  const T* X0 = dec ? L.ax[0].xd : L.ax[0].xr;
-  const T* X1 = dec ? L.ax[1].xd : L.ax[1].xr;
-  const T* X2 = dec ? L.ax[2].xd : L.ax[2].xr;
-  const int nco = c0 * c1 * c2;
+  const int n1 = L.ax[1].n, n2 = L.ax[2].n;
+  const int c1 = L.ax[1].nc, c2 = L.ax[2].nc;
+  const int nco = L.ax[0].nc * c1 * c2;
   for (int idx = threadIdx.x; idx < nco; idx += blockDim.x) {
-    const int k2 = idx % c2, k1 = (idx / c2) % c1, k0 = idx / (c1 * c2);
-    const int p0 = cpos(k0, n0), p1 = cpos(k1, n1), p2 = cpos(k2, n2);
-    T r0[5], r1[5], r2[5];
+    const int k2 = idx % c2, k01 = idx / c2, k1 = k01 % c1, k0 = k01 / c1;
+    const int kk[3] = {k0, k1, k2};
+    int j[3][5], q[3][3];
+    T w[3][5], x[3][3];
 #pragma unroll
-    for (int o = 0; o < 5; ++o) {
-      r0[o] = __ldg(L.ax[0].rw + 5 * k0 + o);
-      r1[o] = __ldg(L.ax[1].rw + 5 * k1 + o);
-      r2[o] = __ldg(L.ax[2].rw + 5 * k2 + o);
+    for (int a = 0; a < 3; ++a) {
+      const AxisK<T>& ax = L.ax[a];
+      const int n = ax.n, nc = ax.nc, k = kk[a], p = cpos(k, n);
+      const T* X = dec ? ax.xd : ax.xr;
+#pragma unroll
+      for (int o = 0; o < 5; ++o) {
+        const int jj = p + o - 2;
+        const bool in = jj >= 0 && jj < n;
+        j[a][o] = in ? jj : p;
+        w[a][o] = in ? __ldg(ax.rw + 5 * k + o) : T(0);
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int qq = k - 1 + d;
+        const bool in = qq >= 0 && qq < nc;
+        q[a][d] = cpos(in ? qq : k, n);
+        x[a][d] = in ? __ldg(X + 3 * k + d) : T(0);
+      }
     }
     T acc = T(0);
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-      const int j0 = p0 + a - 2;
-      if (j0 < 0 || j0 >= n0) continue;
+      T s1 = T(0);
 #pragma unroll
       for (int b = 0; b < 5; ++b) {
-        const int j1 = p1 + b - 2;
-        if (j1 < 0 || j1 >= n1) continue;
-        const T* row = v + (j0 * n1 + j1) * n2;
-        T s = T(0);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          const int j2 = p2 + c - 2;
-          if (j2 >= 0 && j2 < n2) s += r2[c] * row[j2];
-        }
-        acc += r0[a] * r1[b] * s;
+        const T* row = v + (j[0][a] * n1 + j[1][b]) * n2;
+        s1 += w[1][b] * ((w[2][0] * row[j[2][0]] + w[2][1] * row[j[2][1]]) +
+                         (w[2][2] * row[j[2][2]] + (w[2][3] * row[j[2][3]] + w[2][4] * row[j[2][4]])));
       }
+      acc += w[0][a] * s1;
     }
     T xs = T(0);
-    for (int d0 = 0; d0 < 3; ++d0) {
-      const int q0 = k0 - 1 + d0;
-      if (q0 < 0 || q0 >= c0) continue;
-      const T w0 = __ldg(X0 + 3 * k0 + d0);
-      for (int d1 = 0; d1 < 3; ++d1) {
-        const int q1 = k1 - 1 + d1;
-        if (q1 < 0 || q1 >= c1) continue;
-        const T w01 = w0 * __ldg(X1 + 3 * k1 + d1);
-        const T* row = v + (cpos(q0, n0) * n1 + cpos(q1, n1)) * n2;
-        for (int d2 = 0; d2 < 3; ++d2) {
-          const int q2 = k2 - 1 + d2;
-          if (q2 >= 0 && q2 < c2) xs += w01 * __ldg(X2 + 3 * k2 + d2) * row[cpos(q2, n2)];
-        }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T s1 = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T* row = v + (q[0][a] * n1 + q[1][b]) * n2;
+        s1 += x[1][b] * (x[2][0] * row[q[2][0]] + x[2][1] * row[q[2][1]] + x[2][2] * row[q[2][2]]);
       }
+      xs += x[0][a] * s1;
     }
     F[idx] = acc - xs;
   }
 }
 
 // Thomas solves of M_c along every axis of the coarse grid F (one thread
-// per line).
+// per line); values and factors are read eight rows ahead of each
+// recurrence, so the chain waits on arithmetic rather than on loads.
 template <typename T>
 __device__ void solves_small(const LevelK<T>& L, T* F) {
   const int c[3] = {L.ax[0].nc, L.ax[1].nc, L.ax[2].nc};
   for (int a = 2; a >= 0; --a) {
     const AxisK<T>& ax = L.ax[a];
     const int nc = c[a];
-    const int stride = a == 2 ? 1 : a == 1 ? c[2] : c[1] * c[2];
-    const int lines = (c[0] * c[1] * c[2]) / nc;
-    for (int line = threadIdx.x; line < lines; line += blockDim.x) {
-      // Line index -> (outer, inner) around the solved axis.
-      const int inner = line % stride, outer = line / stride;
-      T* l = F + outer * nc * stride + inner;
-      T y = T(0);
-      for (int k = 0; k < nc; ++k) {
-        y = (l[k * stride] - __ldg(ax.ta + k) * y) * __ldg(ax.tm + k);
-        l[k * stride] = y;
-      }
-      T x = T(0);
-      for (int k = nc - 1; k >= 0; --k) {
-        x = l[k * stride] - __ldg(ax.tc + k) * x;
-        l[k * stride] = x;
+    if (L.ax[a].n > 1) {
+      const int stride = a == 2 ? 1 : a == 1 ? c[2] : c[1] * c[2];
+      const int lines = (c[0] * c[1] * c[2]) / nc;
+      for (int line = threadIdx.x; line < lines; line += blockDim.x) {
+        // Line index -> (outer, inner) around the solved axis.
+        const int inner = line % stride, outer = line / stride;
+        T* l = F + outer * nc * stride + inner;
+        T y = T(0);
+        for (int k0 = 0; k0 < nc; k0 += 8) {
+          T f[8], ta[8], tm[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int k = min(k0 + u, nc - 1);
+            f[u] = l[k * stride];
+            ta[u] = __ldg(ax.ta + k);
+            tm[u] = __ldg(ax.tm + k);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (k0 + u < nc) {
+              y = (f[u] - ta[u] * y) * tm[u];
+              l[(k0 + u) * stride] = y;
+            }
+        }
+        T x = T(0);
+        for (int k0 = nc - 1; k0 >= 0; k0 -= 8) {
+          T yv[8], tc[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int k = max(k0 - u, 0);
+            yv[u] = l[k * stride];
+            tc[u] = __ldg(ax.tc + k);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (k0 - u >= 0) {
+              x = yv[u] - tc[u] * x;
+              l[(k0 - u) * stride] = x;
+            }
+        }
       }
     }
     __syncthreads();
@@ -126,40 +154,40 @@ __device__ void solves_small(const LevelK<T>& L, T* F) {
 
 // Multilinear interpolation at fine node (j0, j1, j2) from coarse values
 // `cv` (coarse grid layout, or, with from_fine, the nodal positions of the
-// fine grid `cv`).
+// fine grid `cv`): always the 8 corners (a nodal axis repeats its node under
+// weights 1 and 0, which passes the value unrounded), all loads issued
+// before the arithmetic.
 template <typename T>
 __device__ __forceinline__ T interp_small(const LevelK<T>& L, const T* cv, bool from_fine, int j0,
                                           int j1, int j2) {
-  const int n[3] = {L.ax[0].n, L.ax[1].n, L.ax[2].n};
-  const int c[3] = {L.ax[0].nc, L.ax[1].nc, L.ax[2].nc};
   const int j[3] = {j0, j1, j2};
   int kl[3], kr[3];
   T wl[3], wr[3];
+  bool q[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (is_coef(j[a], n[a])) {
-      kl[a] = (j[a] - 1) >> 1;
-      kr[a] = kl[a] + 1;
-      wl[a] = __ldg(L.ax[a].iwl + j[a]);
-      wr[a] = __ldg(L.ax[a].iwr + j[a]);
-    } else {
-      kl[a] = kr[a] = nodal_k(j[a], n[a], c[a]);
-      wl[a] = T(1);
-      wr[a] = T(0);
+    const AxisK<T>& ax = L.ax[a];
+    q[a] = is_coef(j[a], ax.n);
+    kl[a] = q[a] ? (j[a] >> 1) : nodal_k(j[a], ax.n, ax.nc);
+    kr[a] = q[a] ? kl[a] + 1 : kl[a];
+    wl[a] = q[a] ? __ldg(ax.iwl + j[a]) : T(1);
+    wr[a] = q[a] ? __ldg(ax.iwr + j[a]) : T(0);
+    if (from_fine) {
+      kl[a] = cpos(kl[a], ax.n);
+      kr[a] = cpos(kr[a], ax.n);
     }
   }
-  auto at = [&](int a0, int a1, int a2) -> T {
-    if (from_fine) return cv[(cpos(a0, n[0]) * n[1] + cpos(a1, n[1])) * n[2] + cpos(a2, n[2])];
-    return cv[(a0 * c[1] + a1) * c[2] + a2];
-  };
-  T s = T(0);
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const T w = ((m & 4) ? wr[0] : wl[0]) * ((m & 2) ? wr[1] : wl[1]) * ((m & 1) ? wr[2] : wl[2]);
-    if (w != T(0))
-      s += w * at((m & 4) ? kr[0] : kl[0], (m & 2) ? kr[1] : kl[1], (m & 1) ? kr[2] : kl[2]);
-  }
-  return s;
+  const int m1 = from_fine ? L.ax[1].n : L.ax[1].nc, m2 = from_fine ? L.ax[2].n : L.ax[2].nc;
+  auto at = [&](int a0, int a1, int a2) { return cv[(a0 * m1 + a1) * m2 + a2]; };
+  const T v000 = at(kl[0], kl[1], kl[2]), v001 = at(kl[0], kl[1], kr[2]);
+  const T v010 = at(kl[0], kr[1], kl[2]), v011 = at(kl[0], kr[1], kr[2]);
+  const T v100 = at(kr[0], kl[1], kl[2]), v101 = at(kr[0], kl[1], kr[2]);
+  const T v110 = at(kr[0], kr[1], kl[2]), v111 = at(kr[0], kr[1], kr[2]);
+  auto r2 = [&](T a, T b) { return q[2] ? wl[2] * a + wr[2] * b : a; };
+  auto r1 = [&](T a, T b) { return q[1] ? wl[1] * a + wr[1] * b : a; };
+  const T a0 = r1(r2(v000, v001), r2(v010, v011));
+  const T a1 = r1(r2(v100, v101), r2(v110, v111));
+  return q[0] ? wl[0] * a0 + wr[0] * a1 : a0;
 }
 
 template <typename T, bool DEC>
