@@ -1073,6 +1073,19 @@ def lpt_assign(weights, world):
     return [sorted(p) for p in parts]
 
 
+def serving_assign(sizes, world):
+    """Online partition of a request stream over `world` ranks: each request,
+    in arrival order, goes to the rank with the fewest bytes assigned so far
+    (the lowest rank on a tie).  Every rank computes the same assignment."""
+    load = [0] * world
+    out = []
+    for b in sizes:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out.append(r)
+        load[r] += int(b)
+    return out
+
+
 def run_batched(args, rank, world, local_rank):
     """Batched workload: 256 FP32 fields, each axis from U{33..257}, k^-5/3
     fields; decompose + recompose of all fields per step, in one persistent
@@ -1213,19 +1226,23 @@ def run_batched(args, rank, world, local_rank):
         }))
 
 
-def run_serving(args):
+def run_serving(args, rank=0, world=1, local_rank=0):
     """Serving workload: a seeded Poisson stream (mean 200 requests/s) of
     compress / decompress requests on FP32 k^-5/3 fields, 2D sides from
     {1024, 1025, 2048, 2049, 4096} or 3D sides from {129, 257, 513}, bounds
     from {1e-2, 1e-3, 1e-4} x range, admitted against a 120 GB HBM budget by
-    the library's serving loop; p50 / p99 latency and aggregate GB/s."""
+    the library's serving loop; p50 / p99 latency and aggregate GB/s.  With
+    N > 1 ranks the stream is partitioned over the ranks by bytes
+    (`serving_assign`), each rank serving its share on its own GPU; rank 0
+    merges the latencies and reports all ranks' bytes over the slowest
+    rank's wall time (no collective on the data path)."""
     import numpy as np
     import torch
     from paper_2010_05872_gb300 import binding as B
     from paper_2010_05872_gb300 import build as build_mod
     from paper_2010_05872_gb300 import fields as F
     build_mod.build()
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(local_rank)
     rng = np.random.default_rng(F.SEED_SERVING)
     shapes = [(s, s) for s in (1024, 1025, 2048, 2049, 4096)] + [(s, s, s) for s in (129, 257, 513)]
     nreq = args.serving_requests
@@ -1235,6 +1252,9 @@ def run_serving(args):
     is3d = rng.random(nreq) < 0.5
     pick = np.where(is3d, 5 + rng.integers(0, 3, nreq), rng.integers(0, 5, nreq))
     rels = rng.choice([1e-2, 1e-3, 1e-4], size=nreq)
+    sizes = [4 * int(np.prod(shapes[int(i)])) for i in pick]
+    assign = serving_assign(sizes, world)
+    mine = [k for k in range(nreq) if assign[k] == rank]
     # One field per shape (pinned), compressed once beforehand: the inputs of
     # the decompress requests.  Output buffers are recycled per shape.
     fields, packed, pools = [], [], []
@@ -1253,14 +1273,17 @@ def run_serving(args):
     inflight = {}
     lat = {"compress": [], "decompress": []}
     nbytes = 0
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
-    k = 0
+    m = 0
     done_n = 0
     first_arrival = None
-    last_done = None
-    while done_n < nreq:
+    last_done = arrive[0]
+    while done_n < len(mine):
         now = time.perf_counter() - t0
-        while k < nreq and arrive[k] <= now and free[pick[k]]:
+        while m < len(mine) and arrive[mine[m]] <= now and free[pick[mine[m]]]:
+            k = mine[m]
             i = int(pick[k])
             slot = free[i].pop()
             buf = pools[i][slot]
@@ -1272,7 +1295,7 @@ def run_serving(args):
             inflight[rid] = (i, slot, "compress" if kinds[k] else "decompress", arrive[k])
             if first_arrival is None:
                 first_arrival = now
-            k += 1
+            m += 1
         for rid, st, l, _ in srv.poll():
             i, slot, kind, a = inflight.pop(rid)
             assert st == 0, st
@@ -1286,9 +1309,9 @@ def run_serving(args):
         time.sleep(0.0002)
     wall = last_done - arrive[0]
     counters = srv.counters()
-    # Mix vs alone: the first 16 request kinds again, one at a time.
+    # Mix vs alone: this rank's first 16 request kinds again, one at a time.
     same = True
-    for j in range(16):
+    for j in mine[:16]:
         i = int(pick[j])
         if kinds[j]:
             a = torch.empty(fields[i].numel(), dtype=torch.int64).pin_memory()
@@ -1303,6 +1326,17 @@ def run_serving(args):
             srv2.close()
             same = same and torch.equal(a, b)
     srv.close()
+    if world > 1:
+        parts = [None] * world
+        torch.distributed.all_gather_object(parts, (lat, nbytes, wall, counters, same))
+        if rank != 0:
+            return
+        lat = {kk: [v for p in parts for v in p[0][kk]] for kk in lat}
+        nbytes = sum(p[1] for p in parts)
+        wall = max(p[2] for p in parts)
+        counters = {"peak_running": max(p[3]["peak_running"] for p in parts),
+                    "peak_bytes": max(p[3]["peak_bytes"] for p in parts)}
+        same = all(p[4] for p in parts)
     allat = sorted(lat["compress"] + lat["decompress"])
 
     def pct(v, q):
@@ -1311,13 +1345,14 @@ def run_serving(args):
 
     print(json.dumps({
         "metric": "serving aggregate GB/s (field bytes) with p50/p99 latency",
-        "value": nbytes / wall / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": nreq, "warmup": len(shapes),
+        "value": nbytes / wall / 1e9, "unit": "GB/s", "n_gpus": world, "steps": nreq, "warmup": len(shapes),
         "ms_per_step": 1e3 * wall / nreq, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "Poisson 200 req/s, %d requests, 50%% compress / 50%% decompress, "
                                "2D sides {1024,1025,2048,2049,4096} or 3D sides {129,257,513}, "
                                "k^-5/3 FP32 fields, bounds {1e-2,1e-3,1e-4} x range" % nreq,
-                   "hbm_budget_gb": 120, "slots": 8},
+                   "hbm_budget_gb": 120, "slots": 8,
+                   "parallelism": "requests partitioned over ranks by bytes (serving_assign)"},
         "latency_ms": {"p50": pct(allat, 0.5), "p99": pct(allat, 0.99),
                        "compress_p50": pct(lat["compress"], 0.5), "compress_p99": pct(lat["compress"], 0.99),
                        "decompress_p50": pct(lat["decompress"], 0.5),
@@ -1342,7 +1377,16 @@ def main():
         run_reference(args, rank)
         return
     if args.workload == "serving":
-        run_serving(args)
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        try:
+            run_serving(args, rank, world, local_rank)
+        finally:
+            if world > 1:
+                import torch
+                torch.distributed.destroy_process_group()
         return
     if args.workload == "batched":
         if world > 1:

@@ -1,7 +1,9 @@
 """Multi-rank host logic on CPU (gloo, world size 2): the sharding of
 batched fields over ranks (longest first, every field on exactly one rank,
-balanced loads) and the timing reduction the benchmark applies (barrier,
-maximum over ranks), run as two processes with a 127.0.0.1 rendezvous."""
+balanced loads), the partition of the serving request stream over ranks
+(every request on exactly one rank, bytes balanced), and the timing
+reduction the benchmark applies (barrier, maximum over ranks), run as two
+processes with a 127.0.0.1 rendezvous."""
 import os
 import socket
 
@@ -58,3 +60,39 @@ def test_batched_sharding_and_max_timing_world2():
     assert flat == list(range(n))                      # each field exactly once
     assert tmax == 11.0                                # the maximum over ranks
     assert max(loads) <= 1.05 * min(loads)             # longest-first balance
+
+
+def _serving_worker(rank, world, port, out):
+    import numpy as np
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    rng = np.random.default_rng(F.SEED_SERVING)
+    sizes = [int(v) for v in rng.choice([4 << 20, 16 << 20, 64 << 20, 540 << 20], size=500)]
+    assign = bench.serving_assign(sizes, world)
+    mine = [k for k, r in enumerate(assign) if r == rank]
+    got = [None] * world
+    dist.all_gather_object(got, (mine, assign))
+    if rank == 0:
+        out.put((got, sizes))
+    dist.destroy_process_group()
+
+
+def test_serving_partition_world2():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_serving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got, sizes = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    (mine0, a0), (mine1, a1) = got
+    assert a0 == a1                                    # the same partition on every rank
+    assert sorted(mine0 + mine1) == list(range(len(sizes)))
+    assert not set(mine0) & set(mine1)
+    b0, b1 = sum(sizes[k] for k in mine0), sum(sizes[k] for k in mine1)
+    # Online greedy: the loads differ by at most the largest request.
+    assert abs(b0 - b1) <= max(sizes)
