@@ -235,7 +235,7 @@ int small_top(const DevPlan& p, int stop) {
   for (int l = stop + 1; l <= p.h.L && l - stop <= kSmallMaxLevels; ++l) {
     const auto& d = p.h.shape[l];
     if (d[0] * d[1] * d[2] > kSmallMaxNodes) break;
-    if (small_levels_smem<T>(&lv[stop + 1], l - stop) > 200 * 1024) break;
+    if (small_levels_smem<T>(&lv[stop + 1], l - stop) > kSmallMaxSmem) break;
     ls = l;
   }
   return ls;

@@ -81,7 +81,8 @@ cudaError_t launch_finish(const LevelK<T>& lv, const T* nodal_src, const T* inte
 // (small.cu): `data` is the level-(stop + nlev) grid, decomposed (dec) or
 // recomposed in place; lv[i] is the transition of level stop + 1 + i.
 constexpr int kSmallMaxLevels = 10;
-constexpr int64_t kSmallMaxNodes = 8192;  // nodes of the highest small level
+constexpr int64_t kSmallMaxNodes = 40000;  // nodes of the highest small level
+constexpr size_t kSmallMaxSmem = 220 * 1024;  // its shared memory (every level and table)
 template <typename T>
 size_t small_levels_smem(const LevelK<T>* lv, int nlev);
 template <typename T>

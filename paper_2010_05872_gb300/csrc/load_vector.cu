@@ -45,14 +45,14 @@
 namespace mgb {
 namespace {
 
-template <typename T, bool DEC, int NS, int T1C, bool THREE>
+template <typename T, bool DEC, int NS, int T1C, bool THREE, int CPT>
 __global__ void __launch_bounds__(kLvMaxThreads)
 load_vector_march_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict__ coarse,
                          T* __restrict__ F, MarchGeom g, uint64_t fine_count,
                          unsigned int* __restrict__ status) {
   grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  load_vector_march_tile<T, DEC, NS, T1C, THREE>(lv, fine, coarse, F, g, fine_count, status,
+  load_vector_march_tile<T, DEC, NS, T1C, THREE, false, CPT>(lv, fine, coarse, F, g, fine_count, status,
                                                  blockIdx.x, smem_raw);
 }
 
@@ -77,26 +77,26 @@ bool load_vector_march_supported(const LevelK<T>& lv_in) {
   LevelK<T> lv = lv_in;
   if (lv.ax[0].n == 1) std::swap(lv.ax[0], lv.ax[1]);
   MarchGeom g{};
-  return l2_resident(lv) ? plan_geometry(lv, g, 2, C::T1_L2, C::NS_L2)
-                         : plan_geometry(lv, g, 2, C::T1, C::NS);
+  return l2_resident(lv) ? plan_geometry(lv, g, C::CPT_L2, C::T1_L2, C::NS_L2)
+                         : plan_geometry(lv, g, C::CPT, C::T1, C::NS);
 }
 
-template <typename T, int NS, int T1C>
+template <typename T, int NS, int T1C, int CPT>
 cudaError_t launch_march_shape(const LevelK<T>& lv, bool dec, const T* fine, T* coarse, T* F,
                                unsigned int* status, cudaStream_t s) {
   const int c0 = lv.ax[0].nc;
   MarchGeom g{};
-  if (!plan_geometry(lv, g, 2, T1C, NS)) return cudaErrorInvalidConfiguration;
+  if (!plan_geometry(lv, g, CPT, T1C, NS)) return cudaErrorInvalidConfiguration;
   const bool three = lv.ax[1].n > 1;
   const size_t smem = sizeof(T) * static_cast<size_t>(NS) * g.BUF;
   using KernelFn = void (*)(LevelK<T>, const T*, T*, T*, MarchGeom, uint64_t, unsigned int*);
   KernelFn kernel;
   if (three)
-    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, true>
-                 : load_vector_march_kernel<T, false, NS, T1C, true>;
+    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, true, CPT>
+                 : load_vector_march_kernel<T, false, NS, T1C, true, CPT>;
   else
-    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, false>
-                 : load_vector_march_kernel<T, false, NS, T1C, false>;
+    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, false, CPT>
+                 : load_vector_march_kernel<T, false, NS, T1C, false, CPT>;
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
@@ -121,8 +121,8 @@ cudaError_t launch_load_vector_march(const LevelK<T>& lv_in, bool dec, const T* 
   LevelK<T> lv = lv_in;
   if (lv.ax[0].n == 1) std::swap(lv.ax[0], lv.ax[1]);
   return l2_resident(lv)
-             ? launch_march_shape<T, C::NS_L2, C::T1_L2>(lv, dec, fine, coarse, F, status, s)
-             : launch_march_shape<T, C::NS, C::T1>(lv, dec, fine, coarse, F, status, s);
+             ? launch_march_shape<T, C::NS_L2, C::T1_L2, C::CPT_L2>(lv, dec, fine, coarse, F, status, s)
+             : launch_march_shape<T, C::NS, C::T1, C::CPT>(lv, dec, fine, coarse, F, status, s);
 }
 
 template bool load_vector_march_supported<float>(const LevelK<float>&);

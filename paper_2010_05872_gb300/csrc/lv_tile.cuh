@@ -30,14 +30,16 @@ struct MarchCfg<float> {
   // Levels larger than L2: measured at 513^3 on GB300, (NS, T1) in {2, 3, 4}
   // x {2, 4, 6, 8}, two plane buffers of 2 T1 + 3 = 15 rows gave the shortest
   // finest-level launch.  Levels that stay in L2 march a few planes per CTA,
-  // so their shape favours planes in flight (NS_L2, T1_L2).
-  static constexpr int NS = 2, T1 = 6;
-  static constexpr int NS_L2 = 3, T1_L2 = 4;
+  // so their shape favours planes in flight (NS_L2, T1_L2).  Two coarse
+  // columns per thread (CPT) beat one at 257^3 as well (41 against 43-64 us
+  // over six shapes).
+  static constexpr int NS = 2, T1 = 6, CPT = 2;
+  static constexpr int NS_L2 = 3, T1_L2 = 4, CPT_L2 = 2;
 };
 template <>
 struct MarchCfg<double> {
-  static constexpr int NS = 3, T1 = 4;
-  static constexpr int NS_L2 = 3, T1_L2 = 4;
+  static constexpr int NS = 3, T1 = 4, CPT = 2;
+  static constexpr int NS_L2 = 3, T1_L2 = 4, CPT_L2 = 2;
 };
 
 // One tile (CTA work unit) of the marching load vector; `tile` plays the

@@ -1,118 +1,267 @@
 // The coarsest levels of a transform in one CTA.  Below a few tens of
 // thousands of nodes every per-level kernel is a handful of CTAs whose cost
-// is launch and latency; here one CTA of 1024 threads loads the grid of the
-// highest small level into shared memory, runs the whole decomposition (or
-// recomposition) of the levels below it there, and writes the grid back.
+// is launch and latency; here one CTA (1024 threads) loads the grid of the
+// highest small level and every level's tables into shared memory, runs the
+// whole decomposition (or recomposition) of the levels below it there, and
+// writes the grid back.
 //
 // Per level transition (tables of the level, Section 2):
-//   decomposition : F = R v - (R P) v_c (the load vector, by a direct 5-tap
-//                   tensor stencil per coarse node), Thomas solves along each
-//                   axis, coarse values v_c + z, coefficients v - Pi(v_c);
-//                   after the coarsest level the final coarse values go back
-//                   into the nodal positions, coarsest first;
+//   decomposition : F = R v - (R P) v_c, Thomas solves along each axis,
+//                   coarse values v_c + z, coefficients v - Pi(v_c); after
+//                   the coarsest level the final coarse values go back into
+//                   the nodal positions, coarsest first;
 //   recomposition : the coarse grids are gathered from the nodal positions
 //                   first; then, coarsest first, F = R w - (R S) w_c, the
 //                   solves, c' = Q u - z, and the grid becomes Pi(c') plus the
 //                   coefficients.
 // These are the same operators as the per-level kernels; only the order of
-// the rounding differs.
+// the rounding differs.  Every phase is latency-bound on one SM, so each is
+// laid out to keep many independent loads in flight with little integer
+// work per node:
+//   * the load vector is separable: a walk along axis 1 per (fine plane,
+//     coarse column) applies the axis-2 and axis-1 rows of R with a
+//     five-row window (scratch S = R1 R2 v on every fine plane), then a walk
+//     along axis 0 per coarse (row, column) applies R0 to S and subtracts
+//     X0 of the axis-1/2 products of X on the nodal planes, writing F in
+//     place of S one plane late (a plane of S is no longer read once the
+//     walk has passed it);
+//   * the coefficient / interpolation pass takes a fine row and one nodal
+//     column with the coefficient column to its right, so the axis-0/1
+//     interpolant of the two nodal columns is formed once for both nodes;
+//   * indices come from multiply-high divisions by per-level constants.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "pdl.cuh"
 #include "grid.cuh"
 #include "kernels.cuh"
+#include "tma.cuh"
 #include "trace.hpp"
 
 namespace mgb {
 namespace {
 
-constexpr int kSmallThreads = 512;
-
+// FP32 grids reach 33^3 nodes and take 1024 threads; FP64 ones stay at 17^3
+// (shared-memory capacity), where 512 threads with more registers each do.
 template <typename T>
-struct SmallLevels {
-  LevelK<T> lv[kSmallMaxLevels];  // lv[i]: transition of level stop + 1 + i
+constexpr int small_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+constexpr int kTabArrays = 7;  // iwl, iwr, rw, X, ta, tm, tc
+constexpr int kSmallSegs = kSmallMaxLevels * 3 * kTabArrays;
+
+// Division by a divisor fixed for the launch: q = umulhi(x, m) with
+// m = ceil(2^32 / d), exact while x * d < 2^32 (m = 0 stands for d = 1).
+struct FastDiv {
+  unsigned d, m;
+};
+FastDiv make_fastdiv(unsigned d) {
+  return {d, d <= 1 ? 0u : static_cast<unsigned>((0x100000000ull + d - 1) / d)};
+}
+__device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  return f.m ? static_cast<int>(__umulhi(static_cast<unsigned>(x), f.m)) : x;
+}
+
+// Transition i of the launch: fine grid G[i + 1] (n) -> coarse grid G[i] (c).
+struct SmallLevel {
+  int n[3], c[3];
+  int toff[3];  // each axis's table block, elements from the table base
+  FastDiv dc2, dc1, dn1;
 };
 
-__device__ __forceinline__ int grid_size(const int n[3]) { return n[0] * n[1] * n[2]; }
-
-// F = R v - X v_c on the coarse grid of one transition; v is the fine grid,
-// v_c its values on the coarse nodes (read from the nodal positions of v).
-// Tap positions are clamped into the grid under zero weights, so every load
-// of a node is unconditional and a thread's loads pipeline.
 template <typename T>
-__device__ void load_vector_small(const LevelK<T>& L, bool dec, const T* v, T* F) {
-  const int n1 = L.ax[1].n, n2 = L.ax[2].n;
-  const int c1 = L.ax[1].nc, c2 = L.ax[2].nc;
-  const int nco = L.ax[0].nc * c1 * c2;
-  for (int idx = threadIdx.x; idx < nco; idx += blockDim.x) {
-    const int k2 = idx % c2, k01 = idx / c2, k1 = k01 % c1, k0 = k01 / c1;
-    const int kk[3] = {k0, k1, k2};
-    int j[3][5], q[3][3];
-    T w[3][5], x[3][3];
+struct SmallSeg {  // one table array copied to shared memory
+  const T* src;
+  int dst, count;
+};
+
+template <typename T>
+struct SmallParams {
+  SmallLevel lv[kSmallMaxLevels];
+  int goff[kSmallMaxLevels + 1];  // G[i], elements from the shared-memory base
+  int boff;                       // load-vector scratch (S, then F)
+  int ntop;                       // nodes of the highest grid G[nlev]
+  int nseg;
+  SmallSeg<T> seg[kSmallSegs];
+};
+
+// One axis's tables in shared memory, in this order: iwl, iwr [n],
+// rw [5 nc], X [3 nc] (R P or R S by direction), ta, tm, tc [nc].
+template <typename T>
+struct AxS {
+  const T *iwl, *iwr, *rw, *x, *ta, *tm, *tc;
+};
+__host__ __device__ __forceinline__ int axis_table_size(int n, int nc) { return 2 * n + 11 * nc; }
+template <typename T>
+__device__ __forceinline__ AxS<T> axis_smem(const T* tab, int off, int n, int nc) {
+  AxS<T> a;
+  a.iwl = tab + off;
+  a.iwr = a.iwl + n;
+  a.rw = a.iwr + n;
+  a.x = a.rw + 5 * nc;
+  a.ta = a.x + 3 * nc;
+  a.tm = a.ta + nc;
+  a.tc = a.tm + nc;
+  return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Load vector, first pass: S[j0][k1][k2] = sum_b R1[k1][b] sum_o R2[k2][o]
+// v[j0][cpos(k1) + b - 2][cpos(k2) + o - 2] on every fine plane j0 (taps
+// outside the grid read as zero).  A thread walks one (j0, k2) line along
+// axis 1, forming each fine row's axis-2 sum once and keeping five of them.
+template <typename T>
+__device__ void lv_rows(const SmallLevel& L, const T* tab, const T* v, T* S) {
+  const int n1 = L.n[1], n2 = L.n[2], c1 = L.c[1], c2 = L.c[2];
+  const AxS<T> a1 = axis_smem(tab, L.toff[1], n1, c1);
+  const AxS<T> a2 = axis_smem(tab, L.toff[2], n2, c2);
+  const int items = L.n[0] * c2;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int j0 = fdiv(it, L.dc2), k2 = it - j0 * c2;
+    const int p2 = cpos(k2, n2);
+    int jc[5];
+    T wc[5];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const AxisK<T>& ax = L.ax[a];
-      const int n = ax.n, nc = ax.nc, k = kk[a], p = cpos(k, n);
-      const T* X = dec ? ax.xd : ax.xr;
-#pragma unroll
-      for (int o = 0; o < 5; ++o) {
-        const int jj = p + o - 2;
-        const bool in = jj >= 0 && jj < n;
-        j[a][o] = in ? jj : p;
-        w[a][o] = in ? __ldg(ax.rw + 5 * k + o) : T(0);
-      }
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int qq = k - 1 + d;
-        const bool in = qq >= 0 && qq < nc;
-        q[a][d] = cpos(in ? qq : k, n);
-        x[a][d] = in ? __ldg(X + 3 * k + d) : T(0);
-      }
+    for (int o = 0; o < 5; ++o) {
+      const int jj = p2 + o - 2;
+      const bool in = jj >= 0 && jj < n2;
+      jc[o] = in ? jj : p2;
+      wc[o] = in ? a2.rw[5 * k2 + o] : T(0);
     }
-    T acc = T(0);
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-      T s1 = T(0);
-#pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        const T* row = v + (j[0][a] * n1 + j[1][b]) * n2;
-        s1 += w[1][b] * ((w[2][0] * row[j[2][0]] + w[2][1] * row[j[2][1]]) +
-                         (w[2][2] * row[j[2][2]] + (w[2][3] * row[j[2][3]] + w[2][4] * row[j[2][4]])));
+    const T* plane = v + j0 * n1 * n2;
+    auto rowsum = [&](int j1) -> T {
+      if (j1 < 0 || j1 >= n1) return T(0);
+      const T* r = plane + j1 * n2;
+      return (wc[0] * r[jc[0]] + wc[1] * r[jc[1]]) + (wc[2] * r[jc[2]] + (wc[3] * r[jc[3]] + wc[4] * r[jc[4]]));
+    };
+    T w0 = T(0), w1 = T(0), w2 = rowsum(0), w3 = rowsum(1), w4 = rowsum(2);
+    int p = 0;
+    T* out = S + j0 * c1 * c2 + k2;
+    for (int k1 = 0; k1 < c1; ++k1) {
+      if (k1 > 0) {
+        const int pn = cpos(k1, n1);
+        if (pn - p == 2) {
+          w0 = w2; w1 = w3; w2 = w4;
+          w3 = rowsum(pn + 1);
+          w4 = rowsum(pn + 2);
+        } else {
+          w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+          w4 = rowsum(pn + 2);
+        }
+        p = pn;
       }
-      acc += w[0][a] * s1;
+      const T* r1 = a1.rw + 5 * k1;
+      out[k1 * c2] = (r1[0] * w0 + r1[1] * w1) + (r1[2] * w2 + (r1[3] * w3 + r1[4] * w4));
     }
-    T xs = T(0);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      T s1 = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const T* row = v + (q[0][a] * n1 + q[1][b]) * n2;
-        s1 += x[1][b] * (x[2][0] * row[q[2][0]] + x[2][1] * row[q[2][1]] + x[2][2] * row[q[2][2]]);
-      }
-      xs += x[0][a] * s1;
-    }
-    F[idx] = acc - xs;
   }
 }
 
-// Thomas solves of M_c along every axis of the coarse grid F (one thread
-// per line); values and factors are read eight rows ahead of each
-// recurrence, so the chain waits on arithmetic rather than on loads.
+// Load vector, second pass: F[k0][k1][k2] = sum_a R0[k0][a] S[cpos(k0) + a - 2]
+// - sum_d X0[k0][d] E[k0 - 1 + d], with E[k] = sum X1 X2 of v on the nodal
+// positions of nodal plane k.  A thread walks one coarse (k1, k2) column
+// along axis 0 and writes F[k0 - 1] over S once F[k0] is formed: every
+// later step reads planes of S above cpos(k0) + 2 >= k0 only.
 template <typename T>
-__device__ void solves_small(const LevelK<T>& L, T* F) {
-  const int c[3] = {L.ax[0].nc, L.ax[1].nc, L.ax[2].nc};
+__device__ void lv_planes(const SmallLevel& L, const T* tab, const T* v, T* SF) {
+  const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+  const int c0 = L.c[0], c1 = L.c[1], c2 = L.c[2];
+  const AxS<T> a0 = axis_smem(tab, L.toff[0], n0, c0);
+  const AxS<T> a1 = axis_smem(tab, L.toff[1], n1, c1);
+  const AxS<T> a2 = axis_smem(tab, L.toff[2], n2, c2);
+  const int items = c1 * c2, cs = c1 * c2;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int k1 = fdiv(it, L.dc2), k2 = it - k1 * c2;
+    int o1[3], o2[3];
+    T x1[3], x2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int q1 = k1 - 1 + d, q2 = k2 - 1 + d;
+      const bool in1 = q1 >= 0 && q1 < c1, in2 = q2 >= 0 && q2 < c2;
+      o1[d] = cpos(in1 ? q1 : k1, n1) * n2;
+      x1[d] = in1 ? a1.x[3 * k1 + d] : T(0);
+      o2[d] = cpos(in2 ? q2 : k2, n2);
+      x2[d] = in2 ? a2.x[3 * k2 + d] : T(0);
+    }
+    auto E = [&](int k) -> T {
+      if (k < 0 || k >= c0) return T(0);
+      const T* pl = v + cpos(k, n0) * n1 * n2;
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T* r = pl + o1[b];
+        s += x1[b] * (x2[0] * r[o2[0]] + x2[1] * r[o2[1]] + x2[2] * r[o2[2]]);
+      }
+      return s;
+    };
+    T* col = SF + k1 * c2 + k2;
+    auto sval = [&](int j0) -> T { return (j0 >= 0 && j0 < n0) ? col[j0 * cs] : T(0); };
+    T w0 = T(0), w1 = T(0), w2 = sval(0), w3 = sval(1), w4 = sval(2);
+    T em = T(0), e0 = E(0), ep = E(1);
+    int p = 0;
+    T prev = T(0);
+    for (int k0 = 0; k0 < c0; ++k0) {
+      if (k0 > 0) {
+        const int pn = cpos(k0, n0);
+        if (pn - p == 2) {
+          w0 = w2; w1 = w3; w2 = w4;
+          w3 = sval(pn + 1);
+          w4 = sval(pn + 2);
+        } else {
+          w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+          w4 = sval(pn + 2);
+        }
+        p = pn;
+        em = e0; e0 = ep;
+        ep = E(k0 + 1);
+      }
+      const T* r0 = a0.rw + 5 * k0;
+      const T* xx = a0.x + 3 * k0;
+      const T f = ((r0[0] * w0 + r0[1] * w1) + (r0[2] * w2 + (r0[3] * w3 + r0[4] * w4))) -
+                  (xx[0] * em + xx[1] * e0 + xx[2] * ep);
+      if (k0 > 0) col[(k0 - 1) * cs] = prev;
+      prev = f;
+    }
+    col[(c0 - 1) * cs] = prev;
+  }
+}
+
+// Thomas solves of M_c along every axis of F (one thread per line); values
+// and factors are read eight rows ahead of each recurrence.
+template <typename T>
+__device__ void solves_small(const SmallLevel& L, const T* tab, T* F) {
+  const int c0 = L.c[0], c1 = L.c[1], c2 = L.c[2];
   for (int a = 2; a >= 0; --a) {
-    const AxisK<T>& ax = L.ax[a];
-    const int nc = c[a];
-    if (L.ax[a].n > 1) {
-      const int stride = a == 2 ? 1 : a == 1 ? c[2] : c[1] * c[2];
-      const int lines = (c[0] * c[1] * c[2]) / nc;
+    if (L.n[a] > 1) {
+      const int nc = L.c[a];
+      const AxS<T> ax = axis_smem(tab, L.toff[a], L.n[a], nc);
+      const int stride = a == 2 ? 1 : a == 1 ? c2 : c1 * c2;
+      const int lines = a == 2 ? c0 * c1 : a == 1 ? c0 * c2 : c1 * c2;
       for (int line = threadIdx.x; line < lines; line += blockDim.x) {
-        // Line index -> (outer, inner) around the solved axis.
-        const int inner = line % stride, outer = line / stride;
-        T* l = F + outer * nc * stride + inner;
+        int base;
+        if (a == 2) {
+          base = line * c2;
+        } else if (a == 1) {
+          const int k0 = fdiv(line, L.dc2);
+          base = k0 * c1 * c2 + (line - k0 * c2);
+        } else {
+          base = line;
+        }
+        T* l = F + base;
         T y = T(0);
         for (int k0 = 0; k0 < nc; k0 += 8) {
           T f[8], ta[8], tm[8];
@@ -120,8 +269,8 @@ __device__ void solves_small(const LevelK<T>& L, T* F) {
           for (int u = 0; u < 8; ++u) {
             const int k = min(k0 + u, nc - 1);
             f[u] = l[k * stride];
-            ta[u] = __ldg(ax.ta + k);
-            tm[u] = __ldg(ax.tm + k);
+            ta[u] = ax.ta[k];
+            tm[u] = ax.tm[k];
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u)
@@ -137,7 +286,7 @@ __device__ void solves_small(const LevelK<T>& L, T* F) {
           for (int u = 0; u < 8; ++u) {
             const int k = max(k0 - u, 0);
             yv[u] = l[k * stride];
-            tc[u] = __ldg(ax.tc + k);
+            tc[u] = ax.tc[k];
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u)
@@ -152,178 +301,237 @@ __device__ void solves_small(const LevelK<T>& L, T* F) {
   }
 }
 
-// Multilinear interpolation at fine node (j0, j1, j2) from coarse values
-// `cv` (coarse grid layout, or, with from_fine, the nodal positions of the
-// fine grid `cv`): always the 8 corners (a nodal axis repeats its node under
-// weights 1 and 0, which passes the value unrounded), all loads issued
-// before the arithmetic.
-template <typename T>
-__device__ __forceinline__ T interp_small(const LevelK<T>& L, const T* cv, bool from_fine, int j0,
-                                          int j1, int j2) {
-  const int j[3] = {j0, j1, j2};
-  int kl[3], kr[3];
-  T wl[3], wr[3];
-  bool q[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const AxisK<T>& ax = L.ax[a];
-    q[a] = is_coef(j[a], ax.n);
-    kl[a] = q[a] ? (j[a] >> 1) : nodal_k(j[a], ax.n, ax.nc);
-    kr[a] = q[a] ? kl[a] + 1 : kl[a];
-    wl[a] = q[a] ? __ldg(ax.iwl + j[a]) : T(1);
-    wr[a] = q[a] ? __ldg(ax.iwr + j[a]) : T(0);
-    if (from_fine) {
-      kl[a] = cpos(kl[a], ax.n);
-      kr[a] = cpos(kr[a], ax.n);
+// Coefficients (decomposition: v -= Pi(v_c) off the nodal positions) or
+// interpolation (recomposition: v += Pi(c) off them, v = c on them) for one
+// level.  An item is a fine row (j0, j1) and a coarse column k2: the nodal
+// column cpos(k2) and, when it is a coefficient column, 2 k2 + 1.  The
+// corners are v's nodal positions (decomposition; never written here) or the
+// coarse grid G (recomposition).
+template <typename T, bool DEC>
+__device__ void interp_pass(const SmallLevel& L, const T* tab, T* v, const T* G) {
+  const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+  const int c0 = L.c[0], c1 = L.c[1], c2 = L.c[2];
+  const AxS<T> a0 = axis_smem(tab, L.toff[0], n0, c0);
+  const AxS<T> a1 = axis_smem(tab, L.toff[1], n1, c1);
+  const AxS<T> a2 = axis_smem(tab, L.toff[2], n2, c2);
+  const int items = n0 * n1 * c2;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int q = fdiv(it, L.dc2), k2 = it - q * c2;
+    const int j0 = fdiv(q, L.dn1), j1 = q - j0 * n1;
+    const bool q0 = is_coef(j0, n0), q1 = is_coef(j1, n1);
+    const int kl0 = q0 ? (j0 >> 1) : nodal_k(j0, n0, c0), kr0 = q0 ? kl0 + 1 : kl0;
+    const int kl1 = q1 ? (j1 >> 1) : nodal_k(j1, n1, c1), kr1 = q1 ? kl1 + 1 : kl1;
+    const int jc = 2 * k2 + 1;
+    const bool hasc = jc < n2 - 1;  // odd and inside the row: a coefficient column
+    const int k2r = hasc ? k2 + 1 : k2;
+    int rll, rlr, rrl, rrr, cl, cr;
+    if (DEC) {
+      const int pl0 = cpos(kl0, n0) * n1, pr0 = cpos(kr0, n0) * n1;
+      const int pl1 = cpos(kl1, n1), pr1 = cpos(kr1, n1);
+      rll = (pl0 + pl1) * n2; rlr = (pl0 + pr1) * n2;
+      rrl = (pr0 + pl1) * n2; rrr = (pr0 + pr1) * n2;
+      cl = cpos(k2, n2); cr = cpos(k2r, n2);
+    } else {
+      rll = (kl0 * c1 + kl1) * c2; rlr = (kl0 * c1 + kr1) * c2;
+      rrl = (kr0 * c1 + kl1) * c2; rrr = (kr0 * c1 + kr1) * c2;
+      cl = k2; cr = k2r;
+    }
+    const T* cv = DEC ? v : G;
+    const T vll = cv[rll + cl], vlr = cv[rlr + cl], vrl = cv[rrl + cl], vrr = cv[rrr + cl];
+    const T ull = cv[rll + cr], ulr = cv[rlr + cr], url = cv[rrl + cr], urr = cv[rrr + cr];
+    const T wl0 = q0 ? a0.iwl[j0] : T(1), wr0 = q0 ? a0.iwr[j0] : T(0);
+    const T wl1 = q1 ? a1.iwl[j1] : T(1), wr1 = q1 ? a1.iwr[j1] : T(0);
+    auto lerp01 = [&](T ll, T lr, T rl, T rr) -> T {
+      const T a = q1 ? wl1 * ll + wr1 * lr : ll;
+      const T b = q1 ? wl1 * rl + wr1 * rr : rl;
+      return q0 ? wl0 * a + wr0 * b : a;
+    };
+    const T rl = lerp01(vll, vlr, vrl, vrr);
+    T* row = v + (j0 * n1 + j1) * n2;
+    const int jn = cpos(k2, n2);
+    if (q0 || q1) {
+      if (DEC) row[jn] -= rl;
+      else row[jn] += rl;
+    } else if (!DEC) {
+      row[jn] = rl;
+    }
+    if (hasc) {
+      const T rr = lerp01(ull, ulr, url, urr);
+      const T pv = a2.iwl[jc] * rl + a2.iwr[jc] * rr;
+      if (DEC) row[jc] -= pv;
+      else row[jc] += pv;
     }
   }
-  const int m1 = from_fine ? L.ax[1].n : L.ax[1].nc, m2 = from_fine ? L.ax[2].n : L.ax[2].nc;
-  auto at = [&](int a0, int a1, int a2) { return cv[(a0 * m1 + a1) * m2 + a2]; };
-  const T v000 = at(kl[0], kl[1], kl[2]), v001 = at(kl[0], kl[1], kr[2]);
-  const T v010 = at(kl[0], kr[1], kl[2]), v011 = at(kl[0], kr[1], kr[2]);
-  const T v100 = at(kr[0], kl[1], kl[2]), v101 = at(kr[0], kl[1], kr[2]);
-  const T v110 = at(kr[0], kr[1], kl[2]), v111 = at(kr[0], kr[1], kr[2]);
-  auto r2 = [&](T a, T b) { return q[2] ? wl[2] * a + wr[2] * b : a; };
-  auto r1 = [&](T a, T b) { return q[1] ? wl[1] * a + wr[1] * b : a; };
-  const T a0 = r1(r2(v000, v001), r2(v010, v011));
-  const T a1 = r1(r2(v100, v101), r2(v110, v111));
-  return q[0] ? wl[0] * a0 + wr[0] * a1 : a0;
+}
+
+// The nodal positions of a fine grid (n) and its coarse grid (c): element k
+// of the coarse grid and the fine element it sits on.
+__device__ __forceinline__ int nodal_index(const SmallLevel& L, int k) {
+  const int q = fdiv(k, L.dc2), k2 = k - q * L.c[2];
+  const int k0 = fdiv(q, L.dc1), k1 = q - k0 * L.c[1];
+  return (cpos(k0, L.n[0]) * L.n[1] + cpos(k1, L.n[1])) * L.n[2] + cpos(k2, L.n[2]);
 }
 
 template <typename T, bool DEC>
-__global__ void __launch_bounds__(kSmallThreads)
-small_levels_kernel(SmallLevels<T> sl, int nlev, T* __restrict__ data) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512, 1)
+small_levels_kernel(const __grid_constant__ SmallParams<T> sp, int nlev, T* __restrict__ data) {
   grid_dep_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* base = reinterpret_cast<T*>(smem_raw);
-  // Grids G[i], i = 0..nlev (G[nlev] the top), then the load-vector scratch.
-  T* G[kSmallMaxLevels + 1];
-  int gsz[kSmallMaxLevels + 1];
-  {
-    size_t off = 0;
-    for (int i = 0; i <= nlev; ++i) {
-      const LevelK<T>& L = sl.lv[i < nlev ? i : nlev - 1];
-      const int d[3] = {i < nlev ? L.ax[0].nc : L.ax[0].n, i < nlev ? L.ax[1].nc : L.ax[1].n,
-                        i < nlev ? L.ax[2].nc : L.ax[2].n};
-      gsz[i] = grid_size(d);
-      G[i] = base + off;
-      off += gsz[i];
-    }
-    base += off;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const T* tab = sm;
+  T* top = sm + sp.goff[nlev];
+  const int ntop = sp.ntop;
+  // Every table and the highest grid through asynchronous copies, all in
+  // flight at once.
+  for (int s = threadIdx.x >> 5; s < sp.nseg; s += blockDim.x >> 5) {
+    const SmallSeg<T> g = sp.seg[s];
+    for (int e = threadIdx.x & 31; e < g.count; e += 32) cp_async_elem(sm + g.dst + e, g.src + e);
   }
-  T* Ft = base;
-  const int ntop = gsz[nlev];
-  // Eight loads of a thread in flight at a time (one CTA moves the grid).
-  for (int i0 = threadIdx.x; i0 < ntop; i0 += 8 * blockDim.x) {
-    T t[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + u * blockDim.x;
-      t[u] = i < ntop ? data[i] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i < ntop) G[nlev][i] = t[u];
-    }
-  }
+  constexpr int VEC = 16 / sizeof(T);
+  const bool aligned = (reinterpret_cast<uintptr_t>(data) & 15) == 0;
+  const int nv = aligned ? ntop / VEC : 0;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cp_async_16(top + i * VEC, data + i * VEC);
+  for (int i = nv * VEC + threadIdx.x; i < ntop; i += blockDim.x) cp_async_elem(top + i, data + i);
+  cp_async_wait_all();
   __syncthreads();
+
+  T* SF = sm + sp.boff;
   if (DEC) {
     for (int i = nlev - 1; i >= 0; --i) {
-      const LevelK<T>& L = sl.lv[i];
-      T* v = G[i + 1];
-      const int n0 = L.ax[0].n, n1 = L.ax[1].n, n2 = L.ax[2].n;
-      const int c1 = L.ax[1].nc, c2 = L.ax[2].nc;
-      load_vector_small(L, true, v, Ft);
+      const SmallLevel& L = sp.lv[i];
+      T* v = sm + sp.goff[i + 1];
+      T* G = sm + sp.goff[i];
+      lv_rows(L, tab, v, SF);
       __syncthreads();
-      solves_small(L, Ft);
-      for (int k = threadIdx.x; k < gsz[i]; k += blockDim.x) {
-        const int k2 = k % c2, k1 = (k / c2) % c1, k0 = k / (c1 * c2);
-        G[i][k] = v[(cpos(k0, n0) * n1 + cpos(k1, n1)) * n2 + cpos(k2, n2)] + Ft[k];
-      }
-      // Coefficients from the (unchanged) nodal values of v.
-      for (int x = threadIdx.x; x < gsz[i + 1]; x += blockDim.x) {
-        const int j2 = x % n2, j1 = (x / n2) % n1, j0 = x / (n1 * n2);
-        if (is_coef(j0, n0) || is_coef(j1, n1) || is_coef(j2, n2))
-          v[x] -= interp_small(L, v, true, j0, j1, j2);
-      }
+      lv_planes(L, tab, v, SF);
+      __syncthreads();
+      solves_small(L, tab, SF);
+      const int nc = L.c[0] * L.c[1] * L.c[2];
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) G[k] = v[nodal_index(L, k)] + SF[k];
+      interp_pass<T, true>(L, tab, v, G);
       __syncthreads();
     }
     // Final coarse values into the nodal positions, coarsest first.
     for (int i = 0; i < nlev; ++i) {
-      const LevelK<T>& L = sl.lv[i];
-      const int n0 = L.ax[0].n, n1 = L.ax[1].n, n2 = L.ax[2].n;
-      const int c1 = L.ax[1].nc, c2 = L.ax[2].nc;
-      for (int k = threadIdx.x; k < gsz[i]; k += blockDim.x) {
-        const int k2 = k % c2, k1 = (k / c2) % c1, k0 = k / (c1 * c2);
-        G[i + 1][(cpos(k0, n0) * n1 + cpos(k1, n1)) * n2 + cpos(k2, n2)] = G[i][k];
-      }
+      const SmallLevel& L = sp.lv[i];
+      const T* G = sm + sp.goff[i];
+      T* v = sm + sp.goff[i + 1];
+      const int nc = L.c[0] * L.c[1] * L.c[2];
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) v[nodal_index(L, k)] = G[k];
       __syncthreads();
     }
   } else {
     // Coarse grids from the nodal positions, finest first.
     for (int i = nlev - 1; i >= 0; --i) {
-      const LevelK<T>& L = sl.lv[i];
-      const int n0 = L.ax[0].n, n1 = L.ax[1].n, n2 = L.ax[2].n;
-      const int c1 = L.ax[1].nc, c2 = L.ax[2].nc;
-      for (int k = threadIdx.x; k < gsz[i]; k += blockDim.x) {
-        const int k2 = k % c2, k1 = (k / c2) % c1, k0 = k / (c1 * c2);
-        G[i][k] = G[i + 1][(cpos(k0, n0) * n1 + cpos(k1, n1)) * n2 + cpos(k2, n2)];
-      }
+      const SmallLevel& L = sp.lv[i];
+      const T* v = sm + sp.goff[i + 1];
+      T* G = sm + sp.goff[i];
+      const int nc = L.c[0] * L.c[1] * L.c[2];
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) G[k] = v[nodal_index(L, k)];
       __syncthreads();
     }
     for (int i = 0; i < nlev; ++i) {
-      const LevelK<T>& L = sl.lv[i];
-      T* v = G[i + 1];
-      const int n0 = L.ax[0].n, n1 = L.ax[1].n, n2 = L.ax[2].n;
-      const int c1 = L.ax[1].nc, c2 = L.ax[2].nc;
-      load_vector_small(L, false, v, Ft);
+      const SmallLevel& L = sp.lv[i];
+      T* v = sm + sp.goff[i + 1];
+      T* G = sm + sp.goff[i];
+      lv_rows(L, tab, v, SF);
       __syncthreads();
-      solves_small(L, Ft);
-      for (int k = threadIdx.x; k < gsz[i]; k += blockDim.x) G[i][k] -= Ft[k];
+      lv_planes(L, tab, v, SF);
       __syncthreads();
-      for (int x = threadIdx.x; x < gsz[i + 1]; x += blockDim.x) {
-        const int j2 = x % n2, j1 = (x / n2) % n1, j0 = x / (n1 * n2);
-        if (is_coef(j0, n0) || is_coef(j1, n1) || is_coef(j2, n2)) {
-          v[x] += interp_small(L, G[i], false, j0, j1, j2);
-        } else {
-          const int k0 = nodal_k(j0, n0, L.ax[0].nc), k1 = nodal_k(j1, n1, c1);
-          v[x] = G[i][(k0 * c1 + k1) * c2 + nodal_k(j2, n2, c2)];
-        }
-      }
+      solves_small(L, tab, SF);
+      const int nc = L.c[0] * L.c[1] * L.c[2];
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) G[k] -= SF[k];
+      __syncthreads();
+      interp_pass<T, false>(L, tab, v, G);
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < ntop; i += blockDim.x) data[i] = G[nlev][i];
+  if (aligned) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const V* src = reinterpret_cast<const V*>(top);
+    V* dst = reinterpret_cast<V*>(data);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = src[i];
+  }
+  for (int i = nv * VEC + threadIdx.x; i < ntop; i += blockDim.x) data[i] = top[i];
+}
+
+// Shared-memory layout (elements of T): every axis table block, the coarse
+// grids G[0 .. nlev - 1], the load-vector scratch (n0 c1 c2 of the largest
+// transition, which also holds F), then the highest grid on a 16-byte
+// boundary.  Fills `sp` when given; returns the bytes.
+template <typename T>
+size_t small_layout(const LevelK<T>* lv, int nlev, bool dec, SmallParams<T>* sp) {
+  constexpr int VEC = 16 / sizeof(T);
+  auto up = [](size_t x) { return (x + VEC - 1) / VEC * VEC; };
+  size_t off = 0;
+  int nseg = 0;
+  for (int i = 0; i < nlev; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const AxisK<T>& ax = lv[i].ax[a];
+      const int n = ax.n, nc = ax.nc;
+      if (sp) {
+        sp->lv[i].toff[a] = static_cast<int>(off);
+        const T* src[kTabArrays] = {ax.iwl, ax.iwr, ax.rw, dec ? ax.xd : ax.xr, ax.ta, ax.tm, ax.tc};
+        const int cnt[kTabArrays] = {n, n, 5 * nc, 3 * nc, nc, nc, nc};
+        int d = static_cast<int>(off);
+        for (int t = 0; t < kTabArrays; ++t) {
+          if (src[t] != nullptr && cnt[t] > 0) sp->seg[nseg++] = SmallSeg<T>{src[t], d, cnt[t]};
+          d += cnt[t];
+        }
+      }
+      off += axis_table_size(n, nc);
+    }
+  off = up(off);
+  size_t scratch = 0;
+  for (int i = 0; i < nlev; ++i) {
+    const LevelK<T>& L = lv[i];
+    if (sp) {
+      SmallLevel& s = sp->lv[i];
+      for (int a = 0; a < 3; ++a) {
+        s.n[a] = L.ax[a].n;
+        s.c[a] = L.ax[a].nc;
+      }
+      s.dc2 = make_fastdiv(L.ax[2].nc);
+      s.dc1 = make_fastdiv(L.ax[1].nc);
+      s.dn1 = make_fastdiv(L.ax[1].n);
+      sp->goff[i] = static_cast<int>(off);
+    }
+    off += size_t(L.ax[0].nc) * L.ax[1].nc * L.ax[2].nc;
+    scratch = std::max(scratch, size_t(L.ax[0].n) * L.ax[1].nc * L.ax[2].nc);
+  }
+  off = up(off);
+  if (sp) sp->boff = static_cast<int>(off);
+  off = up(off + scratch);
+  const LevelK<T>& Lt = lv[nlev - 1];
+  const size_t ntop = size_t(Lt.ax[0].n) * Lt.ax[1].n * Lt.ax[2].n;
+  if (sp) {
+    sp->goff[nlev] = static_cast<int>(off);
+    sp->ntop = static_cast<int>(ntop);
+    sp->nseg = nseg;
+  }
+  off += ntop;
+  return sizeof(T) * off;
 }
 
 }  // namespace
 
 template <typename T>
 size_t small_levels_smem(const LevelK<T>* lv, int nlev) {
-  // Grids of every level (coarsest .. top) and one coarse-sized scratch.
-  size_t total = 0, maxc = 0;
-  for (int i = 0; i < nlev; ++i) {
-    const size_t c = size_t(lv[i].ax[0].nc) * lv[i].ax[1].nc * lv[i].ax[2].nc;
-    total += c;
-    maxc = std::max(maxc, c);
-  }
-  total += size_t(lv[nlev - 1].ax[0].n) * lv[nlev - 1].ax[1].n * lv[nlev - 1].ax[2].n;
-  return sizeof(T) * (total + maxc);
+  return small_layout<T>(lv, nlev, true, nullptr);
 }
 
 template <typename T>
 cudaError_t launch_small_levels(const LevelK<T>* lv, int nlev, bool dec, T* data, int level,
                                 cudaStream_t s) {
   if (nlev < 1 || nlev > kSmallMaxLevels) return cudaErrorInvalidValue;
-  SmallLevels<T> sl{};
-  for (int i = 0; i < nlev; ++i) sl.lv[i] = lv[i];
-  const size_t smem = small_levels_smem(lv, nlev);
-  const size_t ntop = size_t(lv[nlev - 1].ax[0].n) * lv[nlev - 1].ax[1].n * lv[nlev - 1].ax[2].n;
-  TraceScope ts(kKSmallLevels, level, 2.0 * sizeof(T) * double(ntop), s);
+  SmallParams<T> sp{};
+  const size_t smem = small_layout<T>(lv, nlev, dec, &sp);
+  // The multiply-high divisions are exact for every index of these grids.
+  if (sp.ntop > kSmallMaxNodes) return cudaErrorInvalidValue;
+  TraceScope ts(kKSmallLevels, level, 2.0 * sizeof(T) * double(sp.ntop), s);
   auto kernel = dec ? small_levels_kernel<T, true> : small_levels_kernel<T, false>;
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  launch_pdl(kernel, dim3(1), dim3(kSmallThreads), smem, s, sl, nlev, data);
+  launch_pdl(kernel, dim3(1), dim3(small_threads<T>()), smem, s, sp, nlev, data);
   return cudaGetLastError();
 }
 
