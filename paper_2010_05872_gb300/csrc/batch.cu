@@ -80,6 +80,7 @@ struct BatchStage {
 
 constexpr int kBatchThreads = 288;
 constexpr int kLvNS = 4, kLvT1 = 4;  // the batched tiles keep their own shape
+constexpr int kLvGMax = 4;           // row groups of a load-vector tile (narrow fields)
 constexpr int kFinNS = 4, kFinT1 = FinishCfg<float>::T1;
 
 __global__ void __launch_bounds__(kBatchThreads, 2)
@@ -125,12 +126,12 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
     const long long c_run = clock64();
     switch (st.kind) {
       case kBLoadVecDec:
-        load_vector_march_tile<float, true, kLvNS, kLvT1, true, true, 1>(st.lv, st.fine, st.coarse, st.F,
+        load_vector_march_tile<float, true, kLvNS, kLvT1, true, true, 1, kLvGMax>(st.lv, st.fine, st.coarse, st.F,
                                                                 st.mg, st.fine_count, status,
                                                                 item.y, smem_raw);
         break;
       case kBLoadVecRec:
-        load_vector_march_tile<float, false, kLvNS, kLvT1, true, true, 1>(st.lv, st.fine, st.coarse, st.F,
+        load_vector_march_tile<float, false, kLvNS, kLvT1, true, true, 1, kLvGMax>(st.lv, st.fine, st.coarse, st.F,
                                                                  st.mg, st.fine_count, status,
                                                                  item.y, smem_raw);
         break;
@@ -256,7 +257,13 @@ int field_stages(const DevPlan& p, float* data, char* ws, int dir, const Tuning&
   };
   auto lv_stage = [&](int l, bool dec) -> int {
     BatchStage s = base(dec ? kBLoadVecDec : kBLoadVecRec, l);
-    if (!plan_geometry(s.lv, s.mg, 1, kLvT1, kLvNS) || s.mg.threads > kBatchThreads) return MGARD_ERR_SHAPE;
+    // As many row groups as the block holds for this width (one column per
+    // thread), no more than the coarse rows need.
+    const int gthreads = 32 * ((s.lv.ax[2].nc + 31) / 32);
+    const int groups = std::max(1, std::min({kLvGMax, kBatchThreads / gthreads,
+                                             (s.lv.ax[1].nc + kLvT1 - 1) / kLvT1}));
+    if (!plan_geometry(s.lv, s.mg, 1, kLvT1, kLvNS, groups) || s.mg.threads > kBatchThreads)
+      return MGARD_ERR_SHAPE;
     const int c0 = s.lv.ax[0].nc;
     s.mg.t0 = std::max(1, std::min(tu.lv_t0, c0));
     s.mg.nb0 = (c0 + s.mg.t0 - 1) / s.mg.t0;

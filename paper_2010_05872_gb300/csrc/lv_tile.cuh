@@ -20,6 +20,8 @@ struct MarchGeom {
   int pitch;           // elements between staged rows (n2 in 3D; the tile width in 2D)
   int BUF;             // elements of one plane buffer (16-byte multiple)
   int threads;         // CTA size
+  int groups;          // row groups (see load_vector_march_tile)
+  int gthreads;        // threads per row group
 };
 
 // Pipeline depth and coarse rows per CTA along axis 1, per element type.
@@ -44,11 +46,15 @@ struct MarchCfg<double> {
 
 // One tile (CTA work unit) of the marching load vector; `tile` plays the
 // role of the block index.  Any block of at least g.threads threads runs
-// it.  PERSIST: the CTA runs further tiles in the same launch, so the tile
+// it.  GMAX > 1 allows row groups: g.groups groups of g.gthreads threads
+// share the staged planes of a tile of g.groups x T1C coarse rows, group q
+// taking coarse rows q T1C .. q T1C + T1C - 1 (staged rows 2 q T1C onwards),
+// so a narrow grid keeps more warps of the block busy.  PERSIST: the CTA runs further tiles in the same launch, so the tile
 // invalidates its barriers at the end (the next tile sets them up again) and
 // reads its few plain-loaded elements through L2 (other CTAs of the launch
 // may have written them).
-template <typename T, bool DEC, int NS, int T1C, bool THREE, bool PERSIST = false, int CPT = 2>
+template <typename T, bool DEC, int NS, int T1C, bool THREE, bool PERSIST = false, int CPT = 2,
+          int GMAX = 1>
 __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
                                                        const T* __restrict__ fine,
                                                        T* __restrict__ coarse, T* __restrict__ F,
@@ -57,19 +63,24 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
                                                        unsigned char*) {
   // The dynamic shared memory of the launch (every tile starts at its base).
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  constexpr int S1M = THREE ? 2 * T1C + 3 : 1;  // staged rows
-  constexpr int TM = THREE ? T1C : 1;           // coarse rows per CTA
+  constexpr int S1M = THREE ? 2 * T1C + 3 : 1;  // staged rows of a row group
+  constexpr int S1T = THREE ? 2 * T1C * GMAX + 3 : 1;  // staged rows of the largest tile
+  constexpr int TM = THREE ? T1C : 1;           // coarse rows per row group
   constexpr int VEC = 16 / sizeof(T);
   constexpr int PADL = 2 * VEC;                 // zeroed elements before a tile
   __shared__ __align__(8) uint64_t bars[NS];
   __shared__ int s_off[NS];   // buffer index of tile element (0, 0)
-  __shared__ T s_w1[S1M][3];  // R1 weight of row s for coarse row base(s) + i
-  __shared__ T s_y1[S1M][3];  // X1 weight of nodal row s for the same coarse rows
-  __shared__ int s_rown[S1M]; // coarse row of a nodal row s, or -1
+  __shared__ T s_w1[S1T][3];  // R1 weight of row s for coarse row base(s) + i
+  __shared__ T s_y1[S1T][3];  // X1 weight of nodal row s for the same coarse rows
+  __shared__ int s_rown[S1T]; // coarse row of a nodal row s, or -1
   __shared__ T s_lg[S1M];     // row sums of the left-over column (see `lrows`)
   __shared__ T s_lh[S1M];
 
   const int tid = threadIdx.x;
+  const int grp = GMAX > 1 ? tid / g.gthreads : 0;          // row group
+  const int ltid = GMAX > 1 ? tid - grp * g.gthreads : tid;  // thread within it
+  const int roff = THREE ? grp * T1C : 0;                    // its first coarse row
+  const int soff = 2 * roff;                                 // its first staged row
   // The copies are issued by lane 0 of the last warp, which owns the fewest
   // columns (often one), so the issue work stays off the busiest warps.
   const int producer = static_cast<int>(blockDim.x) - 32;
@@ -94,7 +105,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
   // Zero the buffers (virtual rows and pads must hold finite values) and
   // build the row tables.
   for (int i = tid; i < NS * g.BUF; i += blockDim.x) vbuf[i] = T(0);
-  for (int s = tid; s < S1M; s += blockDim.x) {
+  for (int s = tid; s < S1T; s += blockDim.x) {
     const int j1 = rbase + s;
     const bool valid = j1 >= 0 && j1 < n1;
     const bool nod = valid && !is_coef(j1, n1);
@@ -133,14 +144,17 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
   // keeps the column's weights in rwc[0] / xc[0] and its sums and
   // accumulators in G1[0][0], H1[0][0], acc[0][.][0].
   constexpr int W = 2 * CPT + 3;
-  const bool lrows = CPT == 2 && S1M <= 32 && (T2 & 1) && (((T2 - 1) / 2) & 31) == 0;
+  const bool lrows = CPT == 2 && GMAX == 1 && S1M <= 32 && (T2 & 1) && (((T2 - 1) / 2) & 31) == 0;
   const int TP = lrows ? T2 - 1 : T2;  // columns taken in pairs
   const int lane = tid & 31;
   const bool lwarp = lrows && (tid >> 5) == (TP / 2) >> 5;
   const int kL = K2 + T2 - 1;          // the left-over column
-  const int kc0 = K2 + CPT * tid;
+  // Coarse rows of the group, and whether it has any (one group: the tile's).
+  const int T1g = GMAX > 1 && THREE ? max(0, min(T1C, T1 - roff)) : T1;
+  const bool gact = GMAX > 1 ? grp < g.groups && T1g > 0 : true;
+  const int kc0 = K2 + CPT * ltid;
   const int ccol = lwarp ? cpos(kL, n2) - cbase
-                         : (CPT * tid < TP ? cpos(kc0, n2) - cbase : 2);  // tile column of kc0's node
+                         : (CPT * ltid < TP ? cpos(kc0, n2) - cbase : 2);  // tile column of kc0's node
   bool actc[CPT];
   int dcol[CPT];
   T rwc[CPT][W], xc[CPT][W];
@@ -149,7 +163,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       const int k = lwarp ? kL : kc0 + c;
-      actc[c] = lwarp ? c == 0 : CPT * tid + c < TP;
+      actc[c] = lwarp ? c == 0 : gact && CPT * ltid + c < TP;
       dcol[c] = actc[c] && !lwarp ? cpos(k, n2) - cpos(kc0, n2) : 2 * c;
 #pragma unroll
       for (int oo = 0; oo < W; ++oo) rwc[c][oo] = xc[c][oo] = T(0);
@@ -206,12 +220,12 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     while (kdone < K0 + T0 && (all || cpos(kdone, n0) + 2 <= upto_plane)) {
 #pragma unroll
       for (int t = 0; t < TM; ++t) {
-        T* dst = F + (static_cast<int64_t>(kdone) * c1 + (K1 + t)) * c2 + kc0;
+        T* dst = F + (static_cast<int64_t>(kdone) * c1 + (K1 + roff + t)) * c2 + kc0;
         if (lwarp && t == 0 && lane < T1)
           F[(static_cast<int64_t>(kdone) * c1 + (K1 + lane)) * c2 + kL] = acc[0][0][0];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-          if (!lwarp && actc[c] && t < T1) dst[c] = acc[c][0][t];
+          if (!lwarp && actc[c] && t < T1g) dst[c] = acc[c][0][t];
           acc[c][0][t] = acc[c][1][t];
           acc[c][1][t] = acc[c][2][t];
           acc[c][2][t] = T(0);
@@ -252,7 +266,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     }
 
     // Warps without a column of this tile skip the arithmetic.
-    if (CPT * (tid & ~31) < TP || lwarp) {
+    if ((gact && CPT * (ltid & ~31) < TP) || lwarp) {
     const bool pn = !is_coef(j, n0);  // nodal plane
     const int kj = pn ? nodal_k(j, n0, c0) : -1;
     const bool gplane = pn && kj >= K0 && kj < K0 + T0;
@@ -301,7 +315,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     } else {
 #pragma unroll
     for (int s = 0; s < S1M; ++s) {
-      const T* row = tile + s * g.pitch;
+      const T* row = tile + (s + soff) * g.pitch;
       T fe[W];  // window: tile columns ccol - 2 .. ccol + W - 3 of row s
       if constexpr (sizeof(T) == 4) {
         // Aligned 8-byte loads cover the window (8-byte words per thread: no
@@ -332,7 +346,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
         for (int o = (c ? 2 * c - 1 : 0); o < W && o <= 2 * c + 4; ++o) gs[c] += rwc[c][o] * fe[o];
       }
       const int base = (s & 1) ? (s - 3) / 2 : s / 2 - 2;
-      const int kr = THREE ? s_rown[s] : 0;
+      const int kr = THREE ? s_rown[s + soff] : 0;
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         if (!THREE) {
@@ -341,7 +355,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const int t = base + i;
-            if (t >= 0 && t < TM) G1[c][t] += s_w1[s][i] * gs[c];
+            if (t >= 0 && t < TM) G1[c][t] += s_w1[s + soff][i] * gs[c];
           }
         }
       }
@@ -357,11 +371,11 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
               const int t = base + i;
-              if (t >= 0 && t < TM) H1[c][t] += s_y1[s][i] * hs;
+              if (t >= 0 && t < TM) H1[c][t] += s_y1[s + soff][i] * hs;
             }
           }
         }
-        if (gplane && kr >= K1 && kr < K1 + T1) {
+        if (gplane && kr >= K1 + roff && kr < K1 + roff + T1g) {
           T* dst = coarse + (static_cast<int64_t>(kj) * c1 + kr) * c2 + kc0;
 #pragma unroll
           for (int c = 0; c < CPT; ++c)
@@ -399,20 +413,21 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 }
 
 // Tile shape of a level for CPT coarse columns per thread, T1 coarse rows per
-// tile and NS plane buffers (the per-level kernel's MarchCfg by default; the
-// batched kernel passes its own).
+// row group, `groups` row groups and NS plane buffers (the per-level kernel's
+// MarchCfg and one group by default; the batched kernel passes its own).
 template <typename T>
 inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g, int cpt = 2, int t1 = MarchCfg<T>::T1,
-                          int ns = MarchCfg<T>::NS) {
+                          int ns = MarchCfg<T>::NS, int groups = 1) {
   const int n1 = lv.ax[1].n, n2 = lv.ax[2].n, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
   const int vec = 16 / static_cast<int>(sizeof(T));
   if (n1 > 1) {
     if (c2 > cpt * kLvMaxThreads) return false;  // rows too wide for one CTA
-    g.t1 = t1;
+    g.t1 = t1 * groups;
     g.tc2 = c2;
     g.pitch = n2;
-    g.BUF = ((4 * vec + (2 * t1 + 3) * n2 + 4 + vec - 1) / vec) * vec;
+    g.BUF = ((4 * vec + (2 * g.t1 + 3) * n2 + 4 + vec - 1) / vec) * vec;
   } else {
+    groups = 1;
     g.t1 = 1;
     g.tc2 = c2 <= cpt * kLvMaxThreads ? c2 : cpt * kLvMaxThreads / 2;
     g.pitch = 2 * g.tc2 + 3;
@@ -420,8 +435,10 @@ inline bool plan_geometry(const LevelK<T>& lv, MarchGeom& g, int cpt = 2, int t1
   }
   g.nb2 = (c2 + g.tc2 - 1) / g.tc2;
   g.nb1 = (c1 + g.t1 - 1) / g.t1;
-  g.threads = 32 * (((g.tc2 + cpt - 1) / cpt + 31) / 32);
-  return g.threads <= kLvMaxThreads && sizeof(T) * static_cast<size_t>(ns) * g.BUF <= 200 * 1024;
+  g.gthreads = 32 * (((g.tc2 + cpt - 1) / cpt + 31) / 32);
+  g.groups = groups;
+  g.threads = g.gthreads * groups;
+  return g.gthreads <= kLvMaxThreads && sizeof(T) * static_cast<size_t>(ns) * g.BUF <= 200 * 1024;
 }
 
 
