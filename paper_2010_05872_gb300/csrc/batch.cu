@@ -80,8 +80,9 @@ struct BatchStage {
 
 constexpr int kBatchThreads = 288;
 constexpr int kLvNS = 4, kLvT1 = 4;  // the batched tiles keep their own shape
-constexpr int kLvGMax = 4;           // row groups of a load-vector tile (narrow fields)
+constexpr int kLvGMax = 8;           // row groups of a load-vector tile (narrow fields)
 constexpr int kFinNS = 4, kFinT1 = FinishCfg<float>::T1;
+constexpr int kFinGMax = 8;          // row groups of a finish tile (narrow fields)
 
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ items, int nitems,
@@ -156,7 +157,7 @@ batch_kernel(const BatchStage* __restrict__ stages, const int4* __restrict__ ite
         break;
       }
       default:
-        finish_march_tile<float, kFinNS, kFinT1, true>(st.lv, st.nodal_src, st.interp_src, st.sign,
+        finish_march_tile<float, kFinNS, kFinT1, true, kFinGMax>(st.lv, st.nodal_src, st.interp_src, st.sign,
                                                  st.fine, st.fg, status, item.y, smem_raw);
         break;
     }
@@ -317,7 +318,12 @@ int field_stages(const DevPlan& p, float* data, char* ws, int dir, const Tuning&
   };
   auto finish_stage = [&](int l, bool dec) -> int {
     BatchStage s = base(kBFinish, l);
-    if (!finish_geometry(s.lv, s.fg) || s.fg.threads > kBatchThreads) return MGARD_ERR_SHAPE;
+    // As many row groups as the block holds for this width (one fine column
+    // per thread), no more than the coarse rows need.
+    const int gthreads = 32 * ((s.lv.ax[2].n + 31) / 32);
+    const int groups = std::max(1, std::min({kFinGMax, kBatchThreads / gthreads,
+                                             (s.lv.ax[1].nc + kFinT1 - 1) / kFinT1}));
+    if (!finish_geometry(s.lv, s.fg, groups) || s.fg.threads > kBatchThreads) return MGARD_ERR_SHAPE;
     const int npairs = (s.lv.ax[0].n + 1) / 2;
     s.fg.t0 = std::max(1, std::min(tu.fin_t0, npairs));
     s.fg.nb0 = (npairs + s.fg.t0 - 1) / s.fg.t0;

@@ -32,6 +32,8 @@ struct FinishGeom {
   int nb0, nb1, nb2;     // CTAs along axes 0, 1, 2
   int FBUF, CBUF;        // elements of a fine-plane buffer and of a coarse-plane buffer
   int threads;
+  int groups;            // row groups (see finish_march_tile)
+  int gthreads;          // threads per row group
 };
 
 // Marching form: a CTA owns fine plane pairs [M0, M1) (planes 2m, 2m + 1) of
@@ -50,8 +52,11 @@ struct FinishGeom {
 // One tile (CTA work unit); `tile` plays the role of the block index and
 // `smem_raw` is the dynamic shared memory.  Any block of at least g.threads
 // threads runs it; a tile returns with its barriers invalidated so that the
-// next tile of a persistent CTA can set them up again.
-template <typename T, int NS, int T1C, bool PERSIST = false>
+// next tile of a persistent CTA can set them up again.  GMAX > 1 allows row
+// groups: g.groups groups of g.gthreads threads share the staged planes of a
+// tile of g.groups x T1C coarse rows, group q writing fine rows 2 q T1C ..
+// 2 q T1C + 2 T1C - 1 of it, so a narrow grid keeps more warps busy.
+template <typename T, int NS, int T1C, bool PERSIST = false, int GMAX = 1>
 __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
                                                   const T* __restrict__ nodal_src,
                                                   const T* __restrict__ interp_src, T sign,
@@ -68,6 +73,9 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
   __shared__ int s_nshift[NC];      // ring of nodal-source planes (decomposition)
 
   const int tid = threadIdx.x;
+  const int grp = GMAX > 1 ? tid / g.gthreads : 0;          // row group
+  const int ltid = GMAX > 1 ? tid - grp * g.gthreads : tid;  // column within the chunk
+  const int croff = grp * T1C, froff = 2 * croff;           // its first coarse / fine row
   // The copies are issued by lane 0 of the last warp, which owns the fewest
   // columns (often one), so the issue work stays off the busiest warps.
   const int producer = static_cast<int>(blockDim.x) - 32;
@@ -151,8 +159,8 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
   };
 
   // Column data of this thread (axis 2).
-  const int j2 = J2lo + tid;
-  const bool colact = tid < W2;
+  const int j2 = J2lo + ltid;
+  const bool colact = GMAX > 1 ? grp < g.groups && froff < R1 && ltid < W2 : tid < W2;
   const bool q2 = colact && is_coef(j2, n2);
   const int kn2 = colact ? nodal_k(j2, n2, c2) : 0;
   const int kl = (q2 ? (j2 >> 1) : kn2) - klo2, kr = q2 ? kl + 1 : kl;
@@ -162,29 +170,44 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
   // coarse row r / 2; odd row r mixes coarse rows r / 2 and r / 2 + 1, except
   // a last fine row n1 - 1 that is nodal (even n1): weights (0, 1).
   // The weights sit in shared memory (read after the first wait's barrier).
-  __shared__ T s_wl1[T1C], s_wr1[T1C];
-  unsigned q1mask = 0u;  // bit r: fine row r is a coefficient row
+  __shared__ T s_wl1[T1C * GMAX], s_wr1[T1C * GMAX];
+  unsigned q1mask = 0u;  // bit r: fine row froff + r is a coefficient row
+  if constexpr (GMAX == 1) {
 #pragma unroll
-  for (int i = 0; i < T1C; ++i) {
-    const int j1 = r1lo + 2 * i + 1;
-    const bool q = 2 * i + 1 < R1 && is_coef(j1, n1);
-    if (tid == i) {
+    for (int i = 0; i < T1C; ++i) {
+      const int j1 = r1lo + 2 * i + 1;
+      const bool q = 2 * i + 1 < R1 && is_coef(j1, n1);
+      if (tid == i) {
+        s_wl1[i] = q ? lv.ax[1].iwl[j1] : T(0);
+        s_wr1[i] = q ? lv.ax[1].iwr[j1] : T(1);
+      }
+      if (q) q1mask |= 1u << (2 * i + 1);
+    }
+  } else {
+    for (int i = tid; i < T1C * GMAX; i += blockDim.x) {
+      const int j1 = r1lo + 2 * i + 1;
+      const bool q = 2 * i + 1 < R1 && is_coef(j1, n1);
       s_wl1[i] = q ? lv.ax[1].iwl[j1] : T(0);
       s_wr1[i] = q ? lv.ax[1].iwr[j1] : T(1);
     }
-    if (q) q1mask |= 1u << (2 * i + 1);
+#pragma unroll
+    for (int i = 0; i < T1C; ++i) {
+      const int j1 = r1lo + froff + 2 * i + 1;
+      const bool q = froff + 2 * i + 1 < R1 && is_coef(j1, n1);
+      if (q) q1mask |= 1u << (2 * i + 1);
+    }
   }
   // Interpolant of coarse plane `cm` at this column and every owned fine row.
   auto interp_plane = [&](int cm, T (&out)[R1M]) {
-    const T* C = cbuf + static_cast<size_t>(cm % NC) * g.CBUF + s_cshift[cm % NC];
+    const T* C = cbuf + static_cast<size_t>(cm % NC) * g.CBUF + s_cshift[cm % NC] + croff * c2;
     T i2[RCM];
 #pragma unroll
     for (int i = 0; i < RCM; ++i)
-      i2[i] = (i < R1c) ? wl2 * C[i * c2 + kl] + wr2 * C[i * c2 + kr] : T(0);
+      i2[i] = (croff + i < R1c) ? wl2 * C[i * c2 + kl] + wr2 * C[i * c2 + kr] : T(0);
 #pragma unroll
     for (int i = 0; i < T1C; ++i) {
       out[2 * i] = i2[i];
-      out[2 * i + 1] = s_wl1[i] * i2[i] + s_wr1[i] * i2[i + 1];
+      out[2 * i + 1] = s_wl1[croff + i] * i2[i] + s_wr1[croff + i] * i2[i + 1];
     }
   };
 
@@ -224,17 +247,19 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
       // Fine plane 2m: nodal along axis 0, coarse plane m.
       {
         const int j0 = 2 * m;
-        const T* fb = fbuf + static_cast<size_t>(2 * stage) * g.FBUF + s_fshift[2 * stage];
-        T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo) * n2 + j2;
-        const T* nsrc = nbuf + static_cast<size_t>(m % NC) * g.CBUF + s_nshift[m % NC] + kcol;
+        const T* fb = fbuf + static_cast<size_t>(2 * stage) * g.FBUF + s_fshift[2 * stage] +
+                      froff * n2 + ltid;
+        T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo + froff) * n2 + j2;
+        const T* nsrc = nbuf + static_cast<size_t>(m % NC) * g.CBUF + s_nshift[m % NC] + kcol +
+                        croff * c2;
 #pragma unroll
         for (int r = 0; r < R1M; ++r) {
-          if (r < R1) {
+          if (froff + r < R1) {
             const bool nodal = !q2 && !((q1mask >> r) & 1u);
             // Fully nodal rows sit on coarse row r / 2, or (0, 1) row r / 2 + 1.
             const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
             const T v = A[r];
-            dst[r * n2] = nodal ? (sep ? nsrc[kr1 * c2] : v) : fb[r * n2 + tid] + sign * v;
+            dst[r * n2] = nodal ? (sep ? nsrc[kr1 * c2] : v) : fb[r * n2] + sign * v;
           }
         }
       }
@@ -244,17 +269,18 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
       if (j0 < n0) {
         const bool q0 = is_coef(j0, n0);
         const T wl0 = q0 ? lv.ax[0].iwl[j0] : T(0), wr0 = q0 ? lv.ax[0].iwr[j0] : T(1);
-        const T* fb = fbuf + static_cast<size_t>(2 * stage + 1) * g.FBUF + s_fshift[2 * stage + 1];
-        T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo) * n2 + j2;
+        const T* fb = fbuf + static_cast<size_t>(2 * stage + 1) * g.FBUF + s_fshift[2 * stage + 1] +
+                      froff * n2 + ltid;
+        T* dst = fine + (static_cast<int64_t>(j0) * n1 + r1lo + froff) * n2 + j2;
         const int mn = (m + 1) % NC;
-        const T* nsrc = nbuf + static_cast<size_t>(mn) * g.CBUF + s_nshift[mn] + kcol;
+        const T* nsrc = nbuf + static_cast<size_t>(mn) * g.CBUF + s_nshift[mn] + kcol + croff * c2;
 #pragma unroll
         for (int r = 0; r < R1M; ++r) {
-          if (r < R1) {
+          if (froff + r < R1) {
             const bool nodal = !q0 && !q2 && !((q1mask >> r) & 1u);
             const int kr1 = (r & 1) ? (r >> 1) + 1 : (r >> 1);
             const T v = wl0 * A[r] + wr0 * B[r];
-            dst[r * n2] = nodal ? (sep ? nsrc[kr1 * c2] : v) : fb[r * n2 + tid] + sign * v;
+            dst[r * n2] = nodal ? (sep ? nsrc[kr1 * c2] : v) : fb[r * n2] + sign * v;
           }
         }
       }
@@ -270,14 +296,17 @@ __device__ __forceinline__ void finish_march_tile(const LevelK<T>& lv,
 }
 
 template <typename T>
-inline bool finish_geometry(const LevelK<T>& lv, FinishGeom& g) {
+inline bool finish_geometry(const LevelK<T>& lv, FinishGeom& g, int groups = 1) {
   const int n1 = lv.ax[1].n, n2 = lv.ax[2].n, c1 = lv.ax[1].nc, c2 = lv.ax[2].nc;
-  g.t1 = (n1 == 1) ? 1 : FinishCfg<T>::T1;
+  if (n1 == 1) groups = 1;
+  g.t1 = (n1 == 1) ? 1 : FinishCfg<T>::T1 * groups;
   if (n1 == 1) g.tc2 = std::min(n2, kFMaxThreads - (kFMaxThreads % 2));
   else if (n2 <= kFMaxThreads) g.tc2 = n2;
   else return false;  // 3D rows wider than one CTA: not contiguous per plane
   if (g.tc2 < n2 && (g.tc2 & 1)) --g.tc2;
-  g.threads = 32 * ((g.tc2 + 31) / 32);
+  g.gthreads = 32 * ((g.tc2 + 31) / 32);
+  g.groups = groups;
+  g.threads = g.gthreads * groups;
   const int vec = 16 / static_cast<int>(sizeof(T));
   const int R1 = (n1 == 1) ? 1 : 2 * g.t1;
   g.FBUF = (((R1 - 1) * n2 + g.tc2 + 2 * vec) / vec + 1) * vec;
@@ -286,7 +315,7 @@ inline bool finish_geometry(const LevelK<T>& lv, FinishGeom& g) {
   g.CBUF = (((R1c - 1) * c2 + kwmax + 2 * vec) / vec + 1) * vec;
   g.nb1 = (c1 + g.t1 - 1) / g.t1;
   g.nb2 = (n2 + g.tc2 - 1) / g.tc2;
-  return g.threads <= kFMaxThreads;
+  return g.gthreads <= kFMaxThreads;
 }
 
 
