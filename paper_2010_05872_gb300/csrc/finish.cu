@@ -193,8 +193,7 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
       per_sm = std::max(per_sm, 1);
       const int npairs = (mv.ax[0].n + 1) / 2;
-      g.t0 = march_chunk(npairs, g.nb1 * g.nb2, 152 * per_sm, 4, 1,
-                         nf_all * sizeof(T) <= kL2ResidentBytes);
+      g.t0 = march_chunk(npairs, g.nb1 * g.nb2, 152 * per_sm, 1);
       g.nb0 = (npairs + g.t0 - 1) / g.t0;
       launch_pdl(kernel, dim3(static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2)), dim3(g.threads), smem,
                  s, mv, nodal_src, interp_src, sign, fine, g, status);

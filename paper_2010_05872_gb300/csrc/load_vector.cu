@@ -101,12 +101,10 @@ cudaError_t launch_march_shape(const LevelK<T>& lv, bool dec, const T* fine, T* 
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
   per_sm = std::max(per_sm, 1);
-  // Coarse planes per CTA: whole waves over the 152 SMs with at least 8
-  // planes per CTA (the 3 halo planes stay a small overhead), or, for a level
-  // that stays in L2, the shortest longest march (a CTA marches 2 t0 + 3
-  // fine planes).
+  // Coarse planes per CTA: the shortest longest march over the waves (a CTA
+  // marches 2 t0 + 3 fine planes).
   const uint64_t count = uint64_t(lv.ax[0].n) * lv.ax[1].n * lv.ax[2].n;
-  g.t0 = march_chunk(c0, g.nb2 * g.nb1, 152 * per_sm, 8, 2, l2_resident(lv));
+  g.t0 = march_chunk(c0, g.nb2 * g.nb1, 152 * per_sm, 2);
   g.nb0 = (c0 + g.t0 - 1) / g.t0;
   const unsigned grid = static_cast<unsigned>(g.nb0 * g.nb1 * g.nb2);
   launch_pdl(kernel, dim3(grid), dim3(g.threads), smem, s, lv, fine, coarse, F, g, count, status);
