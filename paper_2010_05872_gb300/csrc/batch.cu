@@ -81,7 +81,7 @@ struct BatchStage {
 constexpr int kBatchThreads = 288;
 constexpr int kLvNS = 4, kLvT1 = 4;  // the batched tiles keep their own shape
 constexpr int kLvGMax = 8;           // row groups of a load-vector tile (narrow fields)
-constexpr int kFinNS = 4, kFinT1 = FinishCfg<float>::T1;
+constexpr int kFinNS = 4, kFinT1 = 4;  // as the load-vector tiles, a shape of their own
 constexpr int kFinGMax = 8;          // row groups of a finish tile (narrow fields)
 
 __global__ void __launch_bounds__(kBatchThreads, 2)

@@ -29,13 +29,14 @@ template <typename T>
 struct MarchCfg;
 template <>
 struct MarchCfg<float> {
-  // Levels larger than L2: measured at 513^3 on GB300, (NS, T1) in {2, 3, 4}
-  // x {2, 4, 6, 8}, two plane buffers of 2 T1 + 3 = 15 rows gave the shortest
-  // finest-level launch.  Levels that stay in L2 march a few planes per CTA,
-  // so their shape favours planes in flight (NS_L2, T1_L2).  Two coarse
-  // columns per thread (CPT) beat one at 257^3 as well (41 against 43-64 us
-  // over six shapes).
-  static constexpr int NS = 2, T1 = 6, CPT = 2;
+  // Levels larger than L2: measured at 513^3 on GB300 with one wave of
+  // 26-plane marches, (NS, T1) in {(2, 4), (2, 6), (2, 8), (3, 4), (3, 6),
+  // (4, 4)}, two plane buffers of 2 T1 + 3 = 11 rows gave the shortest
+  // finest-level launch (176 us; 182 with T1 = 6).  Levels that stay in L2
+  // march a few planes per CTA, so their shape favours planes in flight
+  // (NS_L2, T1_L2).  Two coarse columns per thread (CPT) beat one at 257^3
+  // as well (41 against 43-64 us over six shapes).
+  static constexpr int NS = 2, T1 = 4, CPT = 2;
   static constexpr int NS_L2 = 3, T1_L2 = 4, CPT_L2 = 2;
 };
 template <>
