@@ -310,12 +310,14 @@ dequantize_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
 }
 
 // Flat forms for aligned arrays: a thread takes vectors of 4 consecutive
-// elements (16-byte loads and stores), kQU vectors in flight, over a
-// persistent grid.  The row of element e is umulhi(e, M) with
+// elements (16-byte loads and stores), QU vectors in flight, over a
+// persistent grid of TH-thread blocks.  Shapes measured at 513^3 FP32 on
+// GB300 over QU x TH in {1, 2, 3, 4, 8} x {128, 256, 512, 1024}: quantize
+// 3 x 512 (258 us, 0.92 of the copy peak), dequantize 1 x 1024 (265 us).  The row of element e is umulhi(e, M) with
 // M = ceil(2^64 / n2), exact for every e of the array (checked on the host);
 // the 4 elements of a vector span at most two rows (n2 >= 4).
-constexpr int kQU = 4;
-constexpr int kQThreads = 256;
+constexpr int kQUq = 3, kQThreadsQ = 512;    // quantize
+constexpr int kQUd = 1, kQThreadsD = 1024;   // dequantize
 
 __device__ __forceinline__ void vec_levels(uint64_t e, uint64_t magic, uint32_t n2,
                                            const uint8_t* __restrict__ lev01,
@@ -334,7 +336,7 @@ __device__ __forceinline__ void vec_levels(uint64_t e, uint64_t magic, uint32_t 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kQThreads)
+__global__ void __launch_bounds__(kQThreadsQ)
 quantize_flat_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
                      const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
                      uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab,
@@ -343,18 +345,19 @@ quantize_flat_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
   __shared__ SmemTable st;
   load_table(tab, st);
   unsigned bad = 0;
-  const uint64_t step = static_cast<uint64_t>(gridDim.x) * kQThreads * kQU;
-  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kQThreads * kQU + threadIdx.x;
+  constexpr int QU = kQUq, TH = kQThreadsQ;
+  const uint64_t step = static_cast<uint64_t>(gridDim.x) * TH * QU;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * TH * QU + threadIdx.x;
        base < nvec; base += step) {
-    T x[kQU][4];
+    T x[QU][4];
 #pragma unroll
-    for (int u = 0; u < kQU; ++u) {
-      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+    for (int u = 0; u < QU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * TH;
       if (v < nvec) Vec4<T>::load(coeffs + 4 * v, x[u]);
     }
 #pragma unroll
-    for (int u = 0; u < kQU; ++u) {
-      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+    for (int u = 0; u < QU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * TH;
       if (v < nvec) {
         int lv[4];
         vec_levels(4 * v, magic, n2, lev01, lev2, stop, lv);
@@ -371,20 +374,21 @@ quantize_flat_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kQThreads)
+__global__ void __launch_bounds__(kQThreadsD)
 dequantize_flat_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
                        const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
                        uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab) {
   grid_dep_enter();
   __shared__ SmemTable st;
   load_table(tab, st);
-  const uint64_t step = static_cast<uint64_t>(gridDim.x) * kQThreads * kQU;
-  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kQThreads * kQU + threadIdx.x;
+  constexpr int QU = kQUd, TH = kQThreadsD;
+  const uint64_t step = static_cast<uint64_t>(gridDim.x) * TH * QU;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * TH * QU + threadIdx.x;
        base < nvec; base += step) {
-    longlong2 k[kQU][2];
+    longlong2 k[QU][2];
 #pragma unroll
-    for (int u = 0; u < kQU; ++u) {
-      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+    for (int u = 0; u < QU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * TH;
       if (v < nvec) {
         const longlong2* in = reinterpret_cast<const longlong2*>(labels + 4 * v);
         k[u][0] = in[0];
@@ -392,8 +396,8 @@ dequantize_flat_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeff
       }
     }
 #pragma unroll
-    for (int u = 0; u < kQU; ++u) {
-      const uint64_t v = base + static_cast<uint64_t>(u) * kQThreads;
+    for (int u = 0; u < QU; ++u) {
+      const uint64_t v = base + static_cast<uint64_t>(u) * TH;
       if (v < nvec) {
         int lv[4];
         vec_levels(4 * v, magic, n2, lev01, lev2, stop, lv);
@@ -420,6 +424,12 @@ struct Lim<float> { static __device__ __forceinline__ float max() { return FLT_M
 template <>
 struct Lim<double> { static __device__ __forceinline__ double max() { return DBL_MAX; } };
 
+// Value range: a grid of kRangeBlocks x kThreads threads, kRangeLoads
+// 16-byte loads in flight per thread (measured at 513^3 FP32 on GB300 over
+// {2, 4, 8} loads x {608, 1216, 2432} blocks: 8 x 608, 91 us).
+constexpr int kRangeLoads = 8;
+constexpr int kRangeBlocks = 608;
+
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 minmax_partial_kernel(const T* __restrict__ data, uint64_t count, double* __restrict__ partial,
@@ -432,15 +442,15 @@ minmax_partial_kernel(const T* __restrict__ data, uint64_t count, double* __rest
   const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   uint64_t done = 0;
   if (VEC) {
-    // Four 16-byte loads of a thread in flight at a time.
+    // kRangeLoads 16-byte loads of a thread in flight at a time.
     const uint64_t ngroups = count / 4;
     uint64_t g = tid;
-    for (; g + 3 * stride < ngroups; g += 4 * stride) {
-      T v[4][4];
+    for (; g + (kRangeLoads - 1) * stride < ngroups; g += kRangeLoads * stride) {
+      T v[kRangeLoads][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) Vec4<T>::load(data + (g + i * stride) * 4, v[i]);
+      for (int i = 0; i < kRangeLoads; ++i) Vec4<T>::load(data + (g + i * stride) * 4, v[i]);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < kRangeLoads; ++i)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           bad |= !finite_val(v[i][u]);
@@ -539,10 +549,10 @@ bool flat_magic(uint64_t count, int64_t n2, uint64_t& magic) {
 }
 
 template <typename K>
-unsigned flat_blocks(K kernel, uint64_t nvec) {
+unsigned flat_blocks(K kernel, uint64_t nvec, int threads, int qu) {
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kQThreads, 0);
-  const uint64_t need = (nvec + uint64_t(kQThreads) * kQU - 1) / (uint64_t(kQThreads) * kQU);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  const uint64_t need = (nvec + uint64_t(threads) * qu - 1) / (uint64_t(threads) * qu);
   const uint64_t cap = 152ull * static_cast<uint64_t>(std::max(per_sm, 1));
   return static_cast<unsigned>(std::max<uint64_t>(1, std::min(need, cap)));
 }
@@ -562,8 +572,9 @@ cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev
   if (aligned16(coeffs) && aligned16(labels) && flat_magic(count, n2, magic)) {
     const uint64_t nvec = count / 4;
     if (nvec > 0)
-      launch_pdl(quantize_flat_kernel<T>, dim3(flat_blocks(quantize_flat_kernel<T>, nvec)),
-                 dim3(kQThreads), 0, s, coeffs, labels, lev01, lev2, nvec,
+      launch_pdl(quantize_flat_kernel<T>,
+                 dim3(flat_blocks(quantize_flat_kernel<T>, nvec, kQThreadsQ, kQUq)),
+                 dim3(kQThreadsQ), 0, s, coeffs, labels, lev01, lev2, nvec,
                  static_cast<uint32_t>(n2), magic, stop_level, tab, flags);
     if (count % 4 == 0) return cudaGetLastError();
     // The last count % 4 elements: one row-tile pass over the last row
@@ -590,8 +601,9 @@ cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* l
   if (aligned16(coeffs) && aligned16(labels) && flat_magic(count, n2, magic)) {
     const uint64_t nvec = count / 4;
     if (nvec > 0)
-      launch_pdl(dequantize_flat_kernel<T>, dim3(flat_blocks(dequantize_flat_kernel<T>, nvec)),
-                 dim3(kQThreads), 0, s, labels, coeffs, lev01, lev2, nvec,
+      launch_pdl(dequantize_flat_kernel<T>,
+                 dim3(flat_blocks(dequantize_flat_kernel<T>, nvec, kQThreadsD, kQUd)),
+                 dim3(kQThreadsD), 0, s, labels, coeffs, lev01, lev2, nvec,
                  static_cast<uint32_t>(n2), magic, stop_level, tab);
     if (count % 4 == 0) return cudaGetLastError();
     const int64_t r_last = rows - 1;
@@ -610,7 +622,7 @@ template <typename T>
 cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigned int* flags,
                           double* result, cudaStream_t s) {
   int64_t blocks = (count / 4 + kThreads - 1) / kThreads;
-  if (blocks > kMinmaxBlocks) blocks = kMinmaxBlocks;
+  if (blocks > kRangeBlocks) blocks = kRangeBlocks;
   if (blocks < 1) blocks = 1;
   TraceScope ts(kKMinmax, -1, double(count) * sizeof(T), s);
   if (aligned16(data))
