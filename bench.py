@@ -367,7 +367,9 @@ def run_gpu(args, rank, world, local_rank):
         B.decompose(buf, None, 0, ws)
         if ev:
             ev[2].record(stream)
-        B.quantize(buf, tau, None, 0, labels)
+        # The labels' flags are read once per batch of steps (quantize_status
+        # after each loop below) instead of the stream waiting on every step.
+        B.quantize_async(buf, tau, None, 0, labels)
         if ev:
             ev[3].record(stream)
         B.dequantize(labels, tau, buf.dtype, None, 0, out=buf)
@@ -383,6 +385,7 @@ def run_gpu(args, rank, world, local_rank):
     for rel in BOUNDS:
         x.copy_(u)
         tau = step(x, rel)
+        B.quantize_status()
         err = (x.double() - u.double()).abs().max().item()
         linf[f"{rel:g}"] = err / tau
         assert err <= tau, (rel, err, tau)
@@ -418,6 +421,7 @@ def run_gpu(args, rank, world, local_rank):
     for i in range(args.warmup):
         step(x, BOUNDS[i % 4])
     torch.cuda.synchronize()
+    B.quantize_status()
 
     # Per-kernel breakdown, outside the timed region: every launch bracketed
     # by trace events (they cost about 2 us of device time per launch, which
@@ -428,6 +432,7 @@ def run_gpu(args, rank, world, local_rank):
     for i in range(kb):
         step(x, BOUNDS[i % 4])
     torch.cuda.synchronize()
+    B.quantize_status()
     B.mgard_trace_enable(False)
     trace = B.mgard_trace_read()
     # Phase split, also outside the timed region: six events per step, no trace.
@@ -435,6 +440,7 @@ def run_gpu(args, rank, world, local_rank):
     for i in range(kb):
         step(x, BOUNDS[i % 4], evs[i])
     torch.cuda.synchronize()
+    B.quantize_status()
     phase = {k: 0.0 for k in ("range", "decompose", "quantize", "dequantize", "recompose")}
     for e in evs:
         for j, k in enumerate(phase):
@@ -461,6 +467,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
+    B.quantize_status()
     B.mgard_trace_enable(False)
     launches = B.mgard_trace_kernel_launches()
     timed_top = [r for r in B.mgard_trace_read()
@@ -538,10 +545,12 @@ def run_gpu(args, rank, world, local_rank):
     for i in range(k64):
         step(x64, BOUNDS[i % 4], ev64[i])
     torch.cuda.synchronize()
+    B.quantize_status()
     ph64 = {k: sum(e[j].elapsed_time(e[j + 1]) for e in ev64) for j, k in enumerate(phase)}
     t64 = sum(ph64.values()) / k64
     x64.copy_(u64)
     tau64 = step(x64, 1e-3)
+    B.quantize_status()
     # The FP64 path against both roofs: HBM on its own bytes (8 B per value)
     # and the measured FP64 FMA rate on the path's algorithmic flops.
     dr64 = (ph64["decompose"] + ph64["recompose"]) / k64

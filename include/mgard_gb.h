@@ -27,7 +27,8 @@
  *    nodes.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
  *    enqueued on it and the calls return without waiting, except
- *    mgard_quantize and mgard_value_range, which wait for their own flags.
+ *    mgard_quantize and mgard_value_range, which wait for their own flags,
+ *    and mgard_quantize_status, which waits to read them.
  *  - The first call for a given (device, dims, coords, dtype) builds a plan
  *    (host FP64 tables, uploaded once with cudaMalloc/cudaMemcpy) and caches
  *    it until mgard_release_plans().  Make that first call outside any CUDA
@@ -193,6 +194,23 @@ int mgard_recompose(int ndim, const int64_t* dims, const double* const* coords, 
 int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, int dtype,
                    int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
                    double* tau_levels_out, void* stream);
+
+/* mgard_quantize without its wait (Section 4.1, the same labels): the call
+ * enqueues the quantization on `stream` and returns; whether a coefficient
+ * was not finite or a label would reach 2^62 is gathered in a word of the
+ * device's context over every such call on the device (all streams) until
+ * mgard_quantize_status reads it.  For a pipeline that checks once per
+ * batch of work instead of once per call. */
+int mgard_quantize_async(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
+                         double* tau_levels_out, void* stream);
+
+/* Waits for `stream`, then reports and clears what the asynchronous
+ * quantizations since the last call gathered: MGARD_ERR_NONFINITE,
+ * MGARD_ERR_OVERFLOW, or MGARD_ERR_TIMEOUT if a bounded device wait gave up
+ * meanwhile; MGARD_OK otherwise.  The stream must be one that follows all of
+ * those quantizations (the flags are read on it). */
+int mgard_quantize_status(void* stream);
 
 /* Bin centres: coeffs[x] = labels[x] * (2 tau_l), computed in FP64 and
  * rounded to dtype (Section 4.1).  Arguments as for mgard_quantize. */

@@ -76,6 +76,9 @@ _SIGNATURES = {
                                                 ctypes.POINTER(ctypes.c_double), _VP]),
     "mgard_quantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, _VP, _VP, _DP, _VP]),
+    "mgard_quantize_async": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, _VP, _VP, _DP, _VP]),
+    "mgard_quantize_status": (ctypes.c_int, [ctypes.c_void_p]),
     "mgard_dequantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, _VP, _VP, _VP]),
     "mgard_value_range": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _VP, _DP, _VP]),
@@ -841,6 +844,28 @@ def quantize(coeffs, tau: float, coords=None, stop_level: int = 0, labels=None, 
                               coeffs.data_ptr(), labels.data_ptr(), _stream(stream))
     _check(rc, "mgard_quantize")
     return labels, taus
+
+
+def quantize_async(coeffs, tau: float, coords=None, stop_level: int = 0, labels=None, stream=None):
+    """quantize without waiting: the labels are enqueued on the stream and
+    their flags gathered until quantize_status."""
+    torch = _torch()
+    _cuda_tensor(coeffs, "coeffs")
+    if labels is None:
+        labels = torch.empty(coeffs.shape, dtype=torch.int64, device=coeffs.device)
+    s = _Shape(coeffs.shape, coords)
+    taus = np.zeros(mgard_num_levels(coeffs.shape) + 1)
+    rc = lib().mgard_quantize_async(s.ndim, s.dims, s.coords, dtype_code(coeffs), int(stop_level),
+                                    float(tau), coeffs.data_ptr(), labels.data_ptr(),
+                                    taus.ctypes.data_as(_DP), _stream(stream))
+    _check(rc, "mgard_quantize_async")
+    return labels, taus
+
+
+def quantize_status(stream=None):
+    """Wait for the stream and raise if any asynchronous quantization since
+    the last check met a non-finite coefficient, an overflow or a timeout."""
+    _check(lib().mgard_quantize_status(_stream(stream)), "mgard_quantize_status")
 
 
 def dequantize(labels, tau: float, dtype, coords=None, stop_level: int = 0, out=None, stream=None):

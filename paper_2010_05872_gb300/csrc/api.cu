@@ -934,6 +934,49 @@ int mgard_quantize(int ndim, const int64_t* dims, const double* const* coords, i
   return quantize_table(*p, dtype, stop_level, tab, coeffs, labels, stream);
 }
 
+int mgard_quantize_async(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, double tau_linf, const void* coeffs, int64_t* labels,
+                         double* tau_levels_out, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_q_args(dtype, coeffs, labels);
+  if (rc != MGARD_OK) return rc;
+  LevelTable tab;
+  rc = make_table(*p, stop_level, tau_linf, tab, tau_levels_out);
+  if (rc != MGARD_OK) return rc;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned int* flags = c->flags + 2;  // gathered until mgard_quantize_status
+  const auto& d = p->h.dims3;
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p->lev01,
+                                    p->lev[2], d[0] * d[1], d[2], stop_level, tab, flags, s));
+  else
+    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p->lev01, p->lev[2],
+                                   d[0] * d[1], d[2], stop_level, tab, flags, s));
+  return MGARD_OK;
+}
+
+int mgard_quantize_status(void* stream) {
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaStreamSynchronize(s));
+  const unsigned f = c->h_flags[2], t = c->h_flags[1];
+  if (f) MGB_TRY(cudaMemsetAsync(c->flags + 2, 0, sizeof(unsigned), s));
+  if (t) {
+    MGB_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(unsigned), s));
+    return MGARD_ERR_TIMEOUT;
+  }
+  if (f & 1u) return MGARD_ERR_NONFINITE;
+  if (f & 2u) return MGARD_ERR_OVERFLOW;
+  return MGARD_OK;
+}
+
 int mgard_quantize_levels(int ndim, const int64_t* dims, const double* const* coords, int dtype,
                           int stop_level, const double* tau_levels, const void* coeffs,
                           int64_t* labels, void* stream) {

@@ -180,6 +180,36 @@ def test_device_errors(cuda):
     assert e.value.code == -6
 
 
+def test_quantize_async_defers_its_checks(cuda):
+    """mgard_quantize_async writes the labels of mgard_quantize and leaves
+    its flags to mgard_quantize_status, which reports the first problem of
+    every call since the last check and then clears it."""
+    torch = cuda
+    dims = (65, 33, 47)
+    x = torch.from_numpy(F.grf_field(dims, seed=17)).cuda()
+    B.quantize_status()  # start from a clear word
+    want, taus = B.quantize(x, 1e-3)
+    got, taus_a = B.quantize_async(x, 1e-3)
+    B.quantize_status()
+    assert torch.equal(got, want)
+    assert np.array_equal(taus, taus_a)
+    # A non-finite coefficient: the call returns, the check reports it once.
+    y = x.clone()
+    y[3, 4, 5] = float("nan")
+    B.quantize_async(y, 1e-3)
+    B.quantize_async(x, 1e-3)  # a later clean call does not hide it
+    with pytest.raises(B.MgardError) as e:
+        B.quantize_status()
+    assert e.value.code == -7
+    B.quantize_status()  # cleared
+    big = torch.full(dims, 1e30, device="cuda")
+    B.quantize_async(big, 1e-3)
+    with pytest.raises(B.MgardError) as e:
+        B.quantize_status()
+    assert e.value.code == -6
+    B.quantize_status()
+
+
 def test_host_buffer_entry_points(cuda):
     torch = cuda
     dims = (65, 65, 65)
