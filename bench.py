@@ -357,28 +357,32 @@ def run_gpu(args, rank, world, local_rank):
     ws = B.workspace(DIMS, torch.float32, dev)
     labels = torch.empty(DIMS, dtype=torch.int64, device=dev)
 
+    # A step waits on nothing: the range stays on the device, where the
+    # quantizer forms tau = rel x (max - min) and its level tolerances (the
+    # same values as the host's), and the labels' flags are read once per
+    # batch of steps (quantize_status after each loop below).
+    rng = torch.empty(2, dtype=torch.float64, device=dev)
+    lo_u, hi_u = B.value_range(u)
+
     def step(buf, rel, ev=None):
         if ev:
             ev[0].record(stream)
-        lo, hi = B.value_range(buf)
-        tau = rel * (hi - lo)
+        B.value_range_async(buf, rng)
         if ev:
             ev[1].record(stream)
         B.decompose(buf, None, 0, ws)
         if ev:
             ev[2].record(stream)
-        # The labels' flags are read once per batch of steps (quantize_status
-        # after each loop below) instead of the stream waiting on every step.
-        B.quantize_async(buf, tau, None, 0, labels)
+        B.quantize_rel_async(buf, rel, rng, None, 0, labels)
         if ev:
             ev[3].record(stream)
-        B.dequantize(labels, tau, buf.dtype, None, 0, out=buf)
+        B.dequantize_rel(labels, rel, rng, buf.dtype, None, 0, out=buf)
         if ev:
             ev[4].record(stream)
         B.recompose(buf, None, 0, ws)
         if ev:
             ev[5].record(stream)
-        return tau
+        return rel * (hi_u - lo_u)  # the tau the device formed (the input's range)
 
     # Correctness of the timed configuration: L-inf error per bound.
     linf = {}

@@ -207,8 +207,9 @@ int mgard_quantize_async(int ndim, const int64_t* dims, const double* const* coo
 
 /* Waits for `stream`, then reports and clears what the asynchronous
  * quantizations since the last call gathered: MGARD_ERR_NONFINITE,
- * MGARD_ERR_OVERFLOW, or MGARD_ERR_TIMEOUT if a bounded device wait gave up
- * meanwhile; MGARD_OK otherwise.  The stream must be one that follows all of
+ * MGARD_ERR_OVERFLOW, MGARD_ERR_ARG (a level tolerance formed on the device
+ * was not positive and finite), or MGARD_ERR_TIMEOUT if a bounded device
+ * wait gave up meanwhile; MGARD_OK otherwise.  The stream must be one that follows all of
  * those quantizations (the flags are read on it). */
 int mgard_quantize_status(void* stream);
 
@@ -224,6 +225,30 @@ int mgard_dequantize(int ndim, const int64_t* dims, const double* const* coords,
  * the stream; MGARD_ERR_NONFINITE if an element is NaN or Inf. */
 int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax_out,
                       void* stream);
+
+/* A relative error bound carried through on the device (Section 4.1, Eq.
+ * LinfTau with tau = rel_bound x (max - min)), so a pipeline of range,
+ * decomposition, quantization, dequantization and recomposition needs no
+ * wait.  mgard_value_range_async writes min and max of the array to
+ * `range` (device, two doubles, 8-byte aligned) and gathers a NaN / Inf
+ * element as mgard_quantize_async does (MGARD_ERR_NONFINITE from
+ * mgard_quantize_status).  mgard_quantize_rel_async and
+ * mgard_dequantize_rel are mgard_quantize_async and mgard_dequantize with
+ * tau read from `range` on the device: every CTA forms the level
+ * tolerances itself with the host's operations in the host's order, so the
+ * labels and values equal those of the host calls given tau = rel_bound x
+ * (max - min) computed in FP64.  A tau that is not positive and finite
+ * (e.g. a constant array) is reported by mgard_quantize_status as
+ * MGARD_ERR_ARG.  The range's partial sums use a per-device buffer: range
+ * calls on different streams must not overlap. */
+int mgard_value_range_async(int64_t count, int dtype, const void* data, double* range,
+                            void* stream);
+int mgard_quantize_rel_async(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                             int stop_level, double rel_bound, const double* range,
+                             const void* coeffs, int64_t* labels, void* stream);
+int mgard_dequantize_rel(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, double rel_bound, const double* range,
+                         const int64_t* labels, void* coeffs, void* stream);
 
 /* Host-buffer forms of decompose / recompose: copy `host_in` (pinned or
  * pageable host memory, the field's element count of dtype) to the device

@@ -79,6 +79,11 @@ _SIGNATURES = {
     "mgard_quantize_async": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, _VP, _VP, _DP, _VP]),
     "mgard_quantize_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "mgard_value_range_async": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _VP, _VP, _VP]),
+    "mgard_quantize_rel_async": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_double, _VP, _VP, _VP, _VP]),
+    "mgard_dequantize_rel": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, _VP, _VP, _VP, _VP]),
     "mgard_dequantize": (ctypes.c_int, [ctypes.c_int, _I64P, _DPP, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, _VP, _VP, _VP]),
     "mgard_value_range": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _VP, _DP, _VP]),
@@ -866,6 +871,48 @@ def quantize_status(stream=None):
     """Wait for the stream and raise if any asynchronous quantization since
     the last check met a non-finite coefficient, an overflow or a timeout."""
     _check(lib().mgard_quantize_status(_stream(stream)), "mgard_quantize_status")
+
+
+def value_range_async(x, range_out=None, stream=None):
+    """min and max of a CUDA tensor into a device float64 tensor of 2, without waiting."""
+    torch = _torch()
+    _cuda_tensor(x, "x")
+    if range_out is None:
+        range_out = torch.empty(2, dtype=torch.float64, device=x.device)
+    rc = lib().mgard_value_range_async(x.numel(), dtype_code(x), x.data_ptr(),
+                                       range_out.data_ptr(), _stream(stream))
+    _check(rc, "mgard_value_range_async")
+    return range_out
+
+
+def quantize_rel_async(coeffs, rel: float, range_dev, coords=None, stop_level: int = 0,
+                       labels=None, stream=None):
+    """Labels with tau = rel x (max - min) of the device range, without waiting."""
+    torch = _torch()
+    _cuda_tensor(coeffs, "coeffs")
+    if labels is None:
+        labels = torch.empty(coeffs.shape, dtype=torch.int64, device=coeffs.device)
+    s = _Shape(coeffs.shape, coords)
+    rc = lib().mgard_quantize_rel_async(s.ndim, s.dims, s.coords, dtype_code(coeffs),
+                                        int(stop_level), float(rel), range_dev.data_ptr(),
+                                        coeffs.data_ptr(), labels.data_ptr(), _stream(stream))
+    _check(rc, "mgard_quantize_rel_async")
+    return labels
+
+
+def dequantize_rel(labels, rel: float, range_dev, dtype, coords=None, stop_level: int = 0,
+                   out=None, stream=None):
+    """Bin centres with tau = rel x (max - min) of the device range."""
+    torch = _torch()
+    _cuda_tensor(labels, "labels")
+    if out is None:
+        out = torch.empty(labels.shape, dtype=dtype, device=labels.device)
+    s = _Shape(labels.shape, coords)
+    rc = lib().mgard_dequantize_rel(s.ndim, s.dims, s.coords, dtype_code(out), int(stop_level),
+                                    float(rel), range_dev.data_ptr(), labels.data_ptr(),
+                                    out.data_ptr(), _stream(stream))
+    _check(rc, "mgard_dequantize_rel")
+    return out
 
 
 def dequantize(labels, tau: float, dtype, coords=None, stop_level: int = 0, out=None, stream=None):

@@ -973,6 +973,7 @@ int mgard_quantize_status(void* stream) {
     return MGARD_ERR_TIMEOUT;
   }
   if (f & 1u) return MGARD_ERR_NONFINITE;
+  if (f & 4u) return MGARD_ERR_ARG;
   if (f & 2u) return MGARD_ERR_OVERFLOW;
   return MGARD_OK;
 }
@@ -1052,6 +1053,91 @@ int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax
   minmax_out[0] = c->h_result[0];
   minmax_out[1] = c->h_result[1];
   return MGARD_OK;
+}
+
+int mgard_value_range_async(int64_t count, int dtype, const void* data, double* range,
+                            void* stream) {
+  if (count < 1 || data == nullptr || range == nullptr) return MGARD_ERR_ARG;
+  if (dtype != MGARD_F32 && dtype != MGARD_F64) return MGARD_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(data) % elem_size(dtype)) return MGARD_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(range) % sizeof(double)) return MGARD_ERR_ARG;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned int* flags = c->flags + 2;  // gathered until mgard_quantize_status
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_minmax<double>(static_cast<const double*>(data), count, c->partial, flags, range, s));
+  else
+    MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, c->partial, flags, range, s));
+  return MGARD_OK;
+}
+
+namespace {
+// The device-range form of the level tolerances for a plan and stopping level.
+int rel_tol(const DevPlan& p, int stop_level, double rel_bound, const double* range,
+            unsigned int* flags, RelTol& rt) {
+  if (stop_level < 0 || stop_level > p.h.L) return MGARD_ERR_LEVEL;
+  if (!(rel_bound > 0.0) || !std::isfinite(rel_bound)) return MGARD_ERR_ARG;
+  if (range == nullptr || reinterpret_cast<uintptr_t>(range) % sizeof(double)) return MGARD_ERR_ARG;
+  rt = RelTol{};
+  rt.range = range;
+  rt.rel = rel_bound;
+  rt.L = p.h.L;
+  rt.stop = stop_level;
+  rt.flags = flags;
+  level_tolerance_terms(p.h, stop_level, &rt.C, &rt.kappa, &rt.kpow);
+  return MGARD_OK;
+}
+}  // namespace
+
+int mgard_quantize_rel_async(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                             int stop_level, double rel_bound, const double* range,
+                             const void* coeffs, int64_t* labels, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_q_args(dtype, coeffs, labels);
+  if (rc != MGARD_OK) return rc;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  RelTol rt;
+  rc = rel_tol(*p, stop_level, rel_bound, range, c->flags + 2, rt);
+  if (rc != MGARD_OK) return rc;
+  const LevelTable tab{};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto& d = p->h.dims3;
+  if (dtype == MGARD_F64)
+    MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p->lev01,
+                                    p->lev[2], d[0] * d[1], d[2], stop_level, tab, c->flags + 2, s,
+                                    &rt));
+  else
+    MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p->lev01, p->lev[2],
+                                   d[0] * d[1], d[2], stop_level, tab, c->flags + 2, s, &rt));
+  return MGARD_OK;
+}
+
+int mgard_dequantize_rel(int ndim, const int64_t* dims, const double* const* coords, int dtype,
+                         int stop_level, double rel_bound, const double* range,
+                         const int64_t* labels, void* coeffs, void* stream) {
+  DevPlan* p = nullptr;
+  int rc = get_plan(ndim, dims, coords, dtype, &p);
+  if (rc != MGARD_OK) return rc;
+  rc = check_q_args(dtype, coeffs, labels);
+  if (rc != MGARD_OK) return rc;
+  DevCtx* c = get_ctx();
+  if (c == nullptr) return MGARD_ERR_CUDA;
+  RelTol rt;
+  rc = rel_tol(*p, stop_level, rel_bound, range, c->flags + 2, rt);
+  if (rc != MGARD_OK) return rc;
+  const LevelTable tab{};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto& d = p->h.dims3;
+  if (dtype == MGARD_F64)
+    return cuda_rc(launch_dequantize<double>(labels, static_cast<double*>(coeffs), p->lev01,
+                                             p->lev[2], d[0] * d[1], d[2], stop_level, tab, s,
+                                             &rt));
+  return cuda_rc(launch_dequantize<float>(labels, static_cast<float*>(coeffs), p->lev01, p->lev[2],
+                                          d[0] * d[1], d[2], stop_level, tab, s, &rt));
 }
 
 int mgard_compress_host(int ndim, const int64_t* dims, const double* const* coords, int dtype,

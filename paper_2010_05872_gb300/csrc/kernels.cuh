@@ -98,14 +98,26 @@ struct LevelTable {
   float qf[48];   // fl32(q_l)
   float dqf[48];  // fl32(q_l - fl32(q_l))
 };
+// Level tolerances formed on the device (Eq. LinfTau) from a range that
+// stays there: tau = rel (max - min), t0 = (1 - kappa) tau / ((1 - kpow) C)
+// and t_l = kappa t_{l-1} above the stopping level, the host's operations
+// in the host's order (IEEE FP64, no contraction), so the table equals the
+// one the host builds from the same tau.
+struct RelTol {
+  const double* range;   // device [min, max]; NULL: the kernels use the host table
+  double rel, C, kappa, kpow;
+  int L, stop;
+  unsigned int* flags;   // receives 4 if tau is not positive and finite
+};
 template <typename T>
 cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev01,
                             const uint8_t* lev2, int64_t rows, int64_t n2, int stop_level,
-                            const LevelTable& tab, unsigned int* flags, cudaStream_t s);
+                            const LevelTable& tab, unsigned int* flags, cudaStream_t s,
+                            const RelTol* rt = nullptr);
 template <typename T>
 cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* lev01,
                               const uint8_t* lev2, int64_t rows, int64_t n2, int stop_level,
-                              const LevelTable& tab, cudaStream_t s);
+                              const LevelTable& tab, cudaStream_t s, const RelTol* rt = nullptr);
 template <typename T>
 cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigned int* flags,
                           double* result, cudaStream_t s);

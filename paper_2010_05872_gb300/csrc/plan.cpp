@@ -351,11 +351,18 @@ void level_tolerances_mode(const HostPlan& p, int stop_level, double tau, int mo
   for (int l = 0; l < stop_level; ++l) out[l] = out[stop_level];
 }
 
+void level_tolerance_terms(const HostPlan& p, int stop_level, double* C, double* kappa,
+                           double* kpow) {
+  *C = linf_constant(p, stop_level);
+  *kappa = std::sqrt(std::pow(2.0, p.ndim));
+  double kp = 1.0;
+  for (int i = 0; i < p.L + 1 - stop_level; ++i) kp *= *kappa;
+  *kpow = kp;
+}
+
 void level_tolerances(const HostPlan& p, int stop_level, double tau, double* out) {
-  const double C = linf_constant(p, stop_level);
-  const double kappa = std::sqrt(std::pow(2.0, p.ndim));
-  double kpow = 1.0;
-  for (int i = 0; i < p.L + 1 - stop_level; ++i) kpow *= kappa;
+  double C, kappa, kpow;
+  level_tolerance_terms(p, stop_level, &C, &kappa, &kpow);
   const double t0 = (1.0 - kappa) * tau / ((1.0 - kpow) * C);
   for (int l = 0; l <= stop_level; ++l) out[l] = t0;
   for (int l = stop_level + 1; l <= p.L; ++l) out[l] = kappa * out[l - 1];

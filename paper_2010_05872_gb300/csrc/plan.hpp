@@ -69,6 +69,12 @@ void release_plans4(int device);
 
 // tau_out receives L+1 values (entries below stop_level repeat tau_{stop}).
 void level_tolerances(const HostPlan& p, int stop_level, double tau, double* tau_out);
+// The terms of level_tolerances: C_Linf, kappa = 2^(d/2) and
+// kappa^(L + 1 - stop_level); tau_l = (1 - kappa) tau / ((1 - kpow) C) x
+// kappa^(l - stop_level) for l above the stopping level.
+void level_tolerance_terms(const HostPlan& p, int stop_level, double* C, double* kappa,
+                           double* kpow);
+
 // mode 0: the geometric rule above; 1: L-inf-optimal widths (tau_l
 // proportional to the level's new nodes, sum tau / C_Linf); 2: tau is an L2
 // bound, tau_l = tau / sqrt(h_l^d #N_L) (Section 4.1).

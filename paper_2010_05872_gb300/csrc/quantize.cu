@@ -203,12 +203,41 @@ struct SmemTable {
   float dqf[48];
 };
 
-__device__ __forceinline__ void load_table(const LevelTable& tab, SmemTable& s) {
-  for (int i = threadIdx.x; i < 48; i += blockDim.x) {
-    s.q[i] = tab.q[i];
-    s.rq[i] = tab.rq[i];
-    s.qf[i] = tab.qf[i];
-    s.dqf[i] = tab.dqf[i];
+// The level table in shared memory: the host's, or (rt.range set) the same
+// table formed from the device range, one thread per level, with the
+// operations of the host's level_tolerances and make_level_table.
+__device__ __forceinline__ void load_table(const LevelTable& tab, const RelTol& rt, SmemTable& s) {
+  if (rt.range == nullptr) {
+    for (int i = threadIdx.x; i < 48; i += blockDim.x) {
+      s.q[i] = tab.q[i];
+      s.rq[i] = tab.rq[i];
+      s.qf[i] = tab.qf[i];
+      s.dqf[i] = tab.dqf[i];
+    }
+  } else if (threadIdx.x < 48) {
+    const int l = threadIdx.x;
+    const double tau = __dmul_rn(rt.rel, __dsub_rn(rt.range[1], rt.range[0]));
+    const double t0 = __ddiv_rn(__dmul_rn(__dsub_rn(1.0, rt.kappa), tau),
+                                __dmul_rn(__dsub_rn(1.0, rt.kpow), rt.C));
+    if (l == 0 && !(tau > 0.0 && isfinite(tau) && t0 > 0.0 && isfinite(t0)) && rt.flags)
+      atomicOr(rt.flags, 4u);
+    double q = 1.0;
+    float rq = __int_as_float(0x7fc00000), qf = 1.0f, dqf = 0.0f;
+    if (l <= rt.L) {
+      double t = t0;  // tau of level max(l, stop)
+      for (int k = rt.stop + 1; k <= l; ++k) t = __dmul_rn(rt.kappa, t);
+      q = __dmul_rn(2.0, t);
+      const float rf = __double2float_rn(__ddiv_rn(1.0, q));
+      rq = (isfinite(rf) && rf >= 1.17549435e-38f) ? rf : __int_as_float(0x7fc00000);
+      const float qf0 = __double2float_rn(q);
+      const bool qok = isfinite(qf0) && qf0 >= 1.17549435e-38f;
+      qf = qok ? qf0 : __int_as_float(0x7fc00000);
+      dqf = qok ? __double2float_rn(__dsub_rn(q, static_cast<double>(qf0))) : 0.0f;
+    }
+    s.q[l] = q;
+    s.rq[l] = rq;
+    s.qf[l] = qf;
+    s.dqf[l] = dqf;
   }
   __syncthreads();
 }
@@ -250,10 +279,11 @@ template <typename T>
 __global__ void __launch_bounds__(kQCols)
 quantize_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
                 const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2, int64_t n2,
-                int64_t nrows, int stop, LevelTable tab, unsigned int* __restrict__ flags) {
+                int64_t nrows, int stop, LevelTable tab, unsigned int* __restrict__ flags,
+                RelTol rt) {
   grid_dep_enter();
   __shared__ SmemTable st;
-  load_table(tab, st);
+  load_table(tab, rt, st);
   const int64_t ngroups = (nrows + kQRows - 1) / kQRows;
   const int64_t nchunks = (n2 + blockDim.x - 1) / blockDim.x;
   unsigned bad = 0;
@@ -282,10 +312,10 @@ template <typename T>
 __global__ void __launch_bounds__(kQCols)
 dequantize_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
                   const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2, int64_t n2,
-                  int64_t nrows, int stop, LevelTable tab) {
+                  int64_t nrows, int stop, LevelTable tab, RelTol rt) {
   grid_dep_enter();
   __shared__ SmemTable st;
-  load_table(tab, st);
+  load_table(tab, rt, st);
   const int64_t ngroups = (nrows + kQRows - 1) / kQRows;
   const int64_t nchunks = (n2 + blockDim.x - 1) / blockDim.x;
   for (int64_t b = blockIdx.x; b < ngroups * nchunks; b += gridDim.x) {
@@ -340,10 +370,10 @@ __global__ void __launch_bounds__(kQThreadsQ)
 quantize_flat_kernel(const T* __restrict__ coeffs, int64_t* __restrict__ labels,
                      const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
                      uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab,
-                     unsigned int* __restrict__ flags) {
+                     unsigned int* __restrict__ flags, RelTol rt) {
   grid_dep_enter();
   __shared__ SmemTable st;
-  load_table(tab, st);
+  load_table(tab, rt, st);
   unsigned bad = 0;
   constexpr int QU = kQUq, TH = kQThreadsQ;
   const uint64_t step = static_cast<uint64_t>(gridDim.x) * TH * QU;
@@ -377,10 +407,11 @@ template <typename T>
 __global__ void __launch_bounds__(kQThreadsD)
 dequantize_flat_kernel(const int64_t* __restrict__ labels, T* __restrict__ coeffs,
                        const uint8_t* __restrict__ lev01, const uint8_t* __restrict__ lev2,
-                       uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab) {
+                       uint64_t nvec, uint32_t n2, uint64_t magic, int stop, LevelTable tab,
+                       RelTol rt) {
   grid_dep_enter();
   __shared__ SmemTable st;
-  load_table(tab, st);
+  load_table(tab, rt, st);
   constexpr int QU = kQUd, TH = kQThreadsD;
   const uint64_t step = static_cast<uint64_t>(gridDim.x) * TH * QU;
   for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * TH * QU + threadIdx.x;
@@ -565,7 +596,9 @@ int row_threads(int64_t n2) {
 template <typename T>
 cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev01,
                             const uint8_t* lev2, int64_t rows, int64_t n2, int stop_level,
-                            const LevelTable& tab, unsigned int* flags, cudaStream_t s) {
+                            const LevelTable& tab, unsigned int* flags, cudaStream_t s,
+                            const RelTol* rtp) {
+  const RelTol rt = rtp ? *rtp : RelTol{};
   const uint64_t count = static_cast<uint64_t>(rows) * n2;
   TraceScope ts(kKQuantize, -1, double(count) * (sizeof(T) + 8), s);
   uint64_t magic = 0;
@@ -575,26 +608,27 @@ cudaError_t launch_quantize(const T* coeffs, int64_t* labels, const uint8_t* lev
       launch_pdl(quantize_flat_kernel<T>,
                  dim3(flat_blocks(quantize_flat_kernel<T>, nvec, kQThreadsQ, kQUq)),
                  dim3(kQThreadsQ), 0, s, coeffs, labels, lev01, lev2, nvec,
-                 static_cast<uint32_t>(n2), magic, stop_level, tab, flags);
+                 static_cast<uint32_t>(n2), magic, stop_level, tab, flags, rt);
     if (count % 4 == 0) return cudaGetLastError();
     // The last count % 4 elements: one row-tile pass over the last row
     // would redo work, so the row-tile kernel takes the whole last row.
     const int64_t r_last = rows - 1;
     ts.more_kernels(1);
     launch_pdl(quantize_kernel<T>, dim3(1), dim3(row_threads(n2)), 0, s, coeffs + r_last * n2,
-               labels + r_last * n2, lev01 + r_last, lev2, n2, 1, stop_level, tab, flags);
+               labels + r_last * n2, lev01 + r_last, lev2, n2, 1, stop_level, tab, flags, rt);
     return cudaGetLastError();
   }
   const int threads = row_threads(n2);
   launch_pdl(quantize_kernel<T>, dim3(row_blocks(quantize_kernel<T>, rows, n2, threads)),
-             dim3(threads), 0, s, coeffs, labels, lev01, lev2, n2, rows, stop_level, tab, flags);
+             dim3(threads), 0, s, coeffs, labels, lev01, lev2, n2, rows, stop_level, tab, flags, rt);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* lev01,
                               const uint8_t* lev2, int64_t rows, int64_t n2, int stop_level,
-                              const LevelTable& tab, cudaStream_t s) {
+                              const LevelTable& tab, cudaStream_t s, const RelTol* rtp) {
+  const RelTol rt = rtp ? *rtp : RelTol{};
   const uint64_t count = static_cast<uint64_t>(rows) * n2;
   TraceScope ts(kKDequantize, -1, double(count) * (sizeof(T) + 8), s);
   uint64_t magic = 0;
@@ -604,17 +638,17 @@ cudaError_t launch_dequantize(const int64_t* labels, T* coeffs, const uint8_t* l
       launch_pdl(dequantize_flat_kernel<T>,
                  dim3(flat_blocks(dequantize_flat_kernel<T>, nvec, kQThreadsD, kQUd)),
                  dim3(kQThreadsD), 0, s, labels, coeffs, lev01, lev2, nvec,
-                 static_cast<uint32_t>(n2), magic, stop_level, tab);
+                 static_cast<uint32_t>(n2), magic, stop_level, tab, rt);
     if (count % 4 == 0) return cudaGetLastError();
     const int64_t r_last = rows - 1;
     ts.more_kernels(1);
     launch_pdl(dequantize_kernel<T>, dim3(1), dim3(row_threads(n2)), 0, s, labels + r_last * n2,
-               coeffs + r_last * n2, lev01 + r_last, lev2, n2, 1, stop_level, tab);
+               coeffs + r_last * n2, lev01 + r_last, lev2, n2, 1, stop_level, tab, rt);
     return cudaGetLastError();
   }
   const int threads = row_threads(n2);
   launch_pdl(dequantize_kernel<T>, dim3(row_blocks(dequantize_kernel<T>, rows, n2, threads)),
-             dim3(threads), 0, s, labels, coeffs, lev01, lev2, n2, rows, stop_level, tab);
+             dim3(threads), 0, s, labels, coeffs, lev01, lev2, n2, rows, stop_level, tab, rt);
   return cudaGetLastError();
 }
 
@@ -640,10 +674,10 @@ cudaError_t launch_minmax(const T* data, int64_t count, double* partial, unsigne
 #define MGB_INST(T)                                                                             \
   template cudaError_t launch_quantize<T>(const T*, int64_t*, const uint8_t*, const uint8_t*,  \
                                           int64_t, int64_t, int, const LevelTable&,             \
-                                          unsigned int*, cudaStream_t);                         \
+                                          unsigned int*, cudaStream_t, const RelTol*);          \
   template cudaError_t launch_dequantize<T>(const int64_t*, T*, const uint8_t*, const uint8_t*, \
                                             int64_t, int64_t, int, const LevelTable&,           \
-                                            cudaStream_t);                                      \
+                                            cudaStream_t, const RelTol*);                       \
   template cudaError_t launch_minmax<T>(const T*, int64_t, double*, unsigned int*, double*,    \
                                         cudaStream_t);
 MGB_INST(float)

@@ -210,6 +210,37 @@ def test_quantize_async_defers_its_checks(cuda):
     B.quantize_status()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_relative_bound_on_the_device_matches_the_host(cuda, dtype):
+    """Range, labels and bin centres with tau formed on the device from the
+    device range equal, bit for bit, those of the host calls given
+    tau = rel x (max - min); a constant array (tau = 0) is reported."""
+    torch = cuda
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    for dims, stop in (((65, 33, 47), 0), ((129, 100), 2), ((700,), 1)):
+        x = torch.from_numpy(F.grf_field(dims, seed=23)).to(tdt).cuda()
+        lo, hi = B.value_range(x)
+        rng = B.value_range_async(x)
+        B.quantize_status()
+        assert rng.cpu().tolist() == [lo, hi]
+        c = B.decompose(x.clone(), None, stop)
+        for rel in (1e-2, 1e-3, 1e-4, 1e-5):
+            tau = rel * (hi - lo)
+            want, _ = B.quantize(c, tau, None, stop)
+            got = B.quantize_rel_async(c, rel, rng, None, stop)
+            B.quantize_status()
+            assert torch.equal(got, want), (dims, rel)
+            back = B.dequantize(want, tau, tdt, None, stop)
+            back_rel = B.dequantize_rel(want, rel, rng, tdt, None, stop)
+            assert torch.equal(back_rel, back), (dims, rel)
+    flat = torch.ones((33, 33), dtype=tdt, device="cuda")
+    rng = B.value_range_async(flat)
+    B.quantize_rel_async(flat, 1e-3, rng)
+    with pytest.raises(B.MgardError) as e:
+        B.quantize_status()
+    assert e.value.code == -1
+
+
 def test_host_buffer_entry_points(cuda):
     torch = cuda
     dims = (65, 65, 65)
