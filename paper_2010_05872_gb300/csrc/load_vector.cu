@@ -45,14 +45,14 @@
 namespace mgb {
 namespace {
 
-template <typename T, bool DEC, int NS, int T1C, bool THREE, int CPT>
+template <typename T, bool DEC, int NS, int T1C, bool THREE, int CPT, bool REG>
 __global__ void __launch_bounds__(kLvMaxThreads)
 load_vector_march_kernel(LevelK<T> lv, const T* __restrict__ fine, T* __restrict__ coarse,
                          T* __restrict__ F, MarchGeom g, uint64_t fine_count,
                          unsigned int* __restrict__ status) {
   grid_dep_enter();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  load_vector_march_tile<T, DEC, NS, T1C, THREE, false, CPT>(lv, fine, coarse, F, g, fine_count, status,
+  load_vector_march_tile<T, DEC, NS, T1C, THREE, false, CPT, 1, REG>(lv, fine, coarse, F, g, fine_count, status,
                                                  blockIdx.x, smem_raw);
 }
 
@@ -91,12 +91,18 @@ cudaError_t launch_march_shape(const LevelK<T>& lv, bool dec, const T* fine, T* 
   const size_t smem = sizeof(T) * static_cast<size_t>(NS) * g.BUF;
   using KernelFn = void (*)(LevelK<T>, const T*, T*, T*, MarchGeom, uint64_t, unsigned int*);
   KernelFn kernel;
+  // Odd axes 1 and 2 (every 2^k + 1 grid): coarse nodes at 2k, zero taps skipped.
+  const bool reg = (lv.ax[1].n & 1) && (lv.ax[2].n & 1);
   if (three)
-    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, true, CPT>
-                 : load_vector_march_kernel<T, false, NS, T1C, true, CPT>;
+    kernel = dec ? (reg ? load_vector_march_kernel<T, true, NS, T1C, true, CPT, true>
+                        : load_vector_march_kernel<T, true, NS, T1C, true, CPT, false>)
+                 : (reg ? load_vector_march_kernel<T, false, NS, T1C, true, CPT, true>
+                        : load_vector_march_kernel<T, false, NS, T1C, true, CPT, false>);
   else
-    kernel = dec ? load_vector_march_kernel<T, true, NS, T1C, false, CPT>
-                 : load_vector_march_kernel<T, false, NS, T1C, false, CPT>;
+    kernel = dec ? (reg ? load_vector_march_kernel<T, true, NS, T1C, false, CPT, true>
+                        : load_vector_march_kernel<T, true, NS, T1C, false, CPT, false>)
+                 : (reg ? load_vector_march_kernel<T, false, NS, T1C, false, CPT, true>
+                        : load_vector_march_kernel<T, false, NS, T1C, false, CPT, false>);
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);

@@ -50,12 +50,16 @@ struct MarchCfg<double> {
 // it.  GMAX > 1 allows row groups: g.groups groups of g.gthreads threads
 // share the staged planes of a tile of g.groups x T1C coarse rows, group q
 // taking coarse rows q T1C .. q T1C + T1C - 1 (staged rows 2 q T1C onwards),
-// so a narrow grid keeps more warps of the block busy.  PERSIST: the CTA runs further tiles in the same launch, so the tile
+// so a narrow grid keeps more warps of the block busy.  REG: axes 1 and 2
+// have odd lengths, so coarse node k sits at 2k on both and the taps that
+// are zero there are skipped (a column's 5-tap R window starts at its
+// node - 2, its X taps sit at even offsets, an odd staged row feeds two
+// coarse rows).  PERSIST: the CTA runs further tiles in the same launch, so the tile
 // invalidates its barriers at the end (the next tile sets them up again) and
 // reads its few plain-loaded elements through L2 (other CTAs of the launch
 // may have written them).
 template <typename T, bool DEC, int NS, int T1C, bool THREE, bool PERSIST = false, int CPT = 2,
-          int GMAX = 1>
+          int GMAX = 1, bool REG = false>
 __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
                                                        const T* __restrict__ fine,
                                                        T* __restrict__ coarse, T* __restrict__ F,
@@ -344,7 +348,8 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
       for (int c = 0; c < CPT; ++c) {
         gs[c] = T(0);
 #pragma unroll
-        for (int o = (c ? 2 * c - 1 : 0); o < W && o <= 2 * c + 4; ++o) gs[c] += rwc[c][o] * fe[o];
+        for (int o = REG ? 2 * c : (c ? 2 * c - 1 : 0); o < W && o <= 2 * c + 4; ++o)
+          gs[c] += rwc[c][o] * fe[o];
       }
       const int base = (s & 1) ? (s - 3) / 2 : s / 2 - 2;
       const int kr = THREE ? s_rown[s + soff] : 0;
@@ -356,6 +361,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const int t = base + i;
+            if (REG && (s & 1) && i == 2) continue;  // a zero weight
             if (t >= 0 && t < TM) G1[c][t] += s_w1[s + soff][i] * gs[c];
           }
         }
@@ -365,7 +371,7 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
         for (int c = 0; c < CPT; ++c) {
           T hs = T(0);
 #pragma unroll
-          for (int o = 2 * c; o < W && o <= 2 * c + 4; ++o) hs += xc[c][o] * fe[o];
+          for (int o = 2 * c; o < W && o <= 2 * c + 4; o += REG ? 2 : 1) hs += xc[c][o] * fe[o];
           if (!THREE) {
             H1[c][0] = hs;
           } else {
