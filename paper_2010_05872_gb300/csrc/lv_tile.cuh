@@ -41,7 +41,11 @@ struct MarchCfg<float> {
 };
 template <>
 struct MarchCfg<double> {
-  static constexpr int NS = 3, T1 = 4, CPT = 2;
+  // FP64 is bound by the FMA rate, so fewer halo rows pay: over (NS, T1) in
+  // {(2, 4), (3, 4), (2, 6), (3, 6), (2, 8)} at 513^3, T1 = 6 gave the
+  // shortest finest launch (2.29 ms; 2.46 with T1 = 4), two buffers the
+  // smaller footprint of the two equal ones.
+  static constexpr int NS = 2, T1 = 6, CPT = 2;
   static constexpr int NS_L2 = 3, T1_L2 = 4, CPT_L2 = 2;
 };
 
