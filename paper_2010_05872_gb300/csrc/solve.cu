@@ -326,7 +326,23 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
                   sizeof(T) * passes * double(c0) * c1 * c2, s);
     const size_t per_row = sizeof(T) * static_cast<size_t>(c2 | 1);
     const size_t tpad = (3 * sizeof(T) * static_cast<size_t>(c2) + 15) / 16 * 16;
-    if (a == 2 && (c2 & 1) && per_row <= 16 * 1024 && c0 * c1 >= 1024) {
+    // FP64 runs the contiguous axis through the segmented kernel as lines of
+    // stride 1: its 16-row chains instead of whole-line Thomas chains, which
+    // FP64's FMA latency makes long (and few lines fit a batch).
+    const bool seg64 = sizeof(T) == 8 && a == 2 && lv.ax[2].n > 1 &&
+                       (c2 + lv.ax[2].seg_len - 1) / lv.ax[2].seg_len <= kSegWarps;
+    if (seg64) {
+      const int nc = static_cast<int>(c2);
+      const int nseg = (nc + lv.ax[2].seg_len - 1) / lv.ax[2].seg_len;
+      const int64_t nlines = c0 * c1;
+      const size_t smem = sizeof(T) * (5 * static_cast<size_t>(nc) + 64 * static_cast<size_t>(nseg));
+      if (c0 * c1 * c2 < (int64_t(1) << 31))
+        launch_pdl(solve_seg_kernel<T, int32_t>, dim3(ceil_div(nlines, 32)), dim3(32 * nseg), smem, s,
+                   lv.ax[2], F, B, static_cast<int32_t>(nlines), int32_t(1), static_cast<int32_t>(nc), m);
+      else
+        launch_pdl(solve_seg_kernel<T, int64_t>, dim3(ceil_div(nlines, 32)), dim3(32 * nseg), smem, s,
+                   lv.ax[2], F, B, nlines, int64_t(1), static_cast<int64_t>(nc), m);
+    } else if (a == 2 && (c2 & 1) && per_row <= 16 * 1024 && c0 * c1 >= 1024) {
       // Odd line length: persistent double-buffered TMA batches of about
       // 32 KB of lines, three CTAs per SM.
       const int64_t nlines = c0 * c1;
