@@ -91,8 +91,8 @@ cudaError_t launch_march_shape(const LevelK<T>& lv, bool dec, const T* fine, T* 
   const size_t smem = sizeof(T) * static_cast<size_t>(NS) * g.BUF;
   using KernelFn = void (*)(LevelK<T>, const T*, T*, T*, MarchGeom, uint64_t, unsigned int*);
   KernelFn kernel;
-  // Odd axes 1 and 2 (every 2^k + 1 grid): coarse nodes at 2k, zero taps skipped.
-  const bool reg = (lv.ax[1].n & 1) && (lv.ax[2].n & 1);
+  // Odd axes (every 2^k + 1 grid): coarse nodes at 2k, zero taps skipped.
+  const bool reg = (lv.ax[0].n & 1) && (lv.ax[1].n & 1) && (lv.ax[2].n & 1);
   if (three)
     kernel = dec ? (reg ? load_vector_march_kernel<T, true, NS, T1C, true, CPT, true>
                         : load_vector_march_kernel<T, true, NS, T1C, true, CPT, false>)

@@ -54,11 +54,11 @@ struct MarchCfg<double> {
 // it.  GMAX > 1 allows row groups: g.groups groups of g.gthreads threads
 // share the staged planes of a tile of g.groups x T1C coarse rows, group q
 // taking coarse rows q T1C .. q T1C + T1C - 1 (staged rows 2 q T1C onwards),
-// so a narrow grid keeps more warps of the block busy.  REG: axes 1 and 2
-// have odd lengths, so coarse node k sits at 2k on both and the taps that
+// so a narrow grid keeps more warps of the block busy.  REG: all three axes
+// have odd lengths, so coarse node k sits at 2k on each and the taps that
 // are zero there are skipped (a column's 5-tap R window starts at its
 // node - 2, its X taps sit at even offsets, an odd staged row feeds two
-// coarse rows).  PERSIST: the CTA runs further tiles in the same launch, so the tile
+// coarse rows, an odd plane feeds two coarse planes through R0 alone).  PERSIST: the CTA runs further tiles in the same launch, so the tile
 // invalidates its barriers at the end (the next tile sets them up again) and
 // reads its few plain-loaded elements through L2 (other CTAs of the launch
 // may have written them).
@@ -408,12 +408,23 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
         if (pn && d >= 0 && d <= 2) yk[k] = __ldg((DEC ? lv.ax[0].xd : lv.ax[0].xr) + 3 * kk + d);
       }
     }
+    if (REG && !pn) {
+      // An odd plane of an odd axis 0 feeds coarse planes kdone and kdone + 1
+      // through R0 alone (wk[2] and every yk are zero).
 #pragma unroll
-    for (int c = 0; c < CPT; ++c)
+      for (int c = 0; c < CPT; ++c)
 #pragma unroll
-      for (int t = 0; t < TM; ++t)
+        for (int t = 0; t < TM; ++t)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) acc[c][k][t] += wk[k] * G1[c][t] - yk[k] * H1[c][t];
+          for (int k = 0; k < 2; ++k) acc[c][k][t] += wk[k] * G1[c][t];
+    } else {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int t = 0; t < TM; ++t)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc[c][k][t] += wk[k] * G1[c][t] - yk[k] * H1[c][t];
+    }
     store_done(j, false);
     }
     __syncthreads();  // every read of this buffer is done
