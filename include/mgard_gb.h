@@ -29,6 +29,14 @@
  *    enqueued on it and the calls return without waiting, except
  *    mgard_quantize and mgard_value_range, which wait for their own flags,
  *    and mgard_quantize_status, which waits to read them.
+ *  - Calls on different streams may run at the same time from different
+ *    host threads (say one field's compression while another's is
+ *    decompressed, so that the two directions of the host link overlap).
+ *    A call that waits keeps its flag word, reduction buffers and pinned
+ *    mirrors per (device, stream) and holds no lock that a call on another
+ *    stream needs while it waits; only mgard_decompose_adaptive waits under
+ *    a per-device lock.  That per-stream scratch (about 20 KB) is made by a
+ *    stream's first such call, so make that call outside any stream capture.
  *  - The first call for a given (device, dims, coords, dtype) builds a plan
  *    (host FP64 tables, uploaded once with cudaMalloc/cudaMemcpy) and caches
  *    it until mgard_release_plans().  Make that first call outside any CUDA
@@ -239,8 +247,8 @@ int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax
  * labels and values equal those of the host calls given tau = rel_bound x
  * (max - min) computed in FP64.  A tau that is not positive and finite
  * (e.g. a constant array) is reported by mgard_quantize_status as
- * MGARD_ERR_ARG.  The range's partial sums use a per-device buffer: range
- * calls on different streams must not overlap. */
+ * MGARD_ERR_ARG.  The range's partial sums use a buffer of the stream's
+ * own, so range calls on different streams may overlap. */
 int mgard_value_range_async(int64_t count, int dtype, const void* data, double* range,
                             void* stream);
 int mgard_quantize_rel_async(int ndim, const int64_t* dims, const double* const* coords, int dtype,

@@ -23,6 +23,7 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 std::mutex g_mu;
 std::map<std::string, std::unique_ptr<DevPlan>> g_plans;
 std::map<int, std::unique_ptr<DevCtx>> g_ctx;
+std::map<std::pair<int, uintptr_t>, std::unique_ptr<StreamScratch>> g_scratch;
 
 template <typename T>
 void fill_levels(DevPlan& p, const std::vector<std::vector<size_t>>& offs, char* base,
@@ -189,13 +190,38 @@ DevCtx* get_ctx() {
   if (cudaMalloc(&c->flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
   if (cudaMemset(c->flags, 0, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
   if (cudaMalloc(&c->partial, 2 * kMinmaxBlocks * sizeof(double)) != cudaSuccess) return nullptr;
-  if (cudaMalloc(&c->result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
-  if (cudaMallocHost(&c->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) return nullptr;
-  if (cudaMallocHost(&c->h_result, 2 * sizeof(double)) != cudaSuccess) return nullptr;
   if (cudaMalloc(&c->sums, 2 * kMaxLevels * sizeof(double)) != cudaSuccess) return nullptr;
   if (cudaMallocHost(&c->h_sums, 2 * kMaxLevels * sizeof(double)) != cudaSuccess) return nullptr;
   DevCtx* raw = c.get();
   g_ctx.emplace(device, std::move(c));
+  return raw;
+}
+
+StreamScratch* get_scratch(cudaStream_t s) {
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return nullptr;
+  const auto key = std::make_pair(device, reinterpret_cast<uintptr_t>(s));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_scratch.find(key);
+  if (it != g_scratch.end()) return it->second.get();
+  auto sc = std::make_unique<StreamScratch>();
+  void* dmem = nullptr;
+  const size_t bytes = 256 + sizeof(double) * (2 * kMinmaxBlocks + 2);
+  if (cudaMalloc(&dmem, bytes) != cudaSuccess) return nullptr;
+  if (cudaMemset(dmem, 0, bytes) != cudaSuccess || cudaMallocHost(&sc->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
+    cudaFree(dmem);
+    return nullptr;
+  }
+  if (cudaMallocHost(&sc->h_result, 2 * sizeof(double)) != cudaSuccess) {
+    cudaFreeHost(sc->h_flags);
+    cudaFree(dmem);
+    return nullptr;
+  }
+  sc->flag = static_cast<unsigned int*>(dmem);
+  sc->result = reinterpret_cast<double*>(static_cast<char*>(dmem) + 256);
+  sc->partial = sc->result + 2;
+  StreamScratch* raw = sc.get();
+  g_scratch.emplace(key, std::move(sc));
   return raw;
 }
 
@@ -632,20 +658,20 @@ int mgard_iso_area(int ndim, const int64_t* dims, const double* const* coords, i
   if (rc != MGARD_OK) return rc;
   if (p->h.ndim != 3) return MGARD_ERR_SHAPE;
   if (data == nullptr || reinterpret_cast<uintptr_t>(data) % elem_size(dtype)) return MGARD_ERR_ARG;
-  DevCtx* c = get_ctx();
-  if (c == nullptr) return MGARD_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScratch* sc = get_scratch(s);
+  if (sc == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(sc->mu);
   const double* x[3] = {p->xc[0], p->xc[1], p->xc[2]};
   if (dtype == MGARD_F64)
     MGB_TRY(launch_iso_area<double>(static_cast<const double*>(data), p->h.dims3.data(), x, iso,
-                                    c->partial, c->result, s));
+                                    sc->partial, sc->result, s));
   else
     MGB_TRY(launch_iso_area<float>(static_cast<const float*>(data), p->h.dims3.data(), x, iso,
-                                   c->partial, c->result, s));
-  MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, sizeof(double), cudaMemcpyDeviceToHost, s));
+                                   sc->partial, sc->result, s));
+  MGB_TRY(cudaMemcpyAsync(sc->h_result, sc->result, sizeof(double), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
-  *area_out = c->h_result[0];
+  *area_out = sc->h_result[0];
   return MGARD_OK;
 }
 
@@ -678,7 +704,7 @@ int check_stream(const uint8_t* h, size_t bytes, int64_t count) {
 
 // Pack on the device; *bytes_out receives the stream size (waits).
 int pack_device(int64_t count, const int64_t* labels, void* out, size_t capacity,
-                size_t* bytes_out, DevCtx* c, cudaStream_t s) {
+                size_t* bytes_out, StreamScratch* sc, cudaStream_t s) {
   size_t bound = 0;
   mgard_pack_bound(count, &bound);
   if (capacity < bound) return MGARD_ERR_WORKSPACE;
@@ -687,12 +713,12 @@ int pack_device(int64_t count, const int64_t* labels, void* out, size_t capacity
   MGB_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(uint64_t) * (nchunks + 1), s));
   cudaError_t e = launch_pack_labels(labels, count, static_cast<uint8_t*>(out), scratch + 1, scratch, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->h_result, scratch, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(sc->h_result, scratch, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(scratch, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return MGARD_ERR_CUDA;
   uint64_t words = 0;
-  std::memcpy(&words, c->h_result, sizeof words);
+  std::memcpy(&words, sc->h_result, sizeof words);
   *bytes_out = pack_header_bytes(count) + 8 * static_cast<size_t>(words);
   return MGARD_OK;
 }
@@ -751,10 +777,11 @@ int mgard_pack_labels(int64_t count, const int64_t* labels, void* out, size_t ca
   if (count < 0 || bytes_out == nullptr || out == nullptr || reinterpret_cast<uintptr_t>(out) % 8)
     return MGARD_ERR_ARG;
   if (count > 0 && (labels == nullptr || reinterpret_cast<uintptr_t>(labels) % 8)) return MGARD_ERR_ARG;
-  DevCtx* c = get_ctx();
-  if (c == nullptr) return MGARD_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(c->mu);
-  return pack_device(count, labels, out, capacity, bytes_out, c, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScratch* sc = get_scratch(s);
+  if (sc == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(sc->mu);
+  return pack_device(count, labels, out, capacity, bytes_out, sc, s);
 }
 
 int mgard_unpack_labels(const void* in, size_t bytes, int64_t count, int64_t* labels, void* stream) {
@@ -810,10 +837,10 @@ int mgard_compress_host_packed(int ndim, const int64_t* dims, const double* cons
   if (rc != MGARD_OK) return rc;
   size_t sb = 0;
   {
-    DevCtx* c = get_ctx();
-    if (c == nullptr) return MGARD_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(c->mu);
-    rc = pack_device(count, dev_labels, dev_stream, dev_capacity, &sb, c, s);
+    StreamScratch* sc = get_scratch(s);
+    if (sc == nullptr) return MGARD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(sc->mu);
+    rc = pack_device(count, dev_labels, dev_stream, dev_capacity, &sb, sc, s);
   }
   if (rc != MGARD_OK) return rc;
   if (sb > host_capacity) return MGARD_ERR_WORKSPACE;
@@ -878,23 +905,26 @@ int quantize_table(const DevPlan& p, int dtype, int stop_level, const LevelTable
                    const void* coeffs, int64_t* labels, void* stream) {
   DevCtx* c = get_ctx();
   if (c == nullptr) return MGARD_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MGB_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s));
+  StreamScratch* sc = get_scratch(s);
+  if (sc == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(sc->mu);
+  MGB_TRY(cudaMemsetAsync(sc->flag, 0, sizeof(unsigned), s));
   const auto& d = p.h.dims3;
   if (dtype == MGARD_F64)
     MGB_TRY(launch_quantize<double>(static_cast<const double*>(coeffs), labels, p.lev01, p.lev[2],
-                                    d[0] * d[1], d[2], stop_level, tab, c->flags, s));
+                                    d[0] * d[1], d[2], stop_level, tab, sc->flag, s));
   else
     MGB_TRY(launch_quantize<float>(static_cast<const float*>(coeffs), labels, p.lev01, p.lev[2],
-                                   d[0] * d[1], d[2], stop_level, tab, c->flags, s));
-  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+                                   d[0] * d[1], d[2], stop_level, tab, sc->flag, s));
+  MGB_TRY(cudaMemcpyAsync(sc->h_flags, sc->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaMemcpyAsync(sc->h_flags + 1, c->flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
-  if (c->h_flags[1]) {
+  if (sc->h_flags[1]) {
     MGB_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(unsigned), s));
     return MGARD_ERR_TIMEOUT;
   }
-  const unsigned f = c->h_flags[0];
+  const unsigned f = sc->h_flags[0];
   if (f & 1u) return MGARD_ERR_NONFINITE;
   if (f & 2u) return MGARD_ERR_OVERFLOW;
   return MGARD_OK;
@@ -962,11 +992,13 @@ int mgard_quantize_async(int ndim, const int64_t* dims, const double* const* coo
 int mgard_quantize_status(void* stream) {
   DevCtx* c = get_ctx();
   if (c == nullptr) return MGARD_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  StreamScratch* sc = get_scratch(s);
+  if (sc == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(sc->mu);
+  MGB_TRY(cudaMemcpyAsync(sc->h_flags, c->flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
-  const unsigned f = c->h_flags[2], t = c->h_flags[1];
+  const unsigned f = sc->h_flags[2], t = sc->h_flags[1];
   if (f) MGB_TRY(cudaMemsetAsync(c->flags + 2, 0, sizeof(unsigned), s));
   if (t) {
     MGB_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(unsigned), s));
@@ -1035,23 +1067,26 @@ int mgard_value_range(int64_t count, int dtype, const void* data, double* minmax
   if (reinterpret_cast<uintptr_t>(data) % elem_size(dtype)) return MGARD_ERR_ARG;
   DevCtx* c = get_ctx();
   if (c == nullptr) return MGARD_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MGB_TRY(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s));
+  StreamScratch* sc = get_scratch(s);
+  if (sc == nullptr) return MGARD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(sc->mu);
+  MGB_TRY(cudaMemsetAsync(sc->flag, 0, sizeof(unsigned), s));
   if (dtype == MGARD_F64)
-    MGB_TRY(launch_minmax<double>(static_cast<const double*>(data), count, c->partial, c->flags, c->result, s));
+    MGB_TRY(launch_minmax<double>(static_cast<const double*>(data), count, sc->partial, sc->flag, sc->result, s));
   else
-    MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, c->partial, c->flags, c->result, s));
-  MGB_TRY(cudaMemcpyAsync(c->h_result, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  MGB_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, sc->partial, sc->flag, sc->result, s));
+  MGB_TRY(cudaMemcpyAsync(sc->h_result, sc->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaMemcpyAsync(sc->h_flags, sc->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MGB_TRY(cudaMemcpyAsync(sc->h_flags + 1, c->flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MGB_TRY(cudaStreamSynchronize(s));
-  if (c->h_flags[1]) {
+  if (sc->h_flags[1]) {
     MGB_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(unsigned), s));
     return MGARD_ERR_TIMEOUT;
   }
-  if (c->h_flags[0] & 1u) return MGARD_ERR_NONFINITE;
-  minmax_out[0] = c->h_result[0];
-  minmax_out[1] = c->h_result[1];
+  if (sc->h_flags[0] & 1u) return MGARD_ERR_NONFINITE;
+  minmax_out[0] = sc->h_result[0];
+  minmax_out[1] = sc->h_result[1];
   return MGARD_OK;
 }
 
@@ -1064,11 +1099,13 @@ int mgard_value_range_async(int64_t count, int dtype, const void* data, double* 
   DevCtx* c = get_ctx();
   if (c == nullptr) return MGARD_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScratch* sc = get_scratch(s);  // its partial sums: ordered by the stream
+  if (sc == nullptr) return MGARD_ERR_CUDA;
   unsigned int* flags = c->flags + 2;  // gathered until mgard_quantize_status
   if (dtype == MGARD_F64)
-    MGB_TRY(launch_minmax<double>(static_cast<const double*>(data), count, c->partial, flags, range, s));
+    MGB_TRY(launch_minmax<double>(static_cast<const double*>(data), count, sc->partial, flags, range, s));
   else
-    MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, c->partial, flags, range, s));
+    MGB_TRY(launch_minmax<float>(static_cast<const float*>(data), count, sc->partial, flags, range, s));
   return MGARD_OK;
 }
 

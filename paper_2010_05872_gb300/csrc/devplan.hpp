@@ -42,15 +42,29 @@ struct DevPlan {
 };
 
 // Small per-device scratch for flags and reductions (allocated once).
+// flags[1] gathers the bounded waits that gave up (every transform and the
+// batched form write it), flags[2] the asynchronous quantizer's problems.
 struct DevCtx {
   unsigned int* flags = nullptr;  // [4]
-  double* partial = nullptr;      // [2 * kMinmaxBlocks]
-  double* result = nullptr;       // [2]
-  unsigned int* h_flags = nullptr;  // pinned host mirrors
-  double* h_result = nullptr;
+  double* partial = nullptr;      // [2 * kMinmaxBlocks] (adaptive decomposition)
   double* sums = nullptr;         // [2 * kMaxLevels] per-level sums of the adaptive decomposition
   double* h_sums = nullptr;       // pinned host mirror
-  std::mutex mu;                  // serialises the calls that wait on these flags
+  std::mutex mu;                  // serialises the adaptive decompositions
+};
+
+// Scratch of the calls that wait on a stream (value range, quantization,
+// the packed stream's size, the iso-surface area, the status read) and of
+// the asynchronous value range, one per (device, stream): such calls on
+// different streams share no buffer and no lock, so one stream's wait (say
+// behind a large host copy) holds up no other.  Created on the stream's
+// first such call and kept for the life of the process.
+struct StreamScratch {
+  unsigned int* flag = nullptr;     // [1] the call's own flag word
+  double* partial = nullptr;        // [2 * kMinmaxBlocks]
+  double* result = nullptr;         // [2]
+  unsigned int* h_flags = nullptr;  // pinned [4]
+  double* h_result = nullptr;       // pinned [2]
+  std::mutex mu;                    // serialises the waiting calls on this stream
 };
 
 // Look up (or build and upload) the plan of this shape/coords/dtype on the
@@ -59,6 +73,9 @@ int get_plan(int ndim, const int64_t* dims, const double* const* coords, int dty
 
 // The per-device flag/reduction context (created on first use).
 DevCtx* get_ctx();
+
+// The scratch of stream `s` on the current device (created on first use).
+StreamScratch* get_scratch(cudaStream_t s);
 
 template <typename T>
 const std::vector<LevelK<T>>& levels(const DevPlan& p);

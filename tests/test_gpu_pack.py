@@ -96,6 +96,76 @@ def test_packed_host_path_matches_unpacked(cuda):
     assert np.abs(out_p.numpy().astype(np.float64) - u).max() <= tau
 
 
+def _round_trips(torch, dims, u, bounds, stream, out):
+    """Packed host round trips of field u at each bound on `stream` (0 = the
+    legacy default stream); appends (stream bytes, tau, reconstruction)."""
+    n = u.size
+    ws = B.workspace(dims, torch.float32)
+    dev = torch.empty(dims, dtype=torch.float32, device="cuda")
+    lab = torch.empty(n, dtype=torch.int64, device="cuda")
+    cap = B.pack_bound(n)
+    dstream = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    hf = torch.from_numpy(u).pin_memory()
+    hs = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    ho = torch.empty(dims, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    sp = stream.cuda_stream if stream is not None else 0
+    for rel in bounds:
+        rc, nbytes, tau = B.mgard_compress_host_packed(
+            dims, None, B.F32, 0, rel, hf.data_ptr(), hs.data_ptr(), cap, dev.data_ptr(),
+            lab.data_ptr(), dstream.data_ptr(), cap, ws.data_ptr(), ws.numel(), sp)
+        assert rc == 0, rc
+        packed = hs.numpy()[:nbytes].copy()
+        rc = B.mgard_decompress_host_packed(
+            dims, None, B.F32, 0, tau, hs.data_ptr(), nbytes, ho.data_ptr(), dev.data_ptr(),
+            lab.data_ptr(), dstream.data_ptr(), cap, ws.data_ptr(), ws.numel(), sp)
+        assert rc == 0, rc
+        out.append((packed, tau, ho.numpy().copy()))
+
+
+def test_two_streams_from_two_threads_match_serial(cuda):
+    """Two host threads each run packed round trips of their own field on
+    their own stream at the same time (each stream's first calls make its
+    scratch while the other stream has work in flight): every packed stream
+    and every reconstruction equals that of the same calls made one after
+    another, and each reconstruction stays within tau of its field."""
+    import threading
+    torch = cuda
+    cases = [((129, 257, 65), F.grf_field((129, 257, 65), seed=11)),
+             ((65, 129, 97), F.grf_field((65, 129, 97), seed=12))]
+    bounds = (1e-2, 1e-3, 1e-4)
+    serial = []
+    for dims, u in cases:
+        got = []
+        _round_trips(torch, dims, u, bounds, None, got)
+        serial.append(got)
+    streams = [torch.cuda.Stream() for _ in cases]
+    results = [[] for _ in cases]
+    errors = []
+
+    def run(q):
+        try:
+            dims, u = cases[q]
+            _round_trips(torch, dims, u, bounds, streams[q], results[q])
+        except BaseException as exc:  # re-raised in the test's thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=run, args=(q,)) for q in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    for (dims, u), want, got in zip(cases, serial, results):
+        assert len(got) == len(bounds)
+        for (pw, tw, rw), (pg, tg, rg) in zip(want, got):
+            assert tg == tw
+            assert np.array_equal(pg, pw)
+            assert np.array_equal(rg, rw)
+            assert np.abs(rg.astype(np.float64) - u).max() <= tg
+
+
 @pytest.mark.parametrize("dims,stop", [((17, 9, 12), 0), ((17, 9, 12), 2), ((33, 20), 1),
                                        ((100,), 3), ((65, 65, 65), 5)])
 def test_lorenzo_matches_oracle(cuda, dims, stop):
