@@ -37,6 +37,7 @@
 #include "kernels.cuh"
 #include "lv_tile.cuh"
 #include "mgard_gb.h"
+#include "pdl.cuh"
 #include "solve_tile.cuh"
 #include "tma.cuh"
 
@@ -414,8 +415,7 @@ int build_batch(int n, const int64_t* dims3, void* const* data, char* ws, size_t
       cudaMemcpy(bp.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
           cudaSuccess)
     return MGARD_ERR_CUDA;
-  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess)
+  if (allow_dynamic_smem(batch_kernel, smem) != cudaSuccess)
     return MGARD_ERR_CUDA;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, smem);

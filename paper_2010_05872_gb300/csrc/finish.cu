@@ -187,8 +187,7 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
           sizeof(T) * (2 * NS * static_cast<size_t>(g.FBUF) +
                        (nodal_src == interp_src ? 1 : 2) * (NS + 1) * static_cast<size_t>(g.CBUF));
       auto kernel = finish_march_kernel<T, NS, FinishCfg<T>::T1>;
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
+      allow_dynamic_smem(kernel, smem);
       int per_sm = 1;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
       per_sm = std::max(per_sm, 1);
@@ -210,8 +209,7 @@ cudaError_t launch_finish(const LevelK<T>& lv_in, const T* nodal_src, const T* i
   const double ncs = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
   TraceScope ts(sign < T(0) ? kKFinishDec : kKFinishRec, level,
                 sizeof(T) * (2 * nf + (nodal_src == interp_src ? 1 : 2) * ncs), s);
-  cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
+  allow_dynamic_smem(finish_kernel<T>, smem);
   launch_pdl(finish_kernel<T>, dim3(grid), dim3(threads), smem, s, lv, nodal_src, interp_src, sign,
              fine);
   return cudaGetLastError();

@@ -493,8 +493,7 @@ int encode(int64_t n, const int64_t* labels, uint8_t* out, size_t capacity, size
   if (nchunks > 0) {
     const int pitch = static_cast<int>(std::max<uint64_t>(1, totals[1]));  // <= kChunkWords
     const size_t smem = sizeof(uint64_t) * kEncWarps * static_cast<size_t>(pitch);
-    HUFF_TRY(cudaFuncSetAttribute(huff_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
+    HUFF_TRY(allow_dynamic_smem(huff_encode_kernel, smem));
     HUFF_TRY(launch_pdl(huff_encode_kernel, dim3(grid_for(nchunks, kEncWarps)), dim3(32 * kEncWarps),
                         smem, s, labels, n, nchunks, static_cast<const uint64_t*>(d_enc),
                         static_cast<const uint64_t*>(words), reinterpret_cast<uint64_t*>(out + hdr),

@@ -103,7 +103,7 @@ cudaError_t launch_march_shape(const LevelK<T>& lv, bool dec, const T* fine, T* 
                         : load_vector_march_kernel<T, true, NS, T1C, false, CPT, false>)
                  : (reg ? load_vector_march_kernel<T, false, NS, T1C, false, CPT, true>
                         : load_vector_march_kernel<T, false, NS, T1C, false, CPT, false>);
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  allow_dynamic_smem(kernel, smem);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem);
   per_sm = std::max(per_sm, 1);

@@ -13,6 +13,8 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
 #include <utility>
 
 namespace mgb {
@@ -43,6 +45,31 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Raise (never lower) the dynamic shared memory `kernel` may be launched
+// with on the current device.  The limit belongs to the kernel, not to a
+// launch: a per-launch set would let a call on another host thread lower it
+// between this thread's set and its launch, which would then be refused.  A
+// limit that only grows stays valid for every launch that raised it to its
+// own need.
+inline cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& g = granted[std::make_pair(device, kernel)];
+  if (bytes <= g) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess) g = bytes;
+  return e;
+}
+
+template <typename... KArgs>
+cudaError_t allow_dynamic_smem(void (*kernel)(KArgs...), size_t bytes) {
+  return allow_dynamic_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 }  // namespace mgb

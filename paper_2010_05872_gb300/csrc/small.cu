@@ -530,7 +530,7 @@ cudaError_t launch_small_levels(const LevelK<T>* lv, int nlev, bool dec, T* data
   if (sp.ntop > kSmallMaxNodes) return cudaErrorInvalidValue;
   TraceScope ts(kKSmallLevels, level, 2.0 * sizeof(T) * double(sp.ntop), s);
   auto kernel = dec ? small_levels_kernel<T, true> : small_levels_kernel<T, false>;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  allow_dynamic_smem(kernel, smem);
   launch_pdl(kernel, dim3(1), dim3(small_threads<T>()), smem, s, sp, nlev, data);
   return cudaGetLastError();
 }

@@ -350,8 +350,7 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
       const int vec = 16 / static_cast<int>(sizeof(T));
       const int bufelems = ((rows * static_cast<int>(c2) + 2 * vec) + vec - 1) / vec * vec;
       const size_t smem = tpad + 2 * sizeof(T) * static_cast<size_t>(bufelems);
-      cudaFuncSetAttribute(solve_contig_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
+      allow_dynamic_smem(solve_contig_pipe_kernel<T>, smem);
       int per_sm = 1;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_contig_pipe_kernel<T>, 128, smem);
       const int64_t nbatch = (nlines + rows - 1) / rows;
@@ -364,8 +363,7 @@ cudaError_t launch_solves(const LevelK<T>& lv, T* F, T* B, ApplyMode mode, int l
       int rows = static_cast<int>(std::min<size_t>(128, (112 * 1024) / per_row));
       rows = std::max(rows, 1);
       const size_t smem = per_row * rows;
-      cudaFuncSetAttribute(solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
+      allow_dynamic_smem(solve_contig_kernel<T>, smem);
       launch_pdl(solve_contig_kernel<T>, dim3(ceil_div(nlines, rows)), dim3(128), smem, s, lv.ax[2],
                  F, B, nlines, rows, m);
     } else if (a != 2 && (lv.ax[a].nc + lv.ax[a].seg_len - 1) / lv.ax[a].seg_len <= kSegWarps) {

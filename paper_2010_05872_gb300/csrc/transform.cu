@@ -189,13 +189,11 @@ cudaError_t launch_load_vector(const LevelK<T>& lv, bool dec, const T* fine, T* 
   const double ncs = double(lv.ax[0].nc) * lv.ax[1].nc * lv.ax[2].nc;
   TraceScope ts(dec ? kKLoadVectorDec : kKLoadVectorRec, level, sizeof(T) * (nf + 2 * ncs), s);
   if (dec) {
-    cudaFuncSetAttribute(load_vector_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
+    allow_dynamic_smem(load_vector_kernel<T, true>, smem);
     launch_pdl(load_vector_kernel<T, true>, dim3(grid), dim3(kThreads), smem, s, lv, fine, coarse,
                F, tk0, tk1, tk2);
   } else {
-    cudaFuncSetAttribute(load_vector_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
+    allow_dynamic_smem(load_vector_kernel<T, false>, smem);
     launch_pdl(load_vector_kernel<T, false>, dim3(grid), dim3(kThreads), smem, s, lv, fine, coarse,
                F, tk0, tk1, tk2);
   }

@@ -123,16 +123,17 @@ def _round_trips(torch, dims, u, bounds, stream, out):
         out.append((packed, tau, ho.numpy().copy()))
 
 
-def test_two_streams_from_two_threads_match_serial(cuda):
-    """Two host threads each run packed round trips of their own field on
+def test_streams_from_several_threads_match_serial(cuda):
+    """Four host threads each run packed round trips of their own field on
     their own stream at the same time (each stream's first calls make its
-    scratch while the other stream has work in flight): every packed stream
+    scratch while the others have work in flight; the four shapes launch the
+    same kernels with different shared-memory sizes): every packed stream
     and every reconstruction equals that of the same calls made one after
     another, and each reconstruction stays within tau of its field."""
     import threading
     torch = cuda
-    cases = [((129, 257, 65), F.grf_field((129, 257, 65), seed=11)),
-             ((65, 129, 97), F.grf_field((65, 129, 97), seed=12))]
+    shapes = [(129, 257, 65), (65, 129, 97), (257, 129, 33), (97, 65, 129)]
+    cases = [(d, F.grf_field(d, seed=11 + i)) for i, d in enumerate(shapes)]
     bounds = (1e-2, 1e-3, 1e-4)
     serial = []
     for dims, u in cases:
