@@ -426,7 +426,9 @@ int mgard_huffman_lengths(int nsym, const uint64_t* counts, uint8_t* lengths);
 int mgard_cost_model(int ndim, const int64_t* dims, int stop_level, const double* tau_levels,
                      double range, double* bits);
 
-/* Free every cached plan (device tables included) of the current device. */
+/* Free every cached plan (device tables included) of the current device.
+ * Call it only while no other host thread is inside a call of this library
+ * on the device: a call in progress may hold one of the freed plans. */
 int mgard_release_plans(void);
 
 /* Batched form: many 3D FP32 fields of uneven shape on uniform grids,
