@@ -37,6 +37,8 @@
  *    stream needs while it waits; only mgard_decompose_adaptive waits under
  *    a per-device lock.  That per-stream scratch (about 20 KB) is made by a
  *    stream's first such call, so make that call outside any stream capture.
+ *    It is keyed by the handle: threads that all pass NULL or
+ *    cudaStreamPerThread share one scratch and take turns on its waits.
  *    mgard_decompose_noalloc is the exception: its calls share one array
  *    per device and must not overlap (see there).
  *  - The first call for a given (device, dims, coords, dtype) builds a plan
