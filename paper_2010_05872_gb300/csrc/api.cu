@@ -1251,7 +1251,8 @@ const char* mgard_error_string(int code) {
   switch (code) {
     case MGARD_OK: return "ok";
     case MGARD_ERR_ARG: return "invalid argument (null or misaligned pointer, bad dtype, tau <= 0)";
-    case MGARD_ERR_SHAPE: return "invalid shape (ndim must be 1..3 and every axis >= 3 nodes)";
+    case MGARD_ERR_SHAPE:
+      return "invalid shape (ndim, or an axis length or node count outside the call's limits)";
     case MGARD_ERR_COORDS: return "coordinates must be finite and strictly increasing";
     case MGARD_ERR_LEVEL: return "stop level outside [0, L]";
     case MGARD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
