@@ -99,6 +99,19 @@ def test_argument_errors(lib):
     assert lib.mgard_error_string(-5).decode().startswith("workspace")
 
 
+def test_axis_length_limits(lib):
+    """The last (contiguous) axis may have up to 2^30 nodes, every other
+    axis up to 2^18 (they index CUDA grid dimensions); one more is a shape
+    error, found on the host."""
+    assert _rc(B.mgard_num_levels, (3, 2 ** 30)) == 0
+    assert _rc(B.mgard_num_levels, (3, 2 ** 30 + 1)) == -2
+    assert _rc(B.mgard_num_levels, (2 ** 18, 3)) == 0
+    assert _rc(B.mgard_num_levels, (2 ** 18 + 1, 3)) == -2
+    assert _rc(B.mgard_num_levels, (3, 2 ** 18 + 1, 3)) == -2
+    assert _rc(B.mgard_num_levels, (2 ** 30,)) == 0
+    assert _rc(B.mgard_num_levels, (2 ** 30 + 1,)) == -2
+
+
 @pytest.mark.parametrize("dims,kind", [((33, 20, 17), "u"), ((10, 17, 9), "g"), ((1000,), "g"),
                                        ((70, 45), "u")])
 def test_level_grid_matches_oracle(lib, dims, kind):
