@@ -227,7 +227,7 @@ def run_reference(args, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{n}^3 FP32 k^-5/3 field per step (the 513^3 workload's "
-                                   f"recipe at a size that fits the time budget), full depth, "
+                                   f"recipe at a size one host core runs in seconds), full depth, "
                                    f"range+decompose+quantize+dequantize+recompose in FP64"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -40,7 +40,7 @@ explicit finite-element operators assembled from the grid coordinates:
 * Progressive recomposition (Section 1, data refactoring): ``Q_k u`` on the
   level-k grid from the decomposed array; and the iso-surface area of a 3D
   grid function (Section 6.2.2's analysis) by marching tetrahedra.
-* The labels' lossless stage (Algorithm 1 line 23; this build's coder is a
+* The labels' lossless stage (Algorithm 1 line 23; this library's coder is a
   chunked zigzag bit packing, a reading) and PSNR (Section 6, "Quality").
 * The other bin-width rules of Section 4.1: L-infinity-optimal widths and
   L2 error control.
@@ -649,7 +649,7 @@ def _zigzag(k: int) -> int:
 
 def pack_labels(labels) -> bytes:
     """The labels' lossless stream.  The paper passes the labels to a
-    general-purpose lossless coder; this build's coder (a reading) packs
+    general-purpose lossless coder; this library's coder (a reading) packs
     them in chunks of 1024: each label is zigzag-coded and stored in the
     chunk's width w, the bit length of the chunk's largest code (0 when all
     are 0), least significant bit first, in little-endian 64-bit words.
