@@ -85,7 +85,7 @@ int mgard_workspace_size(int ndim, const int64_t* dims, int dtype, size_t* bytes
 
 /* Level tolerances tau_l, l = 0..L (host array of L+1 doubles; entries below
  * stop_level repeat tau_{l~}).  Eq. (LinfTau) of Section 4.1 with the
- * stopping level of Algorithm 1 (lines 17-20):
+ * stopping level of Algorithm 1:
  *   tau_{l~} = (1 - k) tau_linf / ((1 - k^(L+1-l~)) C_Linf),
  *   tau_l = k tau_{l-1},  k = sqrt(2^ndim),
  * and C_Linf = 1 + max over decomposed levels of an upper bound of the
@@ -131,7 +131,8 @@ int mgard_dequantize_levels(int ndim, const int64_t* dims, const double* const* 
                             int stop_level, const double* tau_levels, const int64_t* labels,
                             void* coeffs, void* stream);
 
-/* Adaptive decomposition, in place (Section 4.2, Algorithm 1 lines 1-16):
+/* Adaptive decomposition, in place (Section 4.2; the stopping-level search
+ * of Algorithm 1):
  * for l = L, L-1, .., 1 the level-l grid is sampled (the cells of the
  * level-(l-1) grid with every index a multiple of 4, i.e. one 3^3 block in
  * four per dimension) and, over the coefficient nodes of the sampled blocks,
@@ -140,7 +141,7 @@ int mgard_dequantize_levels(int ndim, const int64_t* dims, const double* const* 
  * p = 0.369 / 0.259 / 0.182 at edge / plane / cube nodes) are summed in
  * FP64 (the per-node residuals in the grid's precision), with tau_0 the
  * tolerance of level l were it the stopping level
- * (line 3; tau_linf absolute, > 0) and Lorenzo neighbours outside the grid
+ * (tau_linf absolute, > 0) and Lorenzo neighbours outside the grid
  * taken as 0.  If E_Lorenzo < E_interp the decomposition stops at l~ = l;
  * otherwise level l is decomposed and the loop goes on; l~ = 0 when no level
  * stops it.  On return *stop_out = l~ and `data` equals mgard_decompose with
@@ -194,7 +195,7 @@ int mgard_recompose(int ndim, const int64_t* dims, const double* const* coords, 
                     int stop_level, void* data, void* workspace, size_t ws_bytes,
                     void* stream);
 
-/* Level-wise quantization (Section 4.1; Algorithm 1 lines 17-22).  For
+/* Level-wise quantization (Section 4.1; Algorithm 1's quantization).  For
  * every node x of the finest grid, with l the least level such that x is in
  * N_l, raised to stop_level: labels[x] = round(coeffs[x] / (2 tau_l)) with
  * ties away from zero, in FP64 (IEEE division).  `coeffs` (dtype) and
@@ -295,8 +296,8 @@ int mgard_decompress_host(int ndim, const int64_t* dims, const double* const* co
                           void* host_field, void* dev_data, int64_t* dev_labels, void* workspace,
                           size_t ws_bytes, void* stream);
 
-/* The coarse part's Lorenzo coder (Algorithm 1 line 18, Section 4.2 Eq.
- * lorenzo) as an exact transform of the labels: mgard_lorenzo_encode
+/* The coarse part's Lorenzo coder (the coarse part's coder in Algorithm 1;
+ * Section 4.2 Eq. lorenzo) as an exact transform of the labels: mgard_lorenzo_encode
  * replaces the labels q of the coarse block N_{stop_level} (in the finest
  * layout, device, in place) by q - pred(q), pred the signed sum of the
  * lower neighbours in the coarse grid (0 outside it), in 64-bit
@@ -311,7 +312,7 @@ int mgard_lorenzo_decode(int ndim, const int64_t* dims, const double* const* coo
                          int stop_level, int64_t* labels, void* stream);
 
 /* The labels' lossless stage (Section 4.1: labels go to a lossless coder;
- * Algorithm 1 line 23).  This library's coder packs the labels in chunks
+ * the last step of Algorithm 1).  This library's coder packs the labels in chunks
  * of 1024: zigzag codes (0, -1, 1, -2, .. -> 0, 1, 2, 3, ..) in the chunk's
  * width w (bit length of its largest code), least significant bit first.
  * Stream (little-endian): uint64 count | one width byte per chunk | zero
@@ -391,7 +392,7 @@ int mgard_dequantize_4d(const int64_t* dims, const double* const* coords, int dt
                         double tau_linf, const int64_t* labels, void* coeffs, void* stream);
 
 /* Canonical Huffman coding of the labels (a reading of the lossless encoder
- * of Algorithm 1 line 23, which the paper does not name), the labels'
+ * that Algorithm 1 ends with, which the paper does not name), the labels'
  * order-0 entropy and the cost model of Section 4.1.
  * Stream (little-endian): uint64 N | uint32 K = 32817 | uint32 longest code
  * length (<= 31) | K bytes of code lengths per symbol (0 = unused) | zero

@@ -30,24 +30,24 @@ explicit finite-element operators assembled from the grid coordinates:
   ``z = Q_{l-1}(w)`` of the coefficient function ``w``, subtraction, then
   interpolation plus coefficients.
 * Level tolerances: Eq. (LinfTau) of Section 4.1 with the stopping level of
-  Algorithm 1 (lines 17-20): ``tau_l~ = (1-k) tau / ((1-k^(L+1-l~)) C)``,
+  Algorithm 1: ``tau_l~ = (1-k) tau / ((1-k^(L+1-l~)) C)``,
   ``tau_l = k tau_{l-1}``, ``k = sqrt(2^d)``.
 * Quantizer (Section 4.1): zero-centred bins of width ``q_l = 2 tau_l``,
   label ``round(x / q_l)`` with ties away from zero, value ``label * q_l``.
-* Adaptive stopping level (Section 4.2, Algorithm 1 lines 1-16): sampled
-  sums of the Lorenzo and interpolation prediction errors with the paper's
+* Adaptive stopping level (Section 4.2; the stopping-level search of
+  Algorithm 1): sampled sums of the Lorenzo and interpolation prediction errors with the paper's
   penalty factors, level by level from the finest.
 * Progressive recomposition (Section 1, data refactoring): ``Q_k u`` on the
   level-k grid from the decomposed array; and the iso-surface area of a 3D
   grid function (Section 6.2.2's analysis) by marching tetrahedra.
-* The labels' lossless stage (Algorithm 1 line 23; this library's coder is a
-  chunked zigzag bit packing, a reading) and PSNR (Section 6, "Quality").
+* The labels' lossless stage (the last step of Algorithm 1; this library's
+  coder is a chunked zigzag bit packing, a reading) and PSNR (Section 6, "Quality").
 * The other bin-width rules of Section 4.1: L-infinity-optimal widths and
   L2 error control.
-* The coarse part's Lorenzo coder (Algorithm 1 line 18): Lorenzo residuals
-  of the coarse block's labels and their inverse.
+* The coarse part's Lorenzo coder (the coarse part's coder in Algorithm 1):
+  Lorenzo residuals of the coarse block's labels and their inverse.
 * The labels' order-0 entropy and the cost model of Section 4.1, and a
-  canonical Huffman coder of the labels (a reading of Algorithm 1 line 23's
+  canonical Huffman coder of the labels (a reading of Algorithm 1's final
   lossless encoder, which the paper does not name).
 
 Readings of points the paper leaves open (non-dyadic hierarchy, depth for
@@ -377,8 +377,8 @@ def level_tolerances(H: Hierarchy, stop_level: int, tau: float,
     """Per-level tolerances ``tau_l`` for ``l = 0..L`` (entries below the
     stopping level are unused and set to ``tau_{l~}``).
 
-    Algorithm 1 line 17 gives ``tau_{l~}``; lines 19-20 scale by
-    ``kappa = sqrt(2^d)`` per level (Eq. (LinfTau) with the sum starting at
+    Algorithm 1 sets the stopping level's tolerance first and scales it by
+    ``kappa = sqrt(2^d)`` per finer level (Eq. (LinfTau) with the sum starting at
     the stopping level), so that ``sum_{l>=l~} tau_l = tau / C``."""
     _check_stop(H, stop_level)
     if C is None:
@@ -399,8 +399,8 @@ def level_tolerances(H: Hierarchy, stop_level: int, tau: float,
 def node_levels(H: Hierarchy, stop_level: int = 0) -> np.ndarray:
     """Level of every finest node: the least ``l`` with the node in ``N_l``
     (Section 2's indexing of ``u_mc``), raised to the stopping level because
-    the whole of ``N_{l~}`` is quantized with ``tau_{l~}`` (Algorithm 1 lines
-    17-18)."""
+    the whole of ``N_{l~}`` is quantized with ``tau_{l~}`` (as Algorithm 1
+    does)."""
     per_axis = []
     for d in range(H.ndim):
         lev = np.full(H.levels[H.L][d], H.L, dtype=np.int64)
@@ -446,7 +446,7 @@ def value_range(u: np.ndarray) -> float:
 
 
 # --------------------------------------------------------------------------
-# Adaptive stopping level (Section 4.2, Algorithm 1 lines 1-16)
+# Adaptive stopping level (Section 4.2, Algorithm 1's stopping-level search)
 # --------------------------------------------------------------------------
 
 # Penalty factors, in units of the level's tolerance tau_0 (Section 4.2): the
@@ -490,8 +490,8 @@ def _lorenzo(v: np.ndarray, idx) -> float:
 
 
 def prediction_errors(v: np.ndarray, H: Hierarchy, l: int, tau0: float):
-    """``(E_Lorenzo, E_interp)`` of Algorithm 1 lines 5-9 for the level-l
-    grid ``v``: over every coefficient node (a node outside ``N_{l-1}``) of
+    """``(E_Lorenzo, E_interp)``, Algorithm 1's sampled prediction errors, for
+    the level-l grid ``v``: over every coefficient node (a node outside ``N_{l-1}``) of
     the sampled blocks, ``|Lorenzo prediction - v| + 1.22 tau0`` and
     ``|Pi_{l-1} v - v| + p tau0`` with ``p`` the edge / plane / cube penalty
     of the node (Eqs. (lorenzo), (interp)).  Interpolation uses the grid's
@@ -526,8 +526,8 @@ def prediction_errors(v: np.ndarray, H: Hierarchy, l: int, tau0: float):
 
 
 def adaptive_stop_level(u: np.ndarray, H: Hierarchy, tau: float):
-    """Algorithm 1 lines 1-16: for ``l = L, L-1, ..``, with ``tau_0`` the
-    tolerance of level ``l`` were it the stopping level (line 3), sample
+    """Algorithm 1's stopping-level search: for ``l = L, L-1, ..``, with ``tau_0`` the
+    tolerance of level ``l`` were it the stopping level, sample
     ``Q_l u`` and stop at ``l`` when the Lorenzo estimate is below the
     interpolation estimate; otherwise project to ``Q_{l-1} u`` and go on.
     Reading: the loop ends at level 1 (a level-0 grid has no coarser grid to
@@ -634,7 +634,8 @@ def iso_area(v: np.ndarray, coords, iso: float) -> float:
 
 
 # --------------------------------------------------------------------------
-# Lossless stage for the labels (Section 4.1, Algorithm 1 line 23) and PSNR
+# Lossless stage for the labels (Section 4.1, the last step of Algorithm 1)
+# and PSNR
 # (Section 6, "Quality")
 # --------------------------------------------------------------------------
 
@@ -780,7 +781,8 @@ def l2_error(e: np.ndarray, H: Hierarchy) -> float:
 
 
 # --------------------------------------------------------------------------
-# Coarse-part predictor (Algorithm 1 line 18; Section 4.2, Eq. (lorenzo))
+# Coarse-part predictor (the coarse part's coder in Algorithm 1; Section 4.2,
+# Eq. (lorenzo))
 # --------------------------------------------------------------------------
 
 def _coarse_block(labels, H: Hierarchy, stop_level: int):
@@ -830,7 +832,7 @@ def lorenzo_decode(labels: np.ndarray, H: Hierarchy, stop_level: int) -> np.ndar
 
 # --------------------------------------------------------------------------
 # Entropy of the labels and the cost model (Section 4.1), and a canonical
-# Huffman coder of the labels (a reading of Algorithm 1 line 23's lossless
+# Huffman coder of the labels (a reading of Algorithm 1's final lossless
 # encoder)
 # --------------------------------------------------------------------------
 

@@ -1,5 +1,5 @@
 // Sampled prediction-error sums of the adaptive stopping level (Section 4.2,
-// Algorithm 1 lines 4-9) on one level-l grid.
+// Algorithm 1's sampled prediction errors) on one level-l grid.
 //
 // The sampled blocks are the cells of the level-(l-1) grid whose index is a
 // multiple of 4 along every axis (one block in four per dimension); a cell

@@ -318,8 +318,8 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
 // ahead of their decisions.
 constexpr int64_t kAdaptiveAheadNodes = 20000000;
 
-// Adaptive decomposition (Algorithm 1, lines 1-16): from the finest level
-// down, the sampled prediction-error sums of the level-l grid decide between
+// Adaptive decomposition (the stopping-level search of Algorithm 1): from
+// the finest level down, the sampled prediction-error sums of the level-l grid decide between
 // stopping at l and decomposing it; then the finish passes of the decomposed
 // levels.  One host synchronization per sampled level.
 template <typename T>
@@ -352,7 +352,7 @@ int run_adaptive(const DevPlan& p, double tau, T* data, char* ws, DevCtx* c, cud
   int l = L;
   // Large levels one at a time: sample, wait for the sums, decide.
   for (; l >= 1 && nodes(l) > kAdaptiveAheadNodes; --l) {
-    level_tolerances(p.h, l, tau, t);  // t[l]: tau_0 were l the stopping level (line 3)
+    level_tolerances(p.h, l, tau, t);  // t[l]: tau_0 were l the stopping level
     MGB_TRY(launch_prediction_errors<T>(lv[l], B[l], t[l], c->partial, c->sums + 2 * l, l, s));
     MGB_TRY(cudaMemcpyAsync(c->h_sums + 2 * l, c->sums + 2 * l, 2 * sizeof(double),
                             cudaMemcpyDeviceToHost, s));

@@ -1,5 +1,5 @@
-// The coarse part's Lorenzo coder (Algorithm 1 line 18; Section 4.2, Eq.
-// (lorenzo)), as an exact integer transform of the coarse block's labels.
+// The coarse part's Lorenzo coder (the coarse part's coder in Algorithm 1;
+// Section 4.2, Eq. (lorenzo)), as an exact integer transform of the coarse block's labels.
 //
 // The labels of N_{l~} are the linear quantization of Q_{l~}u with bin
 // 2 tau_{l~}; replacing each by its Lorenzo residual r = q - pred(q) (pred

@@ -1,4 +1,4 @@
-// The labels' lossless stage (Algorithm 1 line 23): a chunked zigzag
+// The labels' lossless stage (the last step of Algorithm 1): a chunked zigzag
 // bit-packing coder, so that compressed labels, not 8-byte integers, cross
 // between host and device.
 //

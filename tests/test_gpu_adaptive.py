@@ -1,5 +1,5 @@
-"""GPU parity of the adaptive stopping level (Section 4.2, Algorithm 1 lines
-1-16) with the FP64 oracle: the chosen level, the sampled error sums of every
+"""GPU parity of the adaptive stopping level (Section 4.2, the stopping-level
+search of Algorithm 1) with the FP64 oracle: the chosen level, the sampled error sums of every
 sampled level, and the decomposed array.
 
 Tolerances: the sums are FP64 on both sides; with FP64 data the level grids
