@@ -1,5 +1,6 @@
 // sm_103a kernels of level-wise quantization (Section 4.1; the quantization
-// step of Algorithm 1), dequantization and the value range that scales a relative bound.
+// step of Algorithm 1), dequantization and the value range that scales a
+// relative bound.
 //
 // Both quantizer directions are defined in FP64 (label = round(x / q) with
 // ties away from zero; value = label * q rounded to the element type).  FP64
