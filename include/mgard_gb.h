@@ -64,7 +64,8 @@ enum { MGARD_F32 = 0, MGARD_F64 = 1 };
 enum {
   MGARD_OK = 0,
   MGARD_ERR_ARG = -1,       /* NULL or misaligned pointer, bad dtype/ndim, tau <= 0 */
-  MGARD_ERR_SHAPE = -2,     /* ndim outside 1..3, or an axis outside 3..2^30 (last) / 3..2^18 (others) */
+  MGARD_ERR_SHAPE = -2,     /* ndim outside 1..3, or an axis outside 3..2^30 (the last)
+                               or 3..2^18 (the others) */
   MGARD_ERR_COORDS = -3,    /* coordinates not finite or not strictly increasing */
   MGARD_ERR_LEVEL = -4,     /* stop_level outside [0, L] */
   MGARD_ERR_WORKSPACE = -5, /* workspace NULL, misaligned or smaller than required */

@@ -208,7 +208,8 @@ StreamScratch* get_scratch(cudaStream_t s) {
   void* dmem = nullptr;
   const size_t bytes = 256 + sizeof(double) * (2 * kMinmaxBlocks + 2);
   if (cudaMalloc(&dmem, bytes) != cudaSuccess) return nullptr;
-  if (cudaMemset(dmem, 0, bytes) != cudaSuccess || cudaMallocHost(&sc->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
+  if (cudaMemset(dmem, 0, bytes) != cudaSuccess ||
+      cudaMallocHost(&sc->h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaFree(dmem);
     return nullptr;
   }
@@ -319,9 +320,9 @@ int run_recompose(const DevPlan& p, int stop, T* data, char* ws, unsigned int* s
 constexpr int64_t kAdaptiveAheadNodes = 20000000;
 
 // Adaptive decomposition (the stopping-level search of Algorithm 1): from
-// the finest level down, the sampled prediction-error sums of the level-l grid decide between
-// stopping at l and decomposing it; then the finish passes of the decomposed
-// levels.  One host synchronization per sampled level.
+// the finest level down, the sampled prediction-error sums of the level-l
+// grid decide between stopping at l and decomposing it; then the finish
+// passes of the decomposed levels.  One host synchronization per sampled level.
 template <typename T>
 int run_adaptive(const DevPlan& p, double tau, T* data, char* ws, DevCtx* c, cudaStream_t s,
                  int* stop_out, double* sums) {
