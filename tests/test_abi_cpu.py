@@ -303,3 +303,38 @@ def test_product_never_reaches_the_oracle():
     start = bench.index("# ------------------------------------------------------------ oracle leg ---")
     end = bench.index("# ---------------------------------------------------------------- clocks ---")
     assert all(start < i < end for i in imports)
+
+
+def test_host_plans_build_the_same_from_many_threads(lib):
+    """The host-only calls build their operator tables per call: eight
+    threads asking at once for the tolerances of mixed shapes and
+    coordinates get what one thread gets."""
+    import threading
+    rng = np.random.default_rng(5)
+    cases = []
+    for i in range(24):
+        dims = tuple(int(v) for v in rng.integers(3, 90, size=1 + i % 3))
+        coords = None
+        if i % 2:
+            coords = [np.cumsum(rng.uniform(0.5, 1.5, n)) for n in dims]
+        cases.append((dims, coords, i % 3, 10.0 ** -(1 + i % 4)))
+
+    def run(case):
+        dims, coords, stop, tau = case
+        stop = min(stop, B.mgard_num_levels(dims))
+        return B.mgard_level_tolerances(dims, coords, stop, tau)
+
+    want = [run(c) for c in cases]
+    got = [None] * len(cases)
+
+    def worker(q):
+        for k in range(q, len(cases), 8):
+            got[k] = run(cases[k])
+
+    threads = [threading.Thread(target=worker, args=(q,)) for q in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for w, g in zip(want, got):
+        assert np.array_equal(np.asarray(w), np.asarray(g))
