@@ -65,6 +65,9 @@ CASES = [
     # 2^k + 1 rows (257 and 129 coarse columns): the left-over column of the
     # paired load-vector rows is taken one staged row per lane.
     ((129, 65, 257), "g", 0), ((300, 513), "z", 0),
+    # Odd axes that are not 2^k + 1 (the all-odd-grid load vector at the top
+    # level, general levels below it).
+    ((75, 67, 139), "g", 0), ((301, 771), "u", 0),
     # Coarse planes of >= 19600 lines: the axis-0 (then axis-1) solves of the
     # top level take the persistent pipelined segmented form.
     ((40, 279, 279), "g", 0), ((279, 40, 279), "g", 0),
