@@ -555,8 +555,8 @@ def recompose_partial(umc: np.ndarray, H: Hierarchy, stop_level: int, level: int
     (stopping level ``stop_level`` <= k = ``level`` <= L): the refactored
     reconstruction of reduced size that Section 1 describes, obtained by
     summing the components of levels ``stop_level .. k`` only, i.e. the
-    recomposition of the levels up to k (Section 2, recomposition steps
-    1-5, stopped at level k)."""
+    recomposition of the levels up to k (Section 2's recomposition,
+    stopped at level k)."""
     _check_stop(H, stop_level)
     if not stop_level <= level <= H.L:
         raise ValueError("target level outside [stop level, L]")

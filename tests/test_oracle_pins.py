@@ -449,6 +449,27 @@ def test_tolerances_sum_and_ratio(dims, stop):
     assert t[stop:].sum() == pytest.approx(tau / C, rel=1e-13)
 
 
+def test_llround_matches_exact_rational_rounding():
+    """Against rounding done in exact rational arithmetic (half away from
+    zero) on random doubles of every magnitude up to 2^62, halves and their
+    neighbours included."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    mags = 2.0 ** rng.uniform(-3, 62, 4000)
+    y = np.concatenate([mags * rng.choice([-1.0, 1.0], mags.size),
+                        np.arange(-40, 41) + 0.5,
+                        np.nextafter(np.arange(-40, 41) + 0.5, np.inf),
+                        np.nextafter(np.arange(-40, 41) + 0.5, -np.inf)])
+    y = y[np.abs(y) < 2.0 ** 62]
+
+    def exact(x):
+        f = Fraction(float(x))
+        r = int(abs(f) + Fraction(1, 2))  # floor(|x| + 1/2): int() truncates a positive value
+        return r if f >= 0 else -r
+
+    assert O.llround(y).tolist() == [exact(x) for x in y]
+
+
 def test_llround_ties_and_edges():
     y = np.array([0.5, -0.5, 1.5, -1.5, 2.5, -2.5, 0.49999999999999994,
                   -0.49999999999999994, 4503599627370495.5, 1e17, -3.0, 0.0])
@@ -709,6 +730,20 @@ def test_psnr_closed_form():
     v = np.array([0.0, 1.1])
     # range 1, mean squared error 0.005
     assert O.psnr(u, v) == pytest.approx(-10 * np.log10(0.005), rel=1e-14)
+
+
+def test_psnr_uses_the_range_of_the_original():
+    """The range term is max u - min u (the reading of the garbled printed
+    formula): a reconstruction whose minimum differs from the original's
+    (here 0.1 against 0) must not change it, and a uniform offset e of a
+    field of range R gives 20 log10(R / |e|)."""
+    u = np.array([0.0, 1.0])
+    v = np.array([0.1, 1.0])
+    assert O.psnr(u, v) == pytest.approx(-10 * np.log10(0.005), rel=1e-14)
+    w = np.random.default_rng(3).uniform(-2.0, 5.0, (7, 5, 3))
+    R = float(w.max() - w.min())
+    assert O.psnr(w, w + 0.01) == pytest.approx(20 * np.log10(R / 0.01), rel=1e-12)
+    assert O.psnr(w, w - 0.01) == pytest.approx(20 * np.log10(R / 0.01), rel=1e-12)
 
 
 # --------------------------------------- L-inf-optimal and L2 bin widths ---
