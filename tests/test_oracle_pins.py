@@ -238,6 +238,29 @@ def test_dense_kronecker_projection(dims, nonuni):
     np.testing.assert_allclose(z.ravel(), z_dense, atol=1e-12)
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mass_matrix_integrates_exactly(seed):
+    """On any grid the P1 mass matrix gives the exact L2 inner products of
+    the functions the space holds: with 1 and x sampled at the nodes of
+    [a, b], 1'M1 = b - a, 1'Mx = (b^2 - a^2)/2 and x'Mx = (b^3 - a^3)/3."""
+    rng = np.random.default_rng(seed)
+    x = np.cumsum(rng.uniform(0.1, 2.0, 9 + seed)) - 3.0
+    a, b = x[0], x[-1]
+    M = O.mass_matrix(x).toarray()
+    one = np.ones_like(x)
+    assert one @ M @ one == pytest.approx(b - a, rel=1e-13)
+    assert one @ M @ x == pytest.approx((b * b - a * a) / 2, rel=1e-12, abs=1e-12)
+    assert x @ M @ x == pytest.approx((b ** 3 - a ** 3) / 3, rel=1e-12)
+
+
+def test_mass_matrix_three_nodes_by_hand():
+    """x = (0, 1, 3): elements of length 1 and 2, each contributing
+    h/3 on its diagonal and h/6 off it."""
+    M = O.mass_matrix(np.array([0.0, 1.0, 3.0])).toarray()
+    exp = np.array([[1 / 3, 1 / 6, 0.0], [1 / 6, 1.0, 1 / 3], [0.0, 1 / 3, 2 / 3]])
+    np.testing.assert_allclose(M, exp, rtol=1e-15, atol=1e-16)
+
+
 def test_galerkin_coarse_mass():
     """M_c assembled on the coarse coordinates equals P^T M_f P (nested P1
     spaces)."""
