@@ -58,7 +58,8 @@ struct MarchCfg<double> {
 // have odd lengths, so coarse node k sits at 2k on each and the taps that
 // are zero there are skipped (a column's 5-tap R window starts at its
 // node - 2, its X taps sit at even offsets, an odd staged row feeds two
-// coarse rows, an odd plane feeds two coarse planes through R0 alone).  PERSIST: the CTA runs further tiles in the same launch, so the tile
+// coarse rows, an odd plane feeds two coarse planes through R0 alone).
+// PERSIST: the CTA runs further tiles in the same launch, so the tile
 // invalidates its barriers at the end (the next tile sets them up again) and
 // reads its few plain-loaded elements through L2 (other CTAs of the launch
 // may have written them).
@@ -214,7 +215,8 @@ __device__ __forceinline__ void load_vector_march_tile(const LevelK<T>& lv,
     mbar_arrive_expect_tx(&bars[slot], bytes);
     if (bytes) tma_bulk_g2s(dst, reinterpret_cast<const char*>(fine) + ab, bytes, &bars[slot]);
     for (uint64_t x = bb > sb ? bb : sb; x < eb; x += sizeof(T))
-      dst[shift + static_cast<int>((x - sb) / sizeof(T))] = PERSIST ? __ldcg(fine + x / sizeof(T)) : fine[x / sizeof(T)];
+      dst[shift + static_cast<int>((x - sb) / sizeof(T))] =
+          PERSIST ? __ldcg(fine + x / sizeof(T)) : fine[x / sizeof(T)];
   };
 
   T acc[CPT][3][TM];
