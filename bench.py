@@ -865,7 +865,7 @@ def run_gpu(args, rank, world, local_rank):
               torch.empty(cap, dtype=torch.uint8).pin_memory(),
               torch.empty(DIMS, dtype=torch.float32).pin_memory())
              for _ in range(lanes_in_flight - 1)]
-    ke2 = lanes_in_flight * ke
+    ke2 = lanes_in_flight * max(ke, 6)  # enough steps per field to amortize filling the pipeline
     e2e_ms = timed_e2e_lanes([lane0] + extra, ke2) * ke / ke2
     del extra
     # Rate and distortion per bound (Section 6, "Quality"): compression
