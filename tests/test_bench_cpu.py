@@ -50,3 +50,30 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert len(lines) == 1, run.stdout[-2000:]
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_algorithmic_counts_match_hand_sums():
+    """The level shapes and the path's algorithmic bytes behind every
+    roofline fraction, against sums written out by hand: 513^3 coarsens
+    513, 257, .., 5, 3 (L = 8) and its decomposed levels hold 154,443,308
+    nodes; 500 x 500 x 100 has L = 6 with N_3 = 64 x 64 x 14 and
+    N_0 = 9 x 9 x 3, and 458,013,232 / 459,093,248 bytes at stopping
+    levels 3 / 0 in FP32 (one read and one write per level and direction)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    s513 = bench.level_sizes((513, 513, 513))
+    assert [v[0] for v in s513] == [513, 257, 129, 65, 33, 17, 9, 5, 3]
+    nodes = sum(n ** 3 for n in (513, 257, 129, 65, 33, 17, 9, 5))
+    assert nodes == 154_443_308
+    assert bench.level_nodes((513, 513, 513)) == nodes
+    assert bench.path_bytes((513, 513, 513), 0, 4) == 16 * nodes
+    assert bench.path_bytes((513, 513, 513), 0, 8) == 32 * nodes
+    s5 = bench.level_sizes((500, 500, 100))
+    assert len(s5) - 1 == 6
+    assert s5[6 - 3] == [64, 64, 14] and s5[6] == [9, 9, 3]
+    top3 = 500 * 500 * 100 + 251 * 251 * 51 + 126 * 126 * 26
+    assert bench.path_bytes((500, 500, 100), 3, 4) == 16 * top3 == 458_013_232
+    all6 = top3 + 64 * 64 * 14 + 33 * 33 * 8 + 17 * 17 * 5
+    assert bench.path_bytes((500, 500, 100), 0, 4) == 16 * all6 == 459_093_248
+    # A stopping level equal to L decomposes nothing.
+    assert bench.path_bytes((65, 65, 65), 5, 4) == 0
